@@ -1,0 +1,171 @@
+"""Oracle A: dense FFT-based homogenisation (the basic scheme, Alg. 1), fp64.
+
+Test infrastructure only (see ``oracle/__init__.py``).
+
+Conventions (readings of the paper, each stated once here):
+  * Voigt order (11, 22, 33, 23, 13, 12). Strains carry engineering shear
+    (gamma = 2 eps), stresses do not, so sigma_V = C_V eps_V (Sec. 2, Voigt
+    paragraph).
+  * Reference medium C0: isotropic with the arithmetic mean of the smallest and
+    largest phase Lame parameters (the paper does not state C0).
+  * Fourier transform: numpy's forward FFT (exp(-2 pi i k x / N)) with numpy's
+    frequency representatives (Nyquist at -N/2). This is the same discrete
+    operator as the SFFT scheme's exp(+2 pi i k x / N) transform with the
+    paper's representatives {-N/2+1, ..., N/2} (App. A) and the conjugated
+    momentum-space operator (Sec. 4.3).
+  * Nyquist symmetrisation (App. A) is read literally: Gamma is real and even in
+    q, so the averaging leaves it unchanged. Iterates are therefore complex;
+    C_eff takes the real part and the imaginary part is reported.
+  * Stop test (Alg. 1): ||eps_{m+1} - eps_m||_F / ||E field||_F < tol, with the
+    unweighted Euclidean norm over voxels and Voigt components.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.fft as sfft
+
+# Voigt index I -> tensor pair (i, j); weight 2 on shear components.
+VOIGT = ((0, 0), (1, 1), (2, 2), (1, 2), (0, 2), (0, 1))
+WEIGHT = np.array([1.0, 1.0, 1.0, 2.0, 2.0, 2.0])
+
+
+def lame(E: float, nu: float):
+    """Lame parameters of an isotropic phase from Young's modulus and Poisson ratio."""
+    lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu))
+    mu = E / (2.0 * (1.0 + nu))
+    return lam, mu
+
+
+def stiffness_tensor(lam: float, mu: float) -> np.ndarray:
+    """Isotropic C_ijkl = lam d_ij d_kl + mu (d_ik d_jl + d_il d_jk)."""
+    d = np.eye(3)
+    return (lam * np.einsum("ij,kl->ijkl", d, d)
+            + mu * (np.einsum("ik,jl->ijkl", d, d) + np.einsum("il,jk->ijkl", d, d)))
+
+
+def stiffness_voigt(lam: float, mu: float) -> np.ndarray:
+    """6x6 Voigt stiffness acting on engineering strain (Sec. 2, Voigt notation)."""
+    C = stiffness_tensor(lam, mu)
+    return np.array([[C[i, j, k, l] for (k, l) in VOIGT] for (i, j) in VOIGT])
+
+
+def reference_lame(E, nu):
+    """(lam0, mu0): arithmetic mean of min and max phase Lame parameters."""
+    lm = [lame(e, v) for e, v in zip(E, nu)]
+    lams = [a for a, _ in lm]
+    mus = [b for _, b in lm]
+    return 0.5 * (min(lams) + max(lams)), 0.5 * (min(mus) + max(mus))
+
+
+def green_tensor_direct(xi: np.ndarray, lam0: float, mu0: float) -> np.ndarray:
+    """Gamma^0_ijkl(xi) of the Direct scheme (k = i q, App. A Table) for an
+    isotropic C0, from eq. (orig_green_eshelby) worked out in closed form:
+
+      Gamma_ijkl = (d_ik n_j n_l + d_il n_j n_k + d_jk n_i n_l + d_jl n_i n_k)/(4 mu0)
+                   - (lam0 + mu0)/(mu0 (lam0 + 2 mu0)) n_i n_j n_k n_l,
+    with n = xi/|xi|, and Gamma(0) = 0.  xi: (..., 3) array. Returns (..., 3,3,3,3)."""
+    xi = np.asarray(xi, dtype=np.float64)
+    r2 = np.sum(xi * xi, axis=-1)
+    zero = r2 == 0
+    nrm = np.sqrt(np.where(zero, 1.0, r2))
+    n = xi / nrm[..., None]
+    d = np.eye(3)
+    t1 = (np.einsum("ik,...j,...l->...ijkl", d, n, n) + np.einsum("il,...j,...k->...ijkl", d, n, n)
+          + np.einsum("jk,...i,...l->...ijkl", d, n, n) + np.einsum("jl,...i,...k->...ijkl", d, n, n))
+    beta0 = (lam0 + mu0) / (mu0 * (lam0 + 2.0 * mu0))
+    t2 = np.einsum("...i,...j,...k,...l->...ijkl", n, n, n, n)
+    g = t1 / (4.0 * mu0) - beta0 * t2
+    g[zero] = 0.0
+    return g
+
+
+def green_voigt_direct(xi: np.ndarray, lam0: float, mu0: float) -> np.ndarray:
+    """Voigt form Gamma_V[I, J] = w_I w_J Gamma_{i_I j_I k_J l_J} (..., 6, 6),
+    mapping a Voigt stress-like polarisation to an engineering strain."""
+    g = green_tensor_direct(xi, lam0, mu0)
+    out = np.empty(g.shape[:-4] + (6, 6))
+    for I, (i, j) in enumerate(VOIGT):
+        for J, (k, l) in enumerate(VOIGT):
+            out[..., I, J] = WEIGHT[I] * WEIGHT[J] * g[..., i, j, k, l]
+    return out
+
+
+def frequencies(N: int) -> np.ndarray:
+    """Integer frequencies xi of numpy's FFT bins (Nyquist at -N/2); q = 2 pi xi / N."""
+    return np.fft.fftfreq(N, d=1.0 / N)
+
+
+def _stiffness_field_apply(phase, Cs, field):
+    """sum_J C(x)[I, J] field[J](x) for a phase-indexed list of 6x6 matrices."""
+    out = np.zeros_like(field)
+    for p, Cp in enumerate(Cs):
+        mask = phase == p
+        if not mask.any():
+            continue
+        out[:, mask] = Cp @ field[:, mask]
+    return out
+
+
+def _apply_green(tau_hat, lam0, mu0):
+    """eps_hat[I] = sum_J Gamma_V[I, J](xi) tau_hat[J], slab by slab in xi_1."""
+    N1, N2, N3 = tau_hat.shape[1:]
+    f1, f2, f3 = frequencies(N1), frequencies(N2), frequencies(N3)
+    out = np.empty_like(tau_hat)
+    x2, x3 = np.meshgrid(f2, f3, indexing="ij")
+    for a in range(N1):
+        xi = np.stack([np.full_like(x2, f1[a]), x2, x3], axis=-1)
+        G = green_voigt_direct(xi, lam0, mu0)               # (N2, N3, 6, 6)
+        out[:, a] = np.einsum("yzIJ,Jyz->Iyz", G, tau_hat[:, a])
+    return out
+
+
+def basic_scheme(phase, E, nu, E_voigt, tol=1e-6, max_iter=5000, lame0=None, workers=-1,
+                 eps0=None):
+    """Alg. 1 (FFT-based homogenisation) on a dense (N1, N2, N3) phase grid.
+
+    Iterates eps_{m+1} = E - IFFT[Gamma_hat FFT[(C - C0) eps_m]] from eps_0 = E
+    until ||eps_{m+1} - eps_m||_F / ||E||_F < tol (Alg. 1; LS eq.
+    (lippmann_schwinger) and its Fourier form). Returns a dict with the final
+    strain field (6, N1, N2, N3) complex, the mean stress sigma_bar = <C eps>
+    (Sec. 2, C_eff paragraph), the iteration count and the residual history."""
+    phase = np.asarray(phase)
+    lam0, mu0 = reference_lame(E, nu) if lame0 is None else lame0
+    C0 = stiffness_voigt(lam0, mu0)
+    Cs = [stiffness_voigt(*lame(e, v)) for e, v in zip(E, nu)]
+    dCs = [C - C0 for C in Cs]
+    Ev = np.asarray(E_voigt, dtype=np.float64)
+    shape = phase.shape
+    Eb = np.broadcast_to(Ev[:, None, None, None], (6,) + shape).astype(np.complex128)
+    eps = Eb.copy() if eps0 is None else np.asarray(eps0, dtype=np.complex128).copy()
+    normE = np.linalg.norm(Ev) * np.sqrt(float(np.prod(shape)))
+    hist = []
+    it = 0
+    for it in range(1, max_iter + 1):
+        tau = _stiffness_field_apply(phase, dCs, eps)
+        tau_hat = sfft.fftn(tau, axes=(1, 2, 3), workers=workers)
+        eps_hat = _apply_green(tau_hat, lam0, mu0)
+        eps_hat[:, 0, 0, 0] = 0.0
+        eps_new = Eb - sfft.ifftn(eps_hat, axes=(1, 2, 3), workers=workers)
+        rel = np.linalg.norm(eps_new - eps) / normE
+        hist.append(rel)
+        eps = eps_new
+        if rel < tol:
+            break
+    sig = _stiffness_field_apply(phase, Cs, eps).reshape(6, -1).mean(axis=1)
+    return dict(eps=eps, sigma_bar=sig, iters=it, history=hist, lame0=(lam0, mu0))
+
+
+def ceff(phase, E, nu, tol=1e-6, max_iter=5000, lame0=None, loads=range(6)):
+    """C_eff column by column from unit Voigt loads E = e_k (Sec. 2). Returns
+    (Ceff real 6x6 with column k = Re sigma_bar(e_k), max |Im sigma_bar|, iters)."""
+    C = np.zeros((6, 6))
+    imag = 0.0
+    iters = []
+    for k in loads:
+        e = np.zeros(6)
+        e[k] = 1.0
+        r = basic_scheme(phase, E, nu, e, tol=tol, max_iter=max_iter, lame0=lame0)
+        C[:, k] = r["sigma_bar"].real
+        imag = max(imag, float(np.abs(r["sigma_bar"].imag).max()))
+        iters.append(r["iters"])
+    return C, imag, iters

@@ -1,0 +1,483 @@
+"""Oracle B: the SFFT-based homogenisation scheme (Alg. 2) on quantised tensor
+trains, in plain numpy fp64/complex128. Test infrastructure only (see
+``oracle/__init__.py``).
+
+Data model (Sec. 3, eq. (tt_format) and (tto_format); Sec. 4.3):
+  * A TT is a list of cores; core k has shape (r_{k-1}, d_k, r_k), r_0 = r_L = 1.
+  * A TTO is a list of cores of shape (a_{k-1}, d_out, d_in, a_k).
+  * Controlled QTT (Sec. 4.3): core 0 is the Voigt core (d = 6); the 3n binary
+    cores (d = 2) follow, grouped by axis x1, x2, x3, most significant bit
+    first (eq. (binary_discretization)).
+  * A raised TTO (eq. (tt_to_tto)) has binary cores G(a, i, j, b) = C(a, i, b) d_ij.
+
+Steps follow the paper's order. Readings where the paper is garbled or silent:
+  * Rounding threshold (eq. (rounding_condition_tt)): the per-bond truncation
+    threshold is delta = eps ||x|| / sqrt(L - 1) (the printed 1/sqrt(1-n) is the
+    square root of a negative number); a bond keeps the smallest rank whose
+    discarded tail sum of squared singular values is <= delta^2, at least 1 and
+    at most r_max ("<=" discards ties).
+  * Matrix-vector product: the paper uses an AMEn-adapted product (App. B); this
+    oracle provides the exact contraction (Table 2, "contract") and a
+    randomized sketch-and-orthogonalise product (successive randomized
+    compression), followed by rounding. Zip-up (SVD truncation on the fly without
+    the right environment) was measured to lose 15-30 % of the product on the
+    Green operator already at n = 3 and is not used.
+  * SFFT: S = P_rev F+ per axis, F+[k, x] = N^-1/2 exp(+2 pi i k x / N), P_rev
+    reverses the n output bits (the QFT without its swap network, Sec. 4.1). The
+    MPO is obtained by TT-SVD of the dense matrix with core b carrying the pair
+    (output bit b, input bit b); the paper's Zip-Up construction (Sec. 4.2) yields
+    the same operator.
+  * Momentum convention (Sec. 4.3): Gamma is evaluated on bit-reversed indices and
+    conjugated: Gamma_S(k') = conj(Gamma(xi(rev k'))), xi in {-N/2+1, ..., N/2}.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import dense
+
+# ------------------------------------------------------------------ helpers
+
+
+def truncation_rank(s: np.ndarray, delta2: float, rmax: int):
+    """Smallest k in [1, rmax] with sum_{i >= k} s_i^2 <= delta2 (s descending).
+    Returns (k, cap_hit) where cap_hit says r_max cut more than delta2 allows."""
+    s2 = np.asarray(s, dtype=np.float64) ** 2
+    tail = np.concatenate([np.cumsum(s2[::-1])[::-1], [0.0]])  # tail[k] = sum_{i>=k}
+    k = len(s2)
+    for j in range(1, len(s2) + 1):
+        if tail[j] <= delta2:
+            k = j
+            break
+    k = max(1, k)
+    cap_hit = k > rmax
+    return min(k, rmax), cap_hit
+
+
+def _svd(M):
+    return np.linalg.svd(M, full_matrices=False)
+
+
+def tt_ranks(cores):
+    return [c.shape[0] for c in cores] + [cores[-1].shape[-1]]
+
+
+# ------------------------------------------------------------------ TT basics
+
+
+def tt_svd(T: np.ndarray, eps: float, rmax: int = 1 << 30):
+    """TT-SVD of a dense tensor (Sec. 3 and App. D): sequential truncated SVDs
+    of the unfoldings, left to right, with per-bond threshold eps||T||/sqrt(L-1)."""
+    dims = T.shape
+    L = len(dims)
+    delta2 = (eps * np.linalg.norm(T)) ** 2 / max(L - 1, 1)
+    cores = []
+    r = 1
+    M = np.asarray(T).reshape(r * dims[0], -1)
+    for k in range(L - 1):
+        U, s, Vh = _svd(M)
+        kk, _ = truncation_rank(s, delta2, rmax)
+        cores.append(U[:, :kk].reshape(r, dims[k], kk))
+        M = (s[:kk, None] * Vh[:kk]).reshape(kk * dims[k + 1], -1)
+        r = kk
+    cores.append(M.reshape(r, dims[-1], 1))
+    return cores
+
+
+def tt_full(cores) -> np.ndarray:
+    """Dense tensor of a TT (eq. (tt_format))."""
+    out = cores[0]
+    for c in cores[1:]:
+        out = np.tensordot(out, c, axes=([out.ndim - 1], [0]))
+    return out.reshape(out.shape[1:-1])
+
+
+def tt_dot(a, b) -> complex:
+    """<a, b> = sum conj(a) b by a left-to-right transfer-matrix sweep."""
+    E = np.ones((1, 1), dtype=np.complex128)
+    for A, B in zip(a, b):
+        # E'[p, q] = sum_{r, s, i} conj(A[r, i, p]) E[r, s] B[s, i, q]
+        E = np.einsum("rip,rs,siq->pq", A.conj(), E, B)
+    return complex(E[0, 0])
+
+
+def left_orthogonalize(cores):
+    """QR sweep left to right (Sec. 3, rounding: orthogonalisation). Returns the
+    new cores (0..L-2 left-orthonormal) and the norm (= ||last core||_F)."""
+    cores = [c.astype(np.complex128, copy=True) for c in cores]
+    for k in range(len(cores) - 1):
+        r0, d, r1 = cores[k].shape
+        Q, R = np.linalg.qr(cores[k].reshape(r0 * d, r1))
+        cores[k] = Q.reshape(r0, d, Q.shape[1])
+        cores[k + 1] = np.tensordot(R, cores[k + 1], axes=([1], [0]))
+    return cores, float(np.linalg.norm(cores[-1]))
+
+
+def tt_norm(cores) -> float:
+    """||x||_F via orthogonalisation (no cancellation for small differences)."""
+    return left_orthogonalize(cores)[1]
+
+
+def tt_round(cores, eps: float, rmax: int, assume_left_orth: bool = False):
+    """TT rounding (Sec. 3, eq. (rounding_condition_tt)): left-to-right QR
+    orthogonalisation, then a right-to-left sweep of truncated SVDs.
+    Result is right-orthogonal (cores 1..L-1 have orthonormal rows).
+    Returns (cores, cap_hit)."""
+    if assume_left_orth:
+        cores = [c.copy() for c in cores]
+        nrm = float(np.linalg.norm(cores[-1]))
+    else:
+        cores, nrm = left_orthogonalize(cores)
+    L = len(cores)
+    delta2 = (eps * nrm) ** 2 / max(L - 1, 1)
+    cap = False
+    for k in range(L - 1, 0, -1):
+        r0, d, r1 = cores[k].shape
+        U, s, Vh = _svd(cores[k].reshape(r0, d * r1))
+        kk, hit = truncation_rank(s, delta2, rmax)
+        cap |= hit
+        cores[k] = Vh[:kk].reshape(kk, d, r1)
+        cores[k - 1] = np.tensordot(cores[k - 1], U[:, :kk] * s[:kk], axes=([2], [0]))
+    return cores, cap
+
+
+def tt_add(a, b, alpha=1.0, beta=1.0):
+    """alpha a + beta b as a TT of rank r(a) + r(b) (Table 2, "x + y")."""
+    L = len(a)
+    out = []
+    for k in range(L):
+        A, B = a[k], b[k]
+        if k == 0:
+            out.append(np.concatenate([alpha * A, beta * B], axis=2))
+        elif k == L - 1:
+            out.append(np.concatenate([A, B], axis=0))
+        else:
+            ra0, d, ra1 = A.shape
+            rb0, _, rb1 = B.shape
+            C = np.zeros((ra0 + rb0, d, ra1 + rb1), dtype=np.complex128)
+            C[:ra0, :, :ra1] = A
+            C[ra0:, :, ra1:] = B
+            out.append(C)
+    return out
+
+
+def tt_right_orthogonalize(cores):
+    """LQ sweep right to left: cores 1..L-1 get orthonormal rows."""
+    cores = [c.astype(np.complex128, copy=True) for c in cores]
+    for k in range(len(cores) - 1, 0, -1):
+        r0, d, r1 = cores[k].shape
+        Q, R = np.linalg.qr(cores[k].reshape(r0, d * r1).conj().T)
+        cores[k] = Q.conj().T.reshape(Q.shape[1], d, r1)
+        cores[k - 1] = np.tensordot(cores[k - 1], R.conj().T, axes=([2], [0]))
+    return cores
+
+
+# ------------------------------------------------------------------ operators
+
+
+def raise_tt(cores):
+    """Raise a TT to a diagonal TTO, G(a, i, j, b) = C(a, i, b) delta_ij (eq. (tt_to_tto))."""
+    out = []
+    for C in cores:
+        r0, d, r1 = C.shape
+        G = np.zeros((r0, d, d, r1), dtype=np.complex128)
+        for i in range(d):
+            G[:, i, i, :] = C[:, i, :]
+        out.append(G)
+    return out
+
+
+def tto_full(op) -> np.ndarray:
+    """Dense matrix (prod d_out) x (prod d_in) of a TTO (eq. (tto_format))."""
+    out = op[0]                                   # (1, o, i, a)
+    for W in op[1:]:
+        out = np.tensordot(out, W, axes=([out.ndim - 1], [0]))
+    out = out.reshape(out.shape[1:-1])            # (o1, i1, o2, i2, ...)
+    L = len(op)
+    perm = [2 * k for k in range(L)] + [2 * k + 1 for k in range(L)]
+    out = out.transpose(perm)
+    do = int(np.prod([W.shape[1] for W in op]))
+    di = int(np.prod([W.shape[2] for W in op]))
+    return out.reshape(do, di)
+
+
+def tto_adjoint(op):
+    """A^H: swap the in/out legs of every core and conjugate."""
+    return [W.transpose(0, 2, 1, 3).conj() for W in op]
+
+
+def tto_apply_exact(op, x):
+    """Exact matrix-vector product (Table 2, "contract"): cores
+    Y_k[(a, s), i, (b, s')] = sum_j W_k[a, i, j, b] X_k[s, j, s'], rank r(A) r(x)."""
+    out = []
+    for W, X in zip(op, x):
+        a0, do, di, a1 = W.shape
+        s0, _, s1 = X.shape
+        Y = np.einsum("aijb,sjt->asibt", W, X)
+        out.append(Y.reshape(a0 * s0, do, a1 * s1))
+    return out
+
+
+# ---------------------------------------------------------------- random sketches
+
+PHILOX_M0, PHILOX_M1 = 0xD2511F53, 0xCD9E8D57
+PHILOX_W0, PHILOX_W1 = 0x9E3779B9, 0xBB67AE85
+SKETCH_TAG = 0x5EC7C0DE
+MASK32 = 0xFFFFFFFF
+
+
+def philox4x32(ctr, key, rounds: int = 10):
+    """Philox-4x32-10 counter-based generator (Salmon, Moraes, Dror, Shaw,
+    "Parallel random numbers: as easy as 1, 2, 3", SC'11), vectorised over
+    uint64 arrays holding 32-bit words. ctr: 4 arrays, key: 2 ints."""
+    c0, c1, c2, c3 = (np.asarray(c, dtype=np.uint64) & MASK32 for c in ctr)
+    k0 = np.uint64(key[0] & MASK32)
+    k1 = np.uint64(key[1] & MASK32)
+    for _ in range(rounds):
+        p0 = np.uint64(PHILOX_M0) * c0
+        p1 = np.uint64(PHILOX_M1) * c2
+        hi0, lo0 = p0 >> np.uint64(32), p0 & np.uint64(MASK32)
+        hi1, lo1 = p1 >> np.uint64(32), p1 & np.uint64(MASK32)
+        c0, c1, c2, c3 = hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0
+        k0 = (k0 + np.uint64(PHILOX_W0)) & np.uint64(MASK32)
+        k1 = (k1 + np.uint64(PHILOX_W1)) & np.uint64(MASK32)
+    return c0, c1, c2, c3
+
+
+def _u32_to_unit(x):
+    """32-bit word -> (int32(x) + 1/2) * 2^-31, exactly representable, in (-1, 1)."""
+    x = np.asarray(x, dtype=np.uint64).astype(np.int64)
+    x = np.where(x >= (1 << 31), x - (1 << 32), x)
+    return (x.astype(np.float64) + 0.5) * 2.0 ** -31
+
+
+def sketch_core(seed: int, apply_id: int, core: int, shape):
+    """Random complex sketch core of the given shape, entries with real and
+    imaginary parts uniform in (-1, 1). Entry e (row-major flat index) of core
+    `core` in product number `apply_id` uses Philox counter
+    (e >> 1, core, apply_id, SKETCH_TAG) and key (seed low, seed high); even e
+    takes words (0, 1), odd e words (2, 3) as (real, imaginary)."""
+    size = int(np.prod(shape))
+    e = np.arange(size, dtype=np.uint64)
+    w = philox4x32((e >> np.uint64(1), np.full(size, core), np.full(size, apply_id),
+                    np.full(size, SKETCH_TAG)), (seed & MASK32, (seed >> 32) & MASK32))
+    odd = (e & np.uint64(1)).astype(bool)
+    re = np.where(odd, w[2], w[0])
+    im = np.where(odd, w[3], w[1])
+    return (_u32_to_unit(re) + 1j * _u32_to_unit(im)).reshape(shape)
+
+
+def sketch_ranks(op, x, ell: int):
+    """Sketch bond sizes: min(ell, exact product rank, left and right grid dims)."""
+    L = len(op)
+    dims = [W.shape[1] for W in op]
+    out = []
+    for k in range(L - 1):
+        left = int(np.prod(dims[:k + 1]))
+        right = int(np.prod(dims[k + 1:]))
+        out.append(min(ell, op[k].shape[3] * x[k].shape[2], left, right))
+    return out
+
+
+def tto_apply_sketched(op, x, ell: int, seed: int, apply_id: int):
+    """Compressed matrix-vector product by successive randomized compression:
+      1. right-to-left: sketch the exact product's right parts with a random TT
+         Omega of ranks ell_k,  Psi_k[a, s, p] = sum W_k[a, o, i, b] X_k[s, i, t]
+         Psi_{k+1}[b, t, q] Omega_k[p, o, q];
+      2. left-to-right: with carry C[r, a, s], form T[r, o, b, t] = sum C W_k X_k,
+         Z = T Psi_{k+1} ((r o) x ell_k), Q = orth(Z) by Householder QR, keep Q as
+         output core k and carry Q^H T.
+    No truncation by tolerance happens here (the rounding that follows does it).
+    Output cores 0..L-2 are left-orthonormal."""
+    L = len(op)
+    ells = sketch_ranks(op, x, ell)
+    psi = [None] * (L + 1)
+    psi[L] = np.ones((1, 1, 1), dtype=np.complex128)
+    for k in range(L - 1, 0, -1):
+        W, X = op[k], x[k]
+        Om = sketch_core(seed, apply_id, k, (ells[k - 1], W.shape[1], 1 if k == L - 1 else ells[k]))
+        # XP[s, i, b, q] = sum_t X[s, i, t] Psi[b, t, q]
+        XP = np.einsum("sit,btq->sibq", X, psi[k + 1])
+        # U[s, i, b, p] = sum_q XP[s, i, b, q] Om[p, o, q]  (o kept)  -> [s, i, b, o, p]
+        U = np.einsum("sibq,poq->sibop", XP, Om)
+        psi[k] = np.einsum("aoib,sibop->asp", W, U)
+    C = np.ones((1, 1, 1), dtype=np.complex128)
+    out = []
+    for k in range(L):
+        W, X = op[k], x[k]
+        CX = np.einsum("ras,sjt->rajt", C, X)
+        T = np.einsum("rajt,aojb->robt", CX, W)
+        r, do, a1, s1 = T.shape
+        if k == L - 1:
+            out.append(T.reshape(r, do, a1 * s1))
+            break
+        Z = np.einsum("robt,btp->rop", T, psi[k + 1]).reshape(r * do, -1)
+        Q, _ = np.linalg.qr(Z)
+        out.append(Q.reshape(r, do, Q.shape[1]))
+        C = np.einsum("mr,rbt->mbt", Q.conj().T, T.reshape(r * do, a1, s1))
+    return out
+
+
+def tto_sandwich_mean(op, x):
+    """Mean over the grid of (A x) without forming A x: the binary cores are
+    contracted with the averaging vector (1/2, 1/2). Returns the Voigt vector
+    mean_x sum_J A[I, J](x) x[J](x) (Sec. 2, the C_eff average)."""
+    W0, X0 = op[0], x[0]                         # (1, 6, 6, a1), (1, 6, s1)
+    V = np.einsum("ijb,jt->ibt", W0[0], X0[0])   # (6, a1, s1)
+    for W, X in zip(op[1:], x[1:]):
+        # V'[I, b, t] = sum_{a, s, i, j} V[I, a, s] W[a, i, j, b] X[s, j, t] / 2
+        V = 0.5 * np.einsum("Ias,aijb,sjt->Ibt", V, W, X)
+    return V[:, 0, 0]
+
+
+# ------------------------------------------------------------------ SFFT MPO
+
+
+def bit_reverse(k: int, n: int) -> int:
+    return int(format(k, f"0{n}b")[::-1], 2)
+
+
+def sfft_dense(n: int) -> np.ndarray:
+    """S = P_rev F+ on one axis: S[k', x] = N^-1/2 exp(2 pi i rev(k') x / N)."""
+    N = 1 << n
+    rev = np.array([bit_reverse(k, n) for k in range(N)])
+    x = np.arange(N)
+    return np.exp(2j * np.pi * np.outer(rev, x) / N) / math.sqrt(N)
+
+
+def matrix_to_mpo(M: np.ndarray, n: int, eps: float, rmax: int = 1 << 30):
+    """TT-SVD of a 2^n x 2^n matrix with core b carrying (out bit b, in bit b),
+    MSB first. Returns cores (f, 2, 2, f')."""
+    T = M.reshape((2,) * n + (2,) * n)
+    perm = [v for b in range(n) for v in (b, n + b)]
+    T = T.transpose(perm).reshape((4,) * n)
+    cores = tt_svd(T, eps, rmax)
+    return [c.reshape(c.shape[0], 2, 2, c.shape[2]) for c in cores]
+
+
+def sfft_axis_mpo(n: int, eps: float = 1e-14):
+    """The SFFT (reduced QFT) of one axis as an MPO (Sec. 4.1-4.2)."""
+    return matrix_to_mpo(sfft_dense(n), n, eps)
+
+
+def sfft_operator(n: int, eps: float = 1e-14, adjoint: bool = False):
+    """3D SFFT TTO on the controlled QTT: identity Voigt core, then the axis
+    MPOs of x1, x2, x3 joined by rank-1 bonds (Sec. 4.3). adjoint -> S^H = S^-1."""
+    ax = sfft_axis_mpo(n, eps)
+    op = [np.eye(6, dtype=np.complex128).reshape(1, 6, 6, 1)] + ax + ax + ax
+    return tto_adjoint(op) if adjoint else op
+
+
+# ------------------------------------------------------------------ Green operator
+
+
+def axis_frequencies_bitrev(n: int) -> np.ndarray:
+    """xi(rev k') for k' = 0..N-1 with the paper's representatives
+    {-N/2+1, ..., N/2} (App. A)."""
+    N = 1 << n
+    k = np.array([bit_reverse(kp, n) for kp in range(N)])
+    return np.where(k <= N // 2, k, k - N).astype(np.float64)
+
+
+def gamma_field_sfft(n: int, lam0: float, mu0: float) -> np.ndarray:
+    """Dense Voigt Green field in the SFFT momentum convention (Sec. 4.3):
+    G[I, J, k'1, k'2, k'3] = conj(Gamma_V[I, J](xi(rev k'1), xi(rev k'2), xi(rev k'3)))."""
+    f = axis_frequencies_bitrev(n)
+    N = 1 << n
+    out = np.empty((6, 6, N, N, N))
+    X2, X3 = np.meshgrid(f, f, indexing="ij")
+    for a in range(N):
+        xi = np.stack([np.full_like(X2, f[a]), X2, X3], axis=-1)
+        out[:, :, a] = np.moveaxis(dense.green_voigt_direct(xi, lam0, mu0), (-2, -1), (0, 1))
+    return out   # real: conj is the identity for the Direct scheme
+
+
+def controlled_field_to_tto(F: np.ndarray, n: int, eps: float, rmax: int):
+    """(6, 6, N, N, N) Voigt-matrix field -> raised TTO: TT-SVD of the
+    (36, 2, ..., 2) tensor, Voigt core reshaped to (1, 6, 6, a1), binary cores raised."""
+    T = F.reshape((36,) + (2,) * (3 * n))
+    cores = tt_svd(T.astype(np.complex128), eps, rmax)
+    c0 = cores[0].reshape(1, 6, 6, cores[0].shape[2])
+    return [c0] + raise_tt(cores[1:])
+
+
+def gamma_qtt(n: int, lam0: float, mu0: float, eps: float, rmax: int = 1 << 30):
+    """Gamma_hat^0 as a raised TTO in the SFFT momentum convention."""
+    return controlled_field_to_tto(gamma_field_sfft(n, lam0, mu0), n, eps, rmax)
+
+
+# ------------------------------------------------------------------ stiffness operator
+
+
+def stiffness_qtt(phase: np.ndarray, n: int, E, nu, lame0, eps: float, rmax: int = 1 << 30):
+    """(C(x) - C0) as a raised TTO (Sec. 4.3): the Voigt-matrix field
+    sum_p (C_p - C0) chi_p(x) compressed by TT-SVD, Voigt core (1, 6, 6, a1)."""
+    N = 1 << n
+    ph = np.broadcast_to(phase, (N, N, N))
+    C0 = dense.stiffness_voigt(*lame0)
+    F = np.zeros((6, 6, N, N, N))
+    for p, (e, v) in enumerate(zip(E, nu)):
+        dC = dense.stiffness_voigt(*dense.lame(e, v)) - C0
+        F += dC[:, :, None, None, None] * (ph == p)[None, None]
+    return controlled_field_to_tto(F, n, eps, rmax)
+
+
+def e_tt(n: int, E_voigt):
+    """Rank-1 mean strain TT (Sec. 4.3): Voigt core E scaled by sqrt(2)^{3n},
+    binary cores (1, 1)/sqrt(2) (right-orthonormal)."""
+    c0 = (np.asarray(E_voigt, dtype=np.complex128) * math.sqrt(2.0) ** (3 * n)).reshape(1, 6, 1)
+    b = np.full((1, 2, 1), 1.0 / math.sqrt(2.0), dtype=np.complex128)
+    return [c0] + [b.copy() for _ in range(3 * n)]
+
+
+def to_voigt_field(cores, n: int) -> np.ndarray:
+    """Dense (6, N, N, N) field of a controlled QTT."""
+    N = 1 << n
+    return tt_full(cores).reshape(6, N, N, N)
+
+
+# ------------------------------------------------------------------ Alg. 2
+
+
+def ls_solve(dC, G, S, Sh, E_voigt, n: int, tol: float, eps: float, rmax: int,
+             max_iter: int = 5000, oversample: int = 16, seed: int = 2412, lame0=None):
+    """Alg. 2 (SFFT-based homogenisation), one unit load:
+        tau_m   = round((C - C0) eps_m)
+        tauh_m  = round(S tau_m)
+        epsh_m  = round(Gamma_hat tauh_m)
+        eps_m+1 = round(E - S^-1 epsh_m)
+    each product by randomized sketching with sketch rank rmax + oversample
+    (product number 4 (m - 1) + j for the j-th product of iteration m), each
+    rounding at (eps, rmax); stop when ||eps_m+1 - eps_m||_F / ||E||_F < tol.
+    sigma_bar = C0 E + mean((C - C0) eps_final) (Sec. 2, C_eff paragraph).
+    Returns dict(eps, sigma_bar, iters, history, max_rank, cap_hit)."""
+    Ett = e_tt(n, E_voigt)
+    normE = tt_norm(Ett)
+    ell = rmax + oversample
+    x = Ett
+    hist = []
+    cap = False
+    maxr = 1
+    it = 0
+    for it in range(1, max_iter + 1):
+        t0 = 4 * (it - 1)
+        tau, h1 = tt_round(tto_apply_sketched(dC, x, ell, seed, t0), eps, rmax, assume_left_orth=True)
+        tauh, h2 = tt_round(tto_apply_sketched(S, tau, ell, seed, t0 + 1), eps, rmax,
+                            assume_left_orth=True)
+        epsh, h3 = tt_round(tto_apply_sketched(G, tauh, ell, seed, t0 + 2), eps, rmax,
+                            assume_left_orth=True)
+        y = tto_apply_sketched(Sh, epsh, ell, seed, t0 + 3)
+        xn, h4 = tt_round(tt_add(Ett, y, 1.0, -1.0), eps, rmax)
+        cap |= h1 | h2 | h3 | h4
+        maxr = max(maxr, *tt_ranks(tau), *tt_ranks(tauh), *tt_ranks(epsh), *tt_ranks(xn))
+        rel = tt_norm(tt_add(xn, x, 1.0, -1.0)) / normE
+        hist.append(rel)
+        x = xn
+        if rel < tol:
+            break
+    sig = tto_sandwich_mean(dC, x)
+    if lame0 is not None:
+        sig = sig + dense.stiffness_voigt(*lame0) @ np.asarray(E_voigt, dtype=np.float64)
+    return dict(eps=x, sigma_bar=sig, iters=it, history=hist, max_rank=maxr, cap_hit=cap)

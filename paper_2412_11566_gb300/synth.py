@@ -1,0 +1,194 @@
+"""Seeded synthetic microstructures (voxel phase fields) and material tables.
+
+This module is shared by the CUDA path, the oracle and the tests. It holds no
+arithmetic of the homogenisation method: it only draws geometry (which voxel
+belongs to which phase) and lists the per-phase (E, nu) pairs of each workload.
+
+Phase fields are uint8 arrays of shape (N1, N2, N3) in C order (x3 fastest);
+0 is the matrix, 1 the inclusion phase. An axis of extent 1 is a broadcast
+axis (the field is constant along it). Voxel (i, j, k) is sampled at its centre
+((i+1/2)/N, (j+1/2)/N, (k+1/2)/N) of the unit cell, with periodic distances.
+
+The shapes follow the paper's geometry families (spheres/boxes, Sec. 5.1;
+fibres and laminates, App. F), at the sizes of the benchmark workloads.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+
+@dataclasses.dataclass(frozen=True)
+class Workload:
+    """A named synthetic workload: geometry, materials and solver settings."""
+    name: str
+    n: int                      # bits per axis, N = 2**n
+    phase: np.ndarray           # uint8 (N1, N2, N3); extent 1 = broadcast axis
+    E: tuple                    # Young's modulus per phase
+    nu: tuple                   # Poisson ratio per phase
+    tol: float                  # stop-test tolerance delta_tol
+    eps_tt: float               # TT rounding accuracy
+    rmax: int                   # TT rank cap
+    loads: tuple = (0, 1, 2, 3, 4, 5)  # Voigt unit load cases to solve
+
+
+def _centres(N: int) -> np.ndarray:
+    return (np.arange(N, dtype=np.float64) + 0.5) / N
+
+
+def _periodic(d: np.ndarray) -> np.ndarray:
+    return d - np.round(d)
+
+
+def sphere_field(n: int, centres, radii) -> np.ndarray:
+    """Union of balls (periodic) on a 2^n grid; centres/radii in cell units."""
+    N = 1 << n
+    c = _centres(N)
+    out = np.zeros((N, N, N), dtype=np.uint8)
+    for (cx, cy, cz), r in zip(centres, radii):
+        dx = _periodic(c - cx) ** 2
+        dy = _periodic(c - cy) ** 2
+        dz = _periodic(c - cz) ** 2
+        inside = (dx[:, None, None] + dy[None, :, None] + dz[None, None, :]) <= r * r
+        out[inside] = 1
+    return out
+
+
+def centred_sphere(n: int, radius: float) -> np.ndarray:
+    return sphere_field(n, [(0.5, 0.5, 0.5)], [radius])
+
+
+def random_spheres(n: int, count: int, rmin: float, rmax: float, seed: int,
+                   max_tries: int = 100000):
+    """Non-overlapping spheres: centres U[0,1)^3, radii U(rmin, rmax).
+
+    Rejection sampling keeps every pair at periodic distance >= r_i + r_j + one
+    voxel. Returns (phase, centres, radii)."""
+    N = 1 << n
+    rng = np.random.default_rng(seed)
+    centres, radii = [], []
+    tries = 0
+    while len(centres) < count:
+        tries += 1
+        if tries > max_tries:
+            raise RuntimeError("sphere packing failed")
+        c = rng.random(3)
+        r = rng.uniform(rmin, rmax)
+        ok = True
+        for c2, r2 in zip(centres, radii):
+            d = np.linalg.norm(_periodic(c - np.asarray(c2)))
+            if d < r + r2 + 1.0 / N:
+                ok = False
+                break
+        if ok:
+            centres.append(tuple(c))
+            radii.append(r)
+    return sphere_field(n, centres, radii), centres, radii
+
+
+def random_fibres(n: int, seed: int, max_tries: int = 1000):
+    """Aligned circular fibres along x3 (broadcast axis: shape (N, N, 1)).
+
+    count ~ U{4..8}, volume fraction phi ~ U(0.3, 0.5), equal radius
+    r = sqrt(phi / (count * pi)); centres U[0,1)^2 with periodic distance
+    >= 2r + one voxel. If packing fails after max_tries the count is reduced.
+    Contrast ~ U(5, 50). Returns (phase, info dict)."""
+    N = 1 << n
+    rng = np.random.default_rng(seed)
+    count = int(rng.integers(4, 9))
+    phi = float(rng.uniform(0.3, 0.5))
+    contrast = float(rng.uniform(5.0, 50.0))
+    while True:
+        r = math.sqrt(phi / (count * math.pi))
+        centres = []
+        tries = 0
+        while len(centres) < count and tries < max_tries:
+            tries += 1
+            c = rng.random(2)
+            if all(np.linalg.norm(_periodic(c - np.asarray(c2))) >= 2 * r + 1.0 / N for c2 in centres):
+                centres.append(tuple(c))
+        if len(centres) == count:
+            break
+        count -= 1
+        if count == 0:
+            raise RuntimeError("fibre packing failed")
+    c = _centres(N)
+    out = np.zeros((N, N, 1), dtype=np.uint8)
+    for cx, cy in centres:
+        d2 = _periodic(c - cx)[:, None] ** 2 + _periodic(c - cy)[None, :] ** 2
+        out[d2 <= r * r, 0] = 1
+    return out, dict(count=count, phi=phi, radius=r, contrast=contrast, centres=centres)
+
+
+def laminate(n: int, layers: int = 2, stiff_first: bool = True) -> np.ndarray:
+    """Layers normal to x3 on voxel faces; layer j is stiff when j is even
+    (stiff_first) and matrix otherwise. Shape (1, 1, N): broadcast x1, x2."""
+    N = 1 << n
+    idx = (np.arange(N) * layers) // N
+    stiff = (idx % 2 == 0) if stiff_first else (idx % 2 == 1)
+    return stiff.astype(np.uint8).reshape(1, 1, N)
+
+
+def laminate_with_fibres(n: int) -> np.ndarray:
+    """8 layers normal to x3 (stiff in layers 0, 2, 4, 6) plus a 4x4 lattice of
+    stiff fibres along x1 centred at ((j+1/2)/4, (k+1/2)/4 + 1/16) in (x2, x3),
+    radius 0.06 L. Shape (1, N, N): broadcast x1."""
+    N = 1 << n
+    c = _centres(N)
+    lay = ((np.floor(c * 8).astype(np.int64) % 2) == 0)
+    out = np.broadcast_to(lay[None, :], (N, N)).copy()
+    for j in range(4):
+        for k in range(4):
+            cy, cz = (j + 0.5) / 4, (k + 0.5) / 4 + 1.0 / 16
+            d2 = _periodic(c - cy)[:, None] ** 2 + _periodic(c - cz)[None, :] ** 2
+            out |= d2 <= 0.06 ** 2
+    return out.astype(np.uint8).reshape(1, N, N)
+
+
+def broadcast_dense(phase: np.ndarray, n: int) -> np.ndarray:
+    """Expand broadcast axes of a phase field to the full (N, N, N) grid."""
+    N = 1 << n
+    return np.ascontiguousarray(np.broadcast_to(phase, (N, N, N)))
+
+
+# ---------------------------------------------------------------- workloads
+
+def sphere32_fp64() -> Workload:
+    """32^3 grid, one centred sphere r = 0.25 L; matrix E=1, nu=0.3; sphere
+    E=10, nu=0.3; load e11; tol 1e-6; eps_tt 1e-8; r_max 64."""
+    return Workload("sphere32", 5, centred_sphere(5, 0.25), (1.0, 10.0), (0.3, 0.3),
+                    1e-6, 1e-8, 64, loads=(0,))
+
+
+def spheres256(n: int = 8, seed: int = 2412) -> Workload:
+    """8 non-overlapping spheres, radius U(0.05, 0.12) L, seeded centres;
+    matrix E=1, nu=0.3; spheres E=20, nu=0.25; 6 loads; tol 1e-4; eps_tt 1e-6;
+    r_max 128."""
+    ph, _, _ = random_spheres(n, 8, 0.05, 0.12, seed)
+    return Workload(f"spheres{1 << n}", n, ph, (1.0, 20.0), (0.3, 0.25), 1e-4, 1e-6, 128)
+
+
+def fibre_batch(items: int = 64, base_seed: int = 2413):
+    """Batch of aligned-fibre microstructures, n ~ U{6,7,8,9} per item."""
+    out = []
+    for i in range(items):
+        rng = np.random.default_rng(base_seed + i)
+        n = int(rng.integers(6, 10))
+        ph, info = random_fibres(n, base_seed + i)
+        out.append(Workload(f"fibres{i}", n, ph, (1.0, info["contrast"]), (0.3, 0.25),
+                            1e-4, 1e-6, 128))
+    return out
+
+
+def sphere128_grad() -> Workload:
+    """128^3 centred sphere at volume fraction 0.15 (r = 0.3296 L), contrast 10."""
+    r = (3 * 0.15 / (4 * math.pi)) ** (1.0 / 3.0)
+    return Workload("sphere128", 7, centred_sphere(7, r), (1.0, 10.0), (0.3, 0.25),
+                    1e-4, 1e-6, 128)
+
+
+def laminate_fibres2048(n: int = 11) -> Workload:
+    return Workload(f"lamfib{1 << n}", n, laminate_with_fibres(n), (1.0, 100.0), (0.3, 0.3),
+                    1e-4, 1e-6, 256)

@@ -1,0 +1,276 @@
+"""Pins of Oracle B (the QTT/SFFT scheme, Alg. 2) against what the paper and
+the mathematics fix: exact TT round trips, the rounding error bound, the
+raised-TTO/Hadamard identity (App. C), the product rank (Table 2), the SFFT as
+a bit-reversed unitary DFT and its printed MPO rank, the momentum-space
+convention (the QTT pipeline equals the dense FFT pipeline), the Philox
+known-answer vectors, and cross-checks of the two oracles."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import dense, qtt as oq
+from paper_2412_11566_gb300 import synth
+from tests._helpers import random_tt
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def test_tt_svd_roundtrip_exact():
+    rng = np.random.default_rng(0)
+    T = rng.standard_normal((6, 2, 2, 2, 2, 2)) + 1j * rng.standard_normal((6, 2, 2, 2, 2, 2))
+    cores = oq.tt_svd(T, 0.0)
+    assert rel(oq.tt_full(cores), T) < 1e-14
+    # full ranks of a random tensor
+    assert oq.tt_ranks(cores) == [1, 6, 12, 8, 4, 2, 1]
+
+
+@pytest.mark.parametrize("eps", [1e-1, 1e-3, 1e-6])
+def test_rounding_error_bound(eps):
+    rng = np.random.default_rng(1)
+    x = random_tt(rng, [6, 2, 2, 2, 2, 2, 2], [1, 5, 8, 9, 8, 6, 3, 1])
+    full = oq.tt_full(x)
+    y, cap = oq.tt_round(x, eps, 1000)
+    assert not cap
+    assert rel(oq.tt_full(y), full) <= eps * (1 + 1e-10)
+    # result is right-orthogonal
+    for c in y[1:]:
+        M = c.reshape(c.shape[0], -1)
+        assert np.allclose(M @ M.conj().T, np.eye(M.shape[0]), atol=1e-12)
+    # rounding of an exact low-rank TT with redundant rank is lossless
+    z, _ = oq.tt_round(oq.tt_add(x, x, 1.0, 1.0), 1e-12, 1000)
+    assert rel(oq.tt_full(z), 2 * full) < 1e-12
+    assert oq.tt_ranks(z) == oq.tt_ranks(oq.tt_round(x, 1e-12, 1000)[0])
+
+
+def test_rank_cap_flag():
+    rng = np.random.default_rng(2)
+    x = random_tt(rng, [6, 2, 2, 2, 2], [1, 6, 10, 4, 2, 1])
+    y, cap = oq.tt_round(x, 1e-12, 3)
+    assert cap and max(oq.tt_ranks(y)) == 3
+
+
+def test_raised_tto_is_hadamard():
+    """App. C: contracting the raised TTO of a with b gives a (.) b."""
+    rng = np.random.default_rng(3)
+    dims = [2, 2, 2, 2, 2]
+    a = random_tt(rng, dims, [1, 2, 3, 3, 2, 1])
+    b = random_tt(rng, dims, [1, 3, 2, 4, 2, 1])
+    c = oq.tto_apply_exact(oq.raise_tt(a), b)
+    assert rel(oq.tt_full(c), oq.tt_full(a) * oq.tt_full(b)) < 1e-14
+    # Table 2: exact product rank r(A) r(x)
+    assert oq.tt_ranks(c) == [ra * rb for ra, rb in zip(oq.tt_ranks(a), oq.tt_ranks(b))]
+
+
+def test_exact_product_equals_dense_matvec():
+    rng = np.random.default_rng(4)
+    op = [rng.standard_normal(s) + 1j * rng.standard_normal(s)
+          for s in [(1, 3, 2, 2), (2, 2, 3, 3), (3, 2, 2, 1)]]
+    x = random_tt(rng, [2, 3, 2], [1, 2, 2, 1])
+    y = oq.tto_apply_exact(op, x)
+    assert rel(oq.tt_full(y).reshape(-1), oq.tto_full(op) @ oq.tt_full(x).reshape(-1)) < 1e-14
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5])
+def test_sfft_is_bit_reversed_unitary_dft(n):
+    """S = P_rev F+ (Sec. 4.1): bit-reversed output of the +i DFT, unitary."""
+    N = 1 << n
+    S = oq.sfft_dense(n)
+    rng = np.random.default_rng(n)
+    x = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    rev = [oq.bit_reverse(k, n) for k in range(N)]
+    assert np.allclose(S @ x, (np.fft.ifft(x) * np.sqrt(N))[rev], atol=1e-12)
+    assert np.allclose(S.conj().T @ S, np.eye(N), atol=1e-12)
+    mpo = oq.sfft_axis_mpo(n, 1e-14)
+    assert np.allclose(oq.tto_full(mpo), S, atol=1e-12)
+
+
+def test_sfft_mpo_rank_printed_value():
+    """The (I)SFFT TTO rank converges to 10 for n >= 8 at accuracy 1e-10."""
+    g = json.load(open(os.path.join(GOLD, "paper_values.json")))["sfft_mpo_rank"]
+    for n in (8, 9):
+        mpo = oq.sfft_axis_mpo(n, g["delta_acc"])
+        assert max(c.shape[0] for c in mpo) == g["value"]
+    # the full QFT (with the reordering) is not low rank: the reduced form matters
+    n = 8
+    N = 1 << n
+    full_dft = np.exp(2j * np.pi * np.outer(np.arange(N), np.arange(N)) / N) / np.sqrt(N)
+    assert max(c.shape[0] for c in oq.matrix_to_mpo(full_dft, n, 1e-10)) > 2 * g["value"]
+
+
+def test_sfft_3d_operator_and_inverse():
+    n = 2
+    N = 1 << n
+    S = oq.tto_full(oq.sfft_operator(n))
+    Sh = oq.tto_full(oq.sfft_operator(n, adjoint=True))
+    assert np.allclose(Sh @ S, np.eye(S.shape[0]), atol=1e-12)
+    rng = np.random.default_rng(7)
+    f = rng.standard_normal((6, N, N, N)) + 1j * rng.standard_normal((6, N, N, N))
+    rev = [oq.bit_reverse(k, n) for k in range(N)]
+    ref = (np.fft.ifftn(f, axes=(1, 2, 3)) * N ** 1.5)[:, rev][:, :, rev][:, :, :, rev]
+    assert np.allclose((S @ f.reshape(-1)).reshape(f.shape), ref, atol=1e-12)
+
+
+@pytest.mark.parametrize("n", [2, 3])
+def test_momentum_convention_matches_dense_pipeline(n):
+    """S^H Gamma_S S equals ifft(Gamma(xi) fft(.)) of the dense scheme: the
+    bit reversal and conjugation of Sec. 4.3 reproduce the FFT scheme's Green
+    operator (with numpy's Nyquist representative)."""
+    N = 1 << n
+    lam0, mu0 = 2.0, 1.0
+    rng = np.random.default_rng(n)
+    tau = rng.standard_normal((6, N, N, N)) + 1j * rng.standard_normal((6, N, N, N))
+    f = dense.frequencies(N)
+    XI = np.stack(np.meshgrid(f, f, f, indexing="ij"), -1)
+    d = np.fft.ifftn(np.einsum("abcIJ,Jabc->Iabc", dense.green_voigt_direct(XI, lam0, mu0),
+                               np.fft.fftn(tau, axes=(1, 2, 3))), axes=(1, 2, 3))
+    S = oq.tto_full(oq.sfft_operator(n))
+    Sh = oq.tto_full(oq.sfft_operator(n, adjoint=True))
+    G = oq.gamma_field_sfft(n, lam0, mu0)
+    v = (S @ tau.reshape(-1)).reshape(tau.shape)
+    w = np.einsum("IJabc,Jabc->Iabc", G, v)
+    q = (Sh @ w.reshape(-1)).reshape(tau.shape)
+    assert np.abs(q - d).max() < 1e-12 * np.abs(d).max()
+    # and the compressed Green TTO reproduces the field
+    Gt = oq.tto_full(oq.gamma_qtt(n, lam0, mu0, 1e-13))
+    assert np.allclose(np.diag(Gt[:N ** 3, :N ** 3]), G[0, 0].reshape(-1), atol=1e-11)
+
+
+def test_gamma_separability():
+    """App. D: Gamma = (1/mu0) Gamma1 - beta0 Gamma2 with Lame-independent parts."""
+    n = 2
+    g_a = oq.gamma_field_sfft(n, 1.0, 1.0)
+    g_b = oq.gamma_field_sfft(n, 3.0, 0.5)
+    # beta0 for each, recover Gamma1, Gamma2 from two parameter sets and predict a third
+    b = lambda l, m: (l + m) / (m * (l + 2 * m))
+    A = np.array([[1 / 1.0, -b(1.0, 1.0)], [1 / 0.5, -b(3.0, 0.5)]])
+    coef = np.linalg.solve(A, np.stack([g_a.reshape(-1), g_b.reshape(-1)]))
+    g_c = oq.gamma_field_sfft(n, 0.7, 2.2)
+    pred = (1 / 2.2) * coef[0] - b(0.7, 2.2) * coef[1]
+    assert np.allclose(pred, g_c.reshape(-1), atol=1e-12)
+
+
+def test_philox_known_answers():
+    kat = json.load(open(os.path.join(GOLD, "philox_kat.json")))["vectors"]
+    for v in kat:
+        ctr = [np.array([int(h, 16)], dtype=np.uint64) for h in v["ctr"]]
+        key = [int(h, 16) for h in v["key"]]
+        out = oq.philox4x32(ctr, key)
+        assert ["%08x" % int(w[0]) for w in out] == v["out"]
+
+
+def test_sketch_core_values():
+    s = oq.sketch_core(2412, 3, 5, (3, 2, 4))
+    assert s.shape == (3, 2, 4)
+    assert np.all(np.abs(s.real) < 1) and np.all(np.abs(s.imag) < 1)
+    # exactly representable values: (int32 + 1/2) 2^-31
+    assert np.all(((s.real * 2 ** 31 - 0.5) % 1) == 0)
+    assert not np.allclose(s, oq.sketch_core(2412, 3, 6, (3, 2, 4)))
+
+
+def test_sketched_product_exact_with_full_sketch():
+    n = 2
+    rng = np.random.default_rng(9)
+    G = oq.gamma_qtt(n, 2.0, 1.0, 1e-13)
+    x = oq.tt_round(random_tt(rng, [6] + [2] * (3 * n), [1, 4, 6, 5, 6, 4, 2, 1]), 1e-14, 100)[0]
+    ref = oq.tto_full(G) @ oq.tt_full(x).reshape(-1)
+    y = oq.tto_apply_sketched(G, x, 10 ** 4, 1, 0)
+    assert rel(oq.tt_full(y).reshape(-1), ref) < 1e-11
+    # output cores 0..L-2 left-orthonormal
+    for c in y[:-1]:
+        M = c.reshape(-1, c.shape[2])
+        assert np.allclose(M.conj().T @ M, np.eye(M.shape[1]), atol=1e-11)
+
+
+def test_e_tt_and_mean():
+    n = 2
+    Ev = np.array([1.0, -2.0, 0.5, 0.0, 3.0, 0.0])
+    E = oq.e_tt(n, Ev)
+    F = oq.to_voigt_field(E, n)
+    assert np.allclose(F, Ev[:, None, None, None] * np.ones((1, 4, 4, 4)))
+    assert np.isclose(oq.tt_norm(E), np.linalg.norm(Ev) * 8)
+    for c in E[1:]:
+        M = c.reshape(c.shape[0], -1)
+        assert np.allclose(M @ M.conj().T, 1)
+    ph = synth.centred_sphere(n, 0.3)
+    dC = oq.stiffness_qtt(ph, n, (1.0, 3.0), (0.3, 0.2), (1.0, 0.7), 1e-13)
+    rng = np.random.default_rng(5)
+    x = random_tt(rng, [6] + [2] * 6, [1, 6, 5, 4, 6, 4, 2, 1])
+    ref = (oq.tto_full(dC) @ oq.tt_full(x).reshape(-1)).reshape(6, -1).mean(axis=1)
+    assert np.allclose(oq.tto_sandwich_mean(dC, x), ref, atol=1e-12)
+
+
+def test_stiffness_qtt_is_the_field():
+    n = 2
+    ph = synth.centred_sphere(n, 0.35)
+    E, nu = (1.0, 5.0), (0.3, 0.25)
+    lam0 = dense.reference_lame(E, nu)
+    dC = oq.stiffness_qtt(ph, n, E, nu, lam0, 1e-13)
+    M = oq.tto_full(dC)
+    C0 = dense.stiffness_voigt(*lam0)
+    ncell = 64
+    for cell in (0, 21, 42):
+        p = ph.reshape(-1)[cell]
+        ref = dense.stiffness_voigt(*dense.lame(E[p], nu[p])) - C0
+        block = M[cell::ncell, cell::ncell]
+        assert np.allclose(block, ref, atol=1e-12)
+    # with the mean reference medium C_A - C0 = -(C_B - C0): Voigt bond rank 1;
+    # any other reference medium gives rank 2
+    assert dC[0].shape[3] == 1
+    assert oq.stiffness_qtt(ph, n, E, nu, (1.0, 0.7), 1e-13)[0].shape[3] == 2
+
+
+@pytest.mark.parametrize("n,load", [(2, 0), (2, 3), (3, 1)])
+def test_qtt_oracle_matches_dense_oracle(n, load):
+    """The two oracles (Alg. 1 and Alg. 2) agree when no truncation bites."""
+    ph = synth.centred_sphere(n, 0.3)
+    E, nu = (1.0, 6.0), (0.3, 0.25)
+    lam0 = dense.reference_lame(E, nu)
+    dC = oq.stiffness_qtt(ph, n, E, nu, lam0, 1e-13)
+    G = oq.gamma_qtt(n, *lam0, 1e-13)
+    S, Sh = oq.sfft_operator(n), oq.sfft_operator(n, adjoint=True)
+    Ev = np.eye(6)[load]
+    r = oq.ls_solve(dC, G, S, Sh, Ev, n, 1e-300, 1e-13, 1000, max_iter=12, lame0=lam0)
+    d = dense.basic_scheme(ph, E, nu, Ev, tol=1e-300, max_iter=12)
+    assert np.allclose(r["history"], d["history"], rtol=1e-7)
+    assert np.abs(r["sigma_bar"] - d["sigma_bar"]).max() < 1e-10
+    assert np.abs(oq.to_voigt_field(r["eps"], n) - d["eps"]).max() < 1e-10
+
+
+def test_laminate_qtt_low_rank_and_exact():
+    """A laminate's strain stays rank-1 per layer pattern: the QTT solve
+    reproduces the closed-form laminate stiffness with small ranks."""
+    from tests.test_oracle_dense import laminate_closed_form
+    n = 3
+    ph1 = synth.laminate(n, 2)
+    E, nu = (9.0, 1.5), (0.3, 0.2)
+    lam0 = dense.reference_lame(E, nu)
+    dC = oq.stiffness_qtt(ph1, n, E, nu, lam0, 1e-12)
+    G = oq.gamma_qtt(n, *lam0, 1e-12)
+    S, Sh = oq.sfft_operator(n), oq.sfft_operator(n, adjoint=True)
+    ref = laminate_closed_form(ph1.reshape(-1), E, nu)
+    for load in (2, 3):
+        r = oq.ls_solve(dC, G, S, Sh, np.eye(6)[load], n, 1e-11, 1e-12, 64, lame0=lam0)
+        assert np.allclose(r["sigma_bar"].real, ref[:, load], atol=1e-8 * np.abs(ref).max())
+        assert r["max_rank"] <= 16
+
+
+def test_pin_catches_missing_bit_reversal(monkeypatch):
+    """Plant a mistake: SFFT without the bit reversal. The DFT pin fails."""
+    monkeypatch.setattr(oq, "bit_reverse", lambda k, n: k)
+    with pytest.raises(AssertionError):
+        test_sfft_is_bit_reversed_unitary_dft.__wrapped__(3) if hasattr(
+            test_sfft_is_bit_reversed_unitary_dft, "__wrapped__") else _sfft_check(3)
+
+
+def _sfft_check(n):
+    N = 1 << n
+    S = oq.sfft_dense(n)
+    x = np.arange(N) + 1j
+    rev = [int(format(k, f"0{n}b")[::-1], 2) for k in range(N)]
+    assert np.allclose(S @ x, (np.fft.ifft(x) * np.sqrt(N))[rev], atol=1e-12)
