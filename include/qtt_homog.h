@@ -1,0 +1,215 @@
+/*
+ * qtt_homog.h -- C ABI of the GB300 (sm_103a) library for SFFT-based
+ * homogenisation: the Moulinec-Suquet basic-scheme Lippmann-Schwinger
+ * iteration on quantised tensor trains (arXiv 2412.11566, Alg. 2), ending in
+ * the 6x6 effective stiffness C_eff.
+ *
+ * Data model (Sec. 3 eq. (tt_format), (tto_format); Sec. 4.3):
+ *   - A tensor train (TT) with L cores; core k has shape (r_{k-1}, d_k, r_k),
+ *     r_0 = r_L = 1, stored row-major (the last index is fastest). Host arrays
+ *     hold complex numbers as interleaved (re, im) doubles; the cores of one TT
+ *     are concatenated in core order.
+ *   - A controlled QTT on a 2^n grid per axis has L = 3n + 1 cores: core 0 is
+ *     the Voigt core (d = 6, order 11, 22, 33, 23, 13, 12; strains with
+ *     engineering shear), then the n bits of x1, of x2, of x3, most significant
+ *     bit first (eq. (binary_discretization)). The field value at voxel
+ *     (i1, i2, i3) is the TT entry at (Voigt, bits(i1), bits(i2), bits(i3)).
+ *   - An operator (TTO) has cores (a_{k-1}, d_out, d_in, a_k). A core flagged
+ *     "diag" is a raised TT core (eq. (tt_to_tto)) stored as (a_{k-1}, d, a_k):
+ *     G(a, i, j, b) = C(a, i, b) delta_ij.
+ *
+ * Ownership: handles are owned by the library until their *_free call. All
+ * device memory of a context comes from the single workspace the caller hands
+ * to qtt_ctx_create (sub-allocated by the library; the caller keeps it alive
+ * until qtt_ctx_destroy). Host arrays are owned by the caller and only read or
+ * written during the call. Calls are ordered on the context's CUDA stream;
+ * every call that returns host values synchronises that stream first.
+ *
+ * Errors: 0 = OK; negative = error (no result): QTT_EINVAL bad argument,
+ * QTT_ENOMEM workspace exhausted, QTT_ECUDA a CUDA error, QTT_ENAN a NaN/Inf
+ * was produced, QTT_ETIMEOUT a device wait ran out. Positive = warning with the
+ * result returned: QTT_WRANKCAP the rank cap dropped more than the tolerance
+ * allows, QTT_WNOCONV the iteration limit was reached. qtt_last_error gives
+ * the message of the last failing call on a context.
+ *
+ * Precision: QTT_FP64 keeps cores in complex128 and runs every step in FP64.
+ * QTT_FP32 keeps cores in complex64 with FP32 contractions and
+ * factorisations; norms, inner products, the Green operator assembly and the
+ * C_eff average stay FP64.
+ */
+#ifndef QTT_HOMOG_H
+#define QTT_HOMOG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QTT_OK 0
+#define QTT_EINVAL (-1)
+#define QTT_ENOMEM (-2)
+#define QTT_ECUDA (-3)
+#define QTT_ENAN (-4)
+#define QTT_ETIMEOUT (-5)
+#define QTT_WRANKCAP 1
+#define QTT_WNOCONV 2
+
+#define QTT_FP64 0
+#define QTT_FP32 1
+
+#define QTT_MAX_CORES 64
+
+typedef struct qtt_ctx* qtt_ctx_t;
+typedef struct qtt_tt* qtt_tt_t;
+typedef struct qtt_op* qtt_op_t;
+
+/* ---------------------------------------------------------------- context */
+
+/* Handles belong to the context that made them: free them before
+ * qtt_ctx_destroy; after it they must not be used or freed. */
+/* Create a context on CUDA device `device`, ordering all work on
+ * `cuda_stream` (a cudaStream_t; NULL = the legacy default stream).
+ * `workspace` is a device buffer of `workspace_bytes` bytes (256-byte
+ * aligned) from which every device allocation of the context is carved.
+ * `seed` keys the counter-based generator of the random sketches.
+ * Returns QTT_EINVAL on a bad precision, device or workspace. */
+int qtt_ctx_create(qtt_ctx_t* out, int device, void* cuda_stream, int precision,
+                   void* workspace, size_t workspace_bytes, uint64_t seed);
+void qtt_ctx_destroy(qtt_ctx_t ctx);
+const char* qtt_last_error(qtt_ctx_t ctx);
+/* Bytes of the workspace currently allocated, and the high-water mark. */
+size_t qtt_ctx_bytes_in_use(qtt_ctx_t ctx);
+size_t qtt_ctx_bytes_peak(qtt_ctx_t ctx);
+/* Number of kernels this context has launched since creation. */
+uint64_t qtt_ctx_launches(qtt_ctx_t ctx);
+/* Kernel-class timing: when on, CUDA events on the context stream bracket
+ * every GEMM, QR and SVD launch. qtt_ctx_profile writes 9 doubles: for class
+ * c in (0 gemm, 1 qr, 2 svd) out[3c] = launches, out[3c+1] = total ms,
+ * out[3c+2] = algorithmic real flops (GEMM: 8 M N K per complex product;
+ * QR: 8 (2 m n^2 - 2 n^3/3); SVD: one Jacobi sweep's count per launch);
+ * reset = 1 clears the counters. */
+int qtt_ctx_set_profiling(qtt_ctx_t ctx, int on);
+int qtt_ctx_profile(qtt_ctx_t ctx, int reset, double* out);
+
+/* ---------------------------------------------------------------- TT handles */
+
+/* Upload a TT: L cores, dims[L], ranks[L+1] (ranks[0] = ranks[L] = 1), host
+ * cores as interleaved complex doubles, concatenated row-major. */
+int qtt_tt_create(qtt_ctx_t ctx, int L, const int* dims, const int* ranks,
+                  const double* cores, qtt_tt_t* out);
+/* TT-SVD of a dense host tensor (Sec. 3; App. D): dims[L] (row-major,
+ * interleaved complex doubles, prod(dims) entries), compressed on the device
+ * with per-bond threshold eps ||T|| / sqrt(L - 1) and rank cap rmax. For
+ * tests and small grids (the dense tensor is copied to the workspace). */
+int qtt_tt_from_dense(qtt_ctx_t ctx, int L, const int* dims, const double* dense, double eps,
+                      int rmax, qtt_tt_t* out);
+/* Shape query: writes *L, dims[L], ranks[L+1] (arrays of QTT_MAX_CORES+1). */
+int qtt_tt_shape(qtt_tt_t tt, int* L, int* dims, int* ranks);
+/* Download the cores (interleaved complex doubles, concatenated). */
+int qtt_tt_export(qtt_ctx_t ctx, qtt_tt_t tt, double* cores);
+void qtt_tt_free(qtt_tt_t tt);
+
+/* Upload an operator: L cores with d_out[L], d_in[L], ranks[L+1] and
+ * diag[L] (1 = raised diagonal core stored (a, d, a'), requires d_out = d_in;
+ * 0 = full core (a, d_out, d_in, a')). */
+int qtt_op_create(qtt_ctx_t ctx, int L, const int* d_out, const int* d_in,
+                  const int* ranks, const int* diag, const double* cores,
+                  qtt_op_t* out);
+int qtt_op_shape(qtt_op_t op, int* L, int* d_out, int* d_in, int* ranks, int* diag);
+int qtt_op_export(qtt_ctx_t ctx, qtt_op_t op, double* cores);
+void qtt_op_free(qtt_op_t op);
+
+/* ---------------------------------------------------------------- operators */
+
+/* (C(x) - C0) as a raised TTO (Sec. 4.3; preprocessing, App. D): the phase
+ * field (host uint8, C order, shape[3] each 1 or 2^n; an extent of 1 is a
+ * broadcast axis) is mapped to the Voigt-matrix field
+ * sum_p (C_p - C0) [phase == p] with isotropic phases (E[p], nu[p]),
+ * p < nphase, and compressed by TT-SVD at eps_tt with rank cap rmax. lame0 =
+ * (lambda0, mu0) of the reference medium, or NULL for the arithmetic mean of
+ * the smallest and largest phase Lame parameters. The handle remembers C0. */
+int qtt_from_phase_field(qtt_ctx_t ctx, const uint8_t* phase, const int shape[3], int n,
+                         int nphase, const double* E, const double* nu,
+                         const double* lame0, double eps_tt, int rmax, qtt_op_t* dC);
+
+/* The SFFT (Sec. 4.1-4.2): S = P_rev F+ per axis, F+[k, x] =
+ * N^-1/2 exp(+2 pi i k x / N), P_rev reversing the n output bits, as a TTO
+ * with an identity Voigt core; adjoint = 1 gives S^H = S^-1. Built on the
+ * device by TT-SVD of the per-axis matrix at accuracy eps. */
+int qtt_sfft_operator(qtt_ctx_t ctx, int n, int adjoint, double eps, qtt_op_t* out);
+
+/* The Green operator Gamma_hat^0 (App. A, eq. (orig_green_eshelby), Direct
+ * scheme k = i q, isotropic C0 = (lambda0, mu0)) in the SFFT momentum
+ * convention (Sec. 4.3: bit-reversed per axis, conjugated), as a raised TTO
+ * compressed by TT-SVD at eps_tt and rank cap rmax. scheme: 0 = Direct. */
+int qtt_gamma_operator(qtt_ctx_t ctx, int n, double lambda0, double mu0, int scheme,
+                       double eps_tt, int rmax, qtt_op_t* out);
+
+/* ---------------------------------------------------------------- TT algebra */
+
+/* y = round(A x): compressed product by randomized sketching with sketch rank
+ * rmax + oversample (sketch entries from the context's Philox-4x32-10 stream
+ * number apply_id), then TT rounding at (eps_tt, rmax) (Sec. 3, Table 2).
+ * The result is right-orthogonal. */
+int qtt_op_apply(qtt_ctx_t ctx, qtt_op_t op, qtt_tt_t in, double eps_tt, int rmax,
+                 int oversample, int apply_id, qtt_tt_t* out);
+/* SFFT, inverse SFFT and Green products with the context's cached operators
+ * (built on first use for the TT's n; Sec. 4.3, Alg. 2 lines 2-4, App. D
+ * lookup table). n[3] must be equal (cubic grids). */
+int sfft_apply(qtt_ctx_t ctx, qtt_tt_t in, double eps_tt, int rmax, qtt_tt_t* out);
+int isfft_apply(qtt_ctx_t ctx, qtt_tt_t in, double eps_tt, int rmax, qtt_tt_t* out);
+int gamma0_apply(qtt_ctx_t ctx, const int n[3], double lambda0, double mu0, int scheme,
+                 qtt_tt_t in, double eps_tt, int rmax, qtt_tt_t* out);
+/* TT rounding in place (Sec. 3, eq. (rounding_condition_tt)): QR sweep left
+ * to right, then truncated SVDs right to left with per-bond threshold
+ * eps_tt ||x|| / sqrt(L - 1) and rank cap rmax. Returns QTT_WRANKCAP when the
+ * cap dropped more than the threshold allows. */
+int tt_round(qtt_ctx_t ctx, qtt_tt_t inout, double eps_tt, int rmax);
+/* <a, b> = sum conj(a) b (FP64 accumulation). */
+int qtt_tt_dot(qtt_ctx_t ctx, qtt_tt_t a, qtt_tt_t b, double* re, double* im);
+/* Grid mean of A x without forming A x; writes 2 * d_out[0] doubles
+ * (interleaved complex, one per component of the first core). */
+int qtt_op_mean_apply(qtt_ctx_t ctx, qtt_op_t op, qtt_tt_t x, double* out);
+
+/* ---------------------------------------------------------------- solver */
+
+typedef struct {
+  double tol;      /* stop when ||eps_{m+1} - eps_m||_F / ||E||_F < tol */
+  int max_iter;    /* iteration cap (QTT_WNOCONV when reached) */
+  double eps_tt;   /* rounding accuracy of every step */
+  int rmax;        /* rank cap of every rounding */
+  int scheme;      /* Green operator discretisation: 0 = Direct */
+  int oversample;  /* sketch rank = rmax + oversample */
+} qtt_solve_params;
+
+typedef struct {
+  int iters;         /* iterations run */
+  double residual;   /* last ||eps_{m+1} - eps_m||_F / ||E||_F */
+  int max_rank;      /* largest TT rank met */
+  int rank_cap_hit;  /* 1 if some rounding hit the cap */
+  double imag_leak;  /* max |Im sigma_bar| */
+  double ms;         /* wall time of the solve */
+} qtt_solve_info;
+
+/* Alg. 2 for one macro strain E_voigt with explicit operators (dC raised, S,
+ * S^H, Gamma raised) and reference stiffness C0 (6x6 row-major): writes
+ * sigma_bar = C0 E + mean(dC eps_final) as 6 interleaved complex values. */
+int ls_solve_ops(qtt_ctx_t ctx, qtt_op_t dC, qtt_op_t S, qtt_op_t Sh, qtt_op_t gamma,
+                 const double C0[36], const double E_voigt[6], const qtt_solve_params* p,
+                 double sigma_bar[12], qtt_solve_info* info);
+/* Alg. 2 with the context's cached S, S^H and Gamma for dC's grid and C0. */
+int ls_solve(qtt_ctx_t ctx, qtt_op_t dC, const double E_voigt[6],
+             const qtt_solve_params* p, double sigma_bar[12], qtt_solve_info* info);
+/* C_eff column by column (Sec. 2): column k = Re sigma_bar for E = e_k, for
+ * the load cases listed in loads[nloads] (NULL = all six). Ceff is 36 doubles,
+ * column-major (Ceff[k*6 + i] = C_eff[i][k]); info has nloads entries. */
+int ls_solve_ceff(qtt_ctx_t ctx, qtt_op_t dC, const qtt_solve_params* p, const int* loads,
+                  int nloads, double* Ceff, qtt_solve_info* info);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QTT_HOMOG_H */

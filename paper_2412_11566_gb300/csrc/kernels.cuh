@@ -1,0 +1,639 @@
+// Device kernels of the QTT homogenisation library (sm_103a).
+//
+// Complex numbers are interleaved (re, im) pairs of R = double (FP64 mode) or
+// float (FP32 mode). Matrices are addressed through (row stride, column
+// stride) pairs so that one GEMM kernel serves every contraction of the
+// tensor-train sweeps without explicit transposes.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace qtt {
+
+template <typename R>
+struct alignas(2 * sizeof(R)) Cx {
+  R x, y;
+};
+
+template <typename R>
+__host__ __device__ __forceinline__ Cx<R> mk(R a, R b) {
+  Cx<R> c;
+  c.x = a;
+  c.y = b;
+  return c;
+}
+template <typename R>
+__device__ __forceinline__ Cx<R> cadd(Cx<R> a, Cx<R> b) { return mk(a.x + b.x, a.y + b.y); }
+template <typename R>
+__device__ __forceinline__ Cx<R> csub(Cx<R> a, Cx<R> b) { return mk(a.x - b.x, a.y - b.y); }
+template <typename R>
+__device__ __forceinline__ Cx<R> cmul(Cx<R> a, Cx<R> b) {
+  return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// conj(a) * b
+template <typename R>
+__device__ __forceinline__ Cx<R> cmulc(Cx<R> a, Cx<R> b) {
+  return mk(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+template <typename R>
+__device__ __forceinline__ Cx<R> cconj(Cx<R> a) { return mk(a.x, -a.y); }
+template <typename R>
+__device__ __forceinline__ R cabs2(Cx<R> a) { return a.x * a.x + a.y * a.y; }
+template <typename R>
+__device__ __forceinline__ Cx<R> cscale(Cx<R> a, R s) { return mk(a.x * s, a.y * s); }
+
+template <typename R>
+__device__ __forceinline__ R warp_sum(R v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+template <typename R>
+__device__ __forceinline__ Cx<R> warp_sum(Cx<R> v) {
+  v.x = warp_sum(v.x);
+  v.y = warp_sum(v.y);
+  return v;
+}
+
+// ------------------------------------------------------------------ GEMM
+// C[b] = alpha * op(A)[b] * op(B)[b] + beta * C[b] for a 3-level batch
+// (b1, b2, b3) and an optional split of K over `ksplit` CTAs (then beta must
+// be 0, C must be zeroed by the caller and partial sums are added atomically).
+struct GemmArgs {
+  int M, N, K;
+  const void* A;
+  long long a_rs, a_cs, a_b1, a_b2, a_b3;
+  const void* B;
+  long long b_rs, b_cs, b_b1, b_b2, b_b3;
+  void* C;
+  long long c_rs, c_cs, c_b1, c_b2, c_b3;
+  int nb1, nb2, nb3, ksplit;
+  int conjA, conjB;
+  double alpha_re, alpha_im, beta_re, beta_im;
+};
+
+template <typename R, int BM, int BN, int BK, int TM, int TN>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+gemm_kernel(GemmArgs g) {
+  constexpr int NT = (BM / TM) * (BN / TN);
+  __shared__ Cx<R> As[BK][BM + 1];
+  __shared__ Cx<R> Bs[BK][BN + 1];
+  int z = blockIdx.z;
+  const int ks = z % g.ksplit;
+  z /= g.ksplit;
+  const int b3 = z % g.nb3;
+  z /= g.nb3;
+  const int b2 = z % g.nb2;
+  const int b1 = z / g.nb2;
+  const Cx<R>* A = (const Cx<R>*)g.A + b1 * g.a_b1 + b2 * g.a_b2 + b3 * g.a_b3;
+  const Cx<R>* B = (const Cx<R>*)g.B + b1 * g.b_b1 + b2 * g.b_b2 + b3 * g.b_b3;
+  Cx<R>* C = (Cx<R>*)g.C + b1 * g.c_b1 + b2 * g.c_b2 + b3 * g.c_b3;
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  // K range of this split
+  const int kchunk = ((g.K + g.ksplit - 1) / g.ksplit + BK - 1) / BK * BK;
+  const int kbeg = ks * kchunk;
+  const int kend = min(g.K, kbeg + kchunk);
+  const int tid = threadIdx.x;
+  const int tr = tid / (BN / TN), tc = tid % (BN / TN);
+  Cx<R> acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = mk<R>(0, 0);
+  const bool a_mfast = (g.a_rs == 1);
+  const bool b_nfast = (g.b_cs == 1);
+  for (int k0 = kbeg; k0 < kend; k0 += BK) {
+    for (int e = tid; e < BM * BK; e += NT) {
+      int mm, kk;
+      if (a_mfast) { mm = e % BM; kk = e / BM; } else { kk = e % BK; mm = e / BK; }
+      const int gm = m0 + mm, gk = k0 + kk;
+      Cx<R> v = mk<R>(0, 0);
+      if (gm < g.M && gk < kend) {
+        v = A[(long long)gm * g.a_rs + (long long)gk * g.a_cs];
+        if (g.conjA) v.y = -v.y;
+      }
+      As[kk][mm] = v;
+    }
+    for (int e = tid; e < BK * BN; e += NT) {
+      int kk, nn;
+      if (b_nfast) { nn = e % BN; kk = e / BN; } else { kk = e % BK; nn = e / BK; }
+      const int gk = k0 + kk, gn = n0 + nn;
+      Cx<R> v = mk<R>(0, 0);
+      if (gk < kend && gn < g.N) {
+        v = B[(long long)gk * g.b_rs + (long long)gn * g.b_cs];
+        if (g.conjB) v.y = -v.y;
+      }
+      Bs[kk][nn] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      Cx<R> a[TM], b[TN];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) a[i] = As[kk][tr + i * (BM / TM)];
+#pragma unroll
+      for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tc + j * (BN / TN)];
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) {
+          acc[i][j].x = fma(a[i].x, b[j].x, fma(-a[i].y, b[j].y, acc[i][j].x));
+          acc[i][j].y = fma(a[i].x, b[j].y, fma(a[i].y, b[j].x, acc[i][j].y));
+        }
+    }
+    __syncthreads();
+  }
+  const Cx<R> alpha = mk<R>((R)g.alpha_re, (R)g.alpha_im);
+  const Cx<R> beta = mk<R>((R)g.beta_re, (R)g.beta_im);
+  const bool use_beta = (g.beta_re != 0.0 || g.beta_im != 0.0);
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+    const int gm = m0 + tr + i * (BM / TM);
+    if (gm >= g.M) continue;
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      const int gn = n0 + tc + j * (BN / TN);
+      if (gn >= g.N) continue;
+      Cx<R>* p = C + (long long)gm * g.c_rs + (long long)gn * g.c_cs;
+      Cx<R> v = cmul(alpha, acc[i][j]);
+      if (g.ksplit > 1) {
+        atomicAdd(&p->x, v.x);
+        atomicAdd(&p->y, v.y);
+      } else {
+        if (use_beta) v = cadd(v, cmul(beta, *p));
+        *p = v;
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ block reduction helper
+template <typename R>
+__device__ R block_sum(R v, R* sh) {
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  const int nw = (blockDim.x + 31) >> 5;
+  R t = (threadIdx.x < nw) ? sh[threadIdx.x] : (R)0;
+  if (w == 0) t = warp_sum(t);
+  if (threadIdx.x == 0) sh[0] = t;
+  __syncthreads();
+  R r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+// ------------------------------------------------------------------ Householder QR
+// One CTA factors the m x n matrix A (element (i, j) at A[i*rs + j*cs],
+// conjugated when conjA) as A = Q R with k = min(m, n): Q is m x k with
+// orthonormal columns (column-major, ld m), R is k x n upper trapezoidal
+// (column-major, ld k). Reflectors H = I - h v v^H with v = x - beta e1 and
+// beta = -phase(x0) ||x||, applied to the trailing columns column by column;
+// Q is accumulated backwards from [I; 0]. W (m x n) is workspace.
+template <typename R>
+__global__ void qr_kernel(int m, int n, const Cx<R>* __restrict__ A, long long rs, long long cs,
+                          int conjA, Cx<R>* W, Cx<R>* Q, Cx<R>* Rm, R* hbuf, Cx<R>* vhead) {
+  __shared__ R red[32];
+  __shared__ Cx<R> s_v0;
+  __shared__ R s_h;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
+  for (long long e = tid; e < (long long)m * n; e += nt) {
+    const int i = (int)(e % m), j = (int)(e / m);
+    Cx<R> v = A[(long long)i * rs + (long long)j * cs];
+    if (conjA) v.y = -v.y;
+    W[e] = v;
+  }
+  __syncthreads();
+  const int k = min(m, n);
+  for (int j = 0; j < k; ++j) {
+    Cx<R>* col = W + (long long)j * m;
+    R s2 = 0;
+    for (int i = j + tid; i < m; i += nt) s2 += cabs2(col[i]);
+    s2 = block_sum(s2, red);
+    if (tid == 0) {
+      const Cx<R> a = col[j];
+      const R s = sqrt(s2);
+      if (s == (R)0) {
+        s_h = 0;
+        s_v0 = mk<R>(0, 0);
+      } else {
+        // hypot keeps |phase| = 1 when |a| is tiny (no underflow of |a|^2)
+        const R aa = hypot(a.x, a.y);
+        const Cx<R> ph = aa > (R)0 ? mk<R>(a.x / aa, a.y / aa) : mk<R>(1, 0);
+        const Cx<R> beta = mk<R>(-ph.x * s, -ph.y * s);
+        const Cx<R> v0 = csub(a, beta);
+        const R vtv = s2 - aa * aa + cabs2(v0);
+        s_h = (R)2 / vtv;
+        s_v0 = v0;
+        col[j] = beta;
+      }
+      hbuf[j] = s_h;
+      vhead[j] = s_v0;
+    }
+    __syncthreads();
+    const R h = s_h;
+    const Cx<R> v0 = s_v0;
+    if (h != (R)0) {
+      for (int c = j + 1 + warp; c < n; c += nw) {
+        Cx<R>* a = W + (long long)c * m;
+        Cx<R> w = mk<R>(0, 0);
+        if (lane == 0) w = cmulc(v0, a[j]);
+        for (int i = j + 1 + lane; i < m; i += 32) w = cadd(w, cmulc(col[i], a[i]));
+        w = warp_sum(w);
+        const Cx<R> hw = cscale(w, h);
+        if (lane == 0) a[j] = csub(a[j], cmul(hw, v0));
+        for (int i = j + 1 + lane; i < m; i += 32) a[i] = csub(a[i], cmul(hw, col[i]));
+      }
+    }
+    __syncthreads();
+  }
+  // R (k x n)
+  for (long long e = tid; e < (long long)k * n; e += nt) {
+    const int i = (int)(e % k), j = (int)(e / k);
+    Rm[e] = (i <= j) ? W[(long long)j * m + i] : mk<R>(0, 0);
+  }
+  // Q = H_0 ... H_{k-1} [I; 0]
+  for (long long e = tid; e < (long long)m * k; e += nt) {
+    const int i = (int)(e % m), j = (int)(e / m);
+    Q[e] = mk<R>(i == j ? (R)1 : (R)0, 0);
+  }
+  __syncthreads();
+  for (int j = k - 1; j >= 0; --j) {
+    const R h = hbuf[j];
+    if (h == (R)0) continue;
+    const Cx<R> v0 = vhead[j];
+    const Cx<R>* col = W + (long long)j * m;
+    for (int c = j + warp; c < k; c += nw) {
+      Cx<R>* q = Q + (long long)c * m;
+      Cx<R> w = mk<R>(0, 0);
+      if (lane == 0) w = cmulc(v0, q[j]);
+      for (int i = j + 1 + lane; i < m; i += 32) w = cadd(w, cmulc(col[i], q[i]));
+      w = warp_sum(w);
+      const Cx<R> hw = cscale(w, h);
+      if (lane == 0) q[j] = csub(q[j], cmul(hw, v0));
+      for (int i = j + 1 + lane; i < m; i += 32) q[i] = csub(q[i], cmul(hw, col[i]));
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ one-sided Jacobi SVD
+// One CTA orthogonalises the n columns of the m x n (m >= n) column-major
+// matrix A in place by complex plane rotations (Hestenes), round-robin
+// ordering so that the n/2 pairs of a round are disjoint, with the rotations
+// accumulated in V (n x n, column-major). At exit A V_in = U diag(sigma):
+// sigma is sorted descending into `sigma`, the columns of A are overwritten
+// by U (unit columns, permuted) and V by the permuted V. The truncation rank
+// k (smallest k >= 1 with sum_{i >= k} sigma_i^2 <= delta2, then min(k,
+// rmax); sigma_i instead of sigma_i^2 when values_are_squares, for the
+// eigenvalues of a Gram matrix) is written to trunc[0] and trunc[1] = 1 if the cap cut more than
+// delta2 allows. `perm` (n ints) and `snorm` (n reals) are workspace.
+// The sweep loop is bounded by max_sweeps; trunc[2] receives the sweeps run.
+template <typename R>
+__global__ void jacobi_svd_kernel(int m, int n, Cx<R>* A, Cx<R>* V, double* sigma,
+                                  int* perm, R* snorm, double delta2, int rmax, int* trunc,
+                                  int max_sweeps, R tol, int values_are_squares) {
+  __shared__ int s_rot;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
+  for (long long e = tid; e < (long long)n * n; e += nt) {
+    const int i = (int)(e % n), j = (int)(e / n);
+    V[e] = mk<R>(i == j ? (R)1 : (R)0, 0);
+  }
+  __shared__ R s_red[32];
+  R f2 = 0;
+  for (long long e = tid; e < (long long)m * n; e += nt) f2 += cabs2(A[e]);
+  f2 = block_sum(f2, s_red);
+  // Columns whose squared norm is below eps^2 ||A||_F^2 are at the rounding
+  // noise floor: rotating them cannot orthogonalise them any further, so they
+  // are left alone (otherwise the sweep never settles).
+  const R eps_r = sizeof(R) == 8 ? (R)2.220446049250313e-16 : (R)1.1920929e-7;
+  const R negl = eps_r * eps_r * f2;
+  const int np = (n + 1) & ~1;  // players (even)
+  const int mp = np - 1;
+  int sweep = 0;
+  if (tid == 0) s_rot = 1;
+  __syncthreads();
+  for (sweep = 0; sweep < max_sweeps && np > 1; ++sweep) {
+    __syncthreads();
+    if (s_rot == 0) break;
+    __syncthreads();
+    if (tid == 0) s_rot = 0;
+    __syncthreads();
+    for (int r = 0; r < mp; ++r) {
+      for (int pi = warp; pi < np / 2; pi += nw) {
+        int p, q;
+        if (pi == 0) {
+          p = 0;
+          q = (r % mp) + 1;
+        } else {
+          p = ((r + pi) % mp) + 1;
+          q = ((r + mp - pi) % mp) + 1;
+        }
+        if (p >= n || q >= n) continue;
+        Cx<R>* ap = A + (long long)p * m;
+        Cx<R>* aq = A + (long long)q * m;
+        R app = 0, aqq = 0;
+        Cx<R> apq = mk<R>(0, 0);
+        for (int i = lane; i < m; i += 32) {
+          const Cx<R> x = ap[i], y = aq[i];
+          app += cabs2(x);
+          aqq += cabs2(y);
+          apq = cadd(apq, cmulc(x, y));
+        }
+        app = warp_sum(app);
+        aqq = warp_sum(aqq);
+        apq = warp_sum(apq);
+        if (app <= negl || aqq <= negl) continue;
+        const R g = hypot(apq.x, apq.y);
+        if (!(g > tol * sqrt(app) * sqrt(aqq))) continue;
+        // reduce to a real symmetric 2x2 problem with phase e^{i phi} = apq/|apq|
+        const Cx<R> e = mk<R>(apq.x / g, apq.y / g);
+        const R zeta = (aqq - app) / ((R)2 * g);
+        const R t = (zeta >= (R)0 ? (R)1 : (R)-1) / (fabs(zeta) + sqrt((R)1 + zeta * zeta));
+        const R c = (R)1 / sqrt((R)1 + t * t);
+        const R s = c * t;
+        // a_p' = c a_p - s conj(e) a_q ; a_q' = s a_p + c conj(e) a_q
+        const Cx<R> ec = cconj(e);
+        for (int i = lane; i < m; i += 32) {
+          const Cx<R> x = ap[i], y = cmul(ec, aq[i]);
+          ap[i] = mk<R>(c * x.x - s * y.x, c * x.y - s * y.y);
+          aq[i] = mk<R>(s * x.x + c * y.x, s * x.y + c * y.y);
+        }
+        Cx<R>* vp = V + (long long)p * n;
+        Cx<R>* vq = V + (long long)q * n;
+        for (int i = lane; i < n; i += 32) {
+          const Cx<R> x = vp[i], y = cmul(ec, vq[i]);
+          vp[i] = mk<R>(c * x.x - s * y.x, c * x.y - s * y.y);
+          vq[i] = mk<R>(s * x.x + c * y.x, s * x.y + c * y.y);
+        }
+        if (lane == 0) s_rot = 1;
+      }
+      __syncthreads();
+    }
+  }
+  __syncthreads();
+  // column norms
+  for (int j = warp; j < n; j += nw) {
+    R s2 = 0;
+    const Cx<R>* a = A + (long long)j * m;
+    for (int i = lane; i < m; i += 32) s2 += cabs2(a[i]);
+    s2 = warp_sum(s2);
+    if (lane == 0) snorm[j] = sqrt(s2);
+  }
+  __syncthreads();
+  // rank of each column in descending order (ties by index)
+  for (int j = tid; j < n; j += nt) {
+    const R sj = snorm[j];
+    int rk = 0;
+    for (int i = 0; i < n; ++i) {
+      const R si = snorm[i];
+      rk += (si > sj) || (si == sj && i < j);
+    }
+    perm[rk] = j;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double tail = 0;
+    int k = n;
+    // tail[j] = sum_{i >= j} s_i^2 ; smallest j >= 1 with tail[j] <= delta2
+    double* tails = sigma;  // reuse sigma as scratch for the tails, fixed below
+    for (int j = n - 1; j >= 0; --j) {
+      const double s = (double)snorm[perm[j]];
+      tail += values_are_squares ? s : s * s;
+      tails[j] = tail;
+    }
+    k = n;
+    for (int j = 1; j < n; ++j)
+      if (tails[j] <= delta2) {
+        k = j;
+        break;
+      }
+    trunc[1] = (k > rmax) ? 1 : 0;
+    trunc[0] = k < rmax ? k : rmax;
+    trunc[2] = sweep;
+  }
+  __syncthreads();
+  for (int j = tid; j < n; j += nt) sigma[j] = (double)snorm[perm[j]];
+  __syncthreads();
+}
+
+// Reorders/normalises columns after jacobi_svd_kernel: Uout[:, j] =
+// A[:, perm[j]] / sigma_j (0 when sigma_j == 0), Vout[:, j] = V[:, perm[j]].
+template <typename R>
+__global__ void svd_finish_kernel(int m, int n, const Cx<R>* A, const Cx<R>* V, const double* sigma,
+                                  const int* perm, Cx<R>* Uout, Cx<R>* Vout) {
+  const long long tot = (long long)m * n + (long long)n * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    if (e < (long long)m * n) {
+      const int i = (int)(e % m), j = (int)(e / m);
+      const double s = sigma[j];
+      const Cx<R> a = A[(long long)perm[j] * m + i];
+      Uout[e] = s > 0 ? mk<R>((R)(a.x / s), (R)(a.y / s)) : mk<R>(0, 0);
+    } else {
+      const long long f = e - (long long)m * n;
+      const int i = (int)(f % n), j = (int)(f / n);
+      Vout[f] = V[(long long)perm[j] * n + i];
+    }
+  }
+}
+
+// ------------------------------------------------------------------ strided copy / permute
+// out[flat] = s * op(in[sum_d idx_d * in_stride_d]) over an up-to-6-D index
+// space (sizes[0] slowest), optional conjugation; out is contiguous or has
+// its own strides.
+struct CopyArgs {
+  int nd;
+  long long size[6];
+  long long in_st[6];
+  long long out_st[6];
+  int conj;
+  double scale;
+};
+
+template <typename R>
+__global__ void copy_kernel(const Cx<R>* __restrict__ in, Cx<R>* __restrict__ out, CopyArgs a,
+                            long long total) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    long long r = e, io = 0, oo = 0;
+    for (int d = a.nd - 1; d >= 0; --d) {
+      const long long i = r % a.size[d];
+      r /= a.size[d];
+      io += i * a.in_st[d];
+      oo += i * a.out_st[d];
+    }
+    if (a.scale == 0.0) {
+      out[oo] = mk<R>(0, 0);
+      continue;
+    }
+    Cx<R> v = in[io];
+    if (a.conj) v.y = -v.y;
+    out[oo] = mk<R>((R)(v.x * a.scale), (R)(v.y * a.scale));
+  }
+}
+
+template <typename Rin, typename Rout>
+__global__ void convert_kernel(const Cx<Rin>* __restrict__ in, Cx<Rout>* __restrict__ out,
+                               long long total) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x)
+    out[e] = mk<Rout>((Rout)in[e].x, (Rout)in[e].y);
+}
+
+// Scale column j of an m x k column-major matrix by sigma[j].
+template <typename R>
+__global__ void scale_cols_kernel(Cx<R>* M, int m, int k, const double* sigma) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)m * k;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(e / m);
+    M[e] = cscale(M[e], (R)sigma[j]);
+  }
+}
+
+// sum |x|^2 in FP64, atomically added to *out.
+template <typename R>
+__global__ void norm2_kernel(const Cx<R>* __restrict__ x, long long n, double* out) {
+  double s = 0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x)
+    s += (double)x[e].x * x[e].x + (double)x[e].y * x[e].y;
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
+}
+
+// ------------------------------------------------------------------ Philox sketches
+// Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of two 32x32
+// multiplications with key schedule increments (Weyl sequence).
+__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(M0, c[0]), lo0 = M0 * c[0];
+    const uint32_t hi1 = __umulhi(M1, c[2]), lo1 = M1 * c[2];
+    const uint32_t n0 = hi1 ^ c[1] ^ k0, n1 = lo1, n2 = hi0 ^ c[3] ^ k1, n3 = lo0;
+    c[0] = n0;
+    c[1] = n1;
+    c[2] = n2;
+    c[3] = n3;
+    k0 += W0;
+    k1 += W1;
+  }
+}
+
+__device__ __forceinline__ double u32_unit(uint32_t w) {
+  return ((double)(int32_t)w + 0.5) * 4.656612873077392578125e-10;  // 2^-31
+}
+
+// Sketch core entries: entry e uses counter (e >> 1, core, apply_id, tag) and
+// key (seed low, seed high); even e takes words (0, 1), odd e words (2, 3) as
+// (re, im), each mapped to (int32(w) + 1/2) 2^-31 in (-1, 1).
+template <typename R>
+__global__ void sketch_kernel(Cx<R>* out, long long count, uint64_t seed, int core, int apply_id) {
+  const uint32_t tag = 0x5EC7C0DEu;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < count;
+       e += (long long)gridDim.x * blockDim.x) {
+    uint32_t c[4] = {(uint32_t)(e >> 1), (uint32_t)core, (uint32_t)apply_id, tag};
+    philox4x32_10(c, (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32));
+    const uint32_t wr = (e & 1) ? c[2] : c[0];
+    const uint32_t wi = (e & 1) ? c[3] : c[1];
+    out[e] = mk<R>((R)u32_unit(wr), (R)u32_unit(wi));
+  }
+}
+
+// ------------------------------------------------------------------ dense fields (preprocessing)
+
+// Voigt pair I -> (i, j) and weights 1,1,1,2,2,2.
+__device__ __forceinline__ void voigt_ij(int I, int& i, int& j) {
+  const int a[6] = {0, 1, 2, 1, 0, 0};
+  const int b[6] = {0, 1, 2, 2, 2, 1};
+  i = a[I];
+  j = b[I];
+}
+
+__device__ __forceinline__ int bitrev(int k, int n) { return (int)(__brev((unsigned)k) >> (32 - n)); }
+
+// Green operator of the Direct scheme in the SFFT momentum convention:
+// out[(I*6 + J) * N^3 + (k1 * N + k2) * N + k3] = Gamma_V[I, J](xi) with
+// xi_a = xi(rev k_a), xi(k) = k for k <= N/2 else k - N, and
+// Gamma_ijkl = (d_ik n_j n_l + d_il n_j n_k + d_jk n_i n_l + d_jl n_i n_k) / (4 mu0)
+//              - (lam0 + mu0) / (mu0 (lam0 + 2 mu0)) n_i n_j n_k n_l,
+// Gamma_V[I, J] = w_I w_J Gamma_{i_I j_I k_J l_J}, Gamma(0) = 0. Real-valued, so
+// the conjugation of the convention is the identity.
+__global__ void gamma_field_kernel(Cx<double>* out, int n, double lam0, double mu0) {
+  const long long N = 1ll << n, N3 = N * N * N;
+  const double beta0 = (lam0 + mu0) / (mu0 * (lam0 + 2.0 * mu0));
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N3;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int k1 = (int)(e / (N * N)), k2 = (int)((e / N) % N), k3 = (int)(e % N);
+    double xi[3];
+    const int ks[3] = {k1, k2, k3};
+    for (int a = 0; a < 3; ++a) {
+      const int k = n > 0 ? bitrev(ks[a], n) : 0;
+      xi[a] = (k <= N / 2) ? (double)k : (double)(k - N);
+    }
+    const double r2 = xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2];
+    double nn[3] = {0, 0, 0};
+    if (r2 > 0) {
+      const double r = sqrt(r2);
+      for (int a = 0; a < 3; ++a) nn[a] = xi[a] / r;
+    }
+    for (int I = 0; I < 6; ++I) {
+      int i, j;
+      voigt_ij(I, i, j);
+      for (int J = 0; J < 6; ++J) {
+        int k, l;
+        voigt_ij(J, k, l);
+        double g = 0;
+        if (r2 > 0) {
+          const double t1 = (i == k) * nn[j] * nn[l] + (i == l) * nn[j] * nn[k] +
+                            (j == k) * nn[i] * nn[l] + (j == l) * nn[i] * nn[k];
+          g = t1 / (4.0 * mu0) - beta0 * nn[i] * nn[j] * nn[k] * nn[l];
+        }
+        const double w = (I < 3 ? 1.0 : 2.0) * (J < 3 ? 1.0 : 2.0);
+        out[((long long)(I * 6 + J)) * N3 + e] = mk<double>(w * g, 0.0);
+      }
+    }
+  }
+}
+
+// Voigt-matrix stiffness-difference field from a phase array with broadcast
+// axes: out[P * cells + c] = dC[phase(c)][P] where P indexes the 36 Voigt
+// pairs (row-major 6x6) and c runs over the non-broadcast cells.
+__global__ void stiffness_field_kernel(const uint8_t* phase, long long cells, const double* dC,
+                                       int nphase, Cx<double>* out) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < cells;
+       c += (long long)gridDim.x * blockDim.x) {
+    int p = phase[c];
+    if (p >= nphase) p = nphase - 1;
+    for (int P = 0; P < 36; ++P) out[(long long)P * cells + c] = mk<double>(dC[p * 36 + P], 0.0);
+  }
+}
+
+// SFFT tensor of one axis in core order: out[e], e = sum_b (2 o_b + i_b) 4^(n-1-b),
+// = S[k', x] = N^-1/2 exp(2 pi i rev(k') x / N) with k' bits o_b, x bits i_b (MSB first).
+__global__ void sfft_tensor_kernel(double* out, int n) {
+  const long long N = 1ll << n, tot = N * N;
+  const double inv = 1.0 / sqrt((double)N);
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    int kp = 0, x = 0;
+    for (int b = 0; b < n; ++b) {
+      const int digit = (int)((e >> (2 * (n - 1 - b))) & 3);
+      kp = (kp << 1) | (digit >> 1);
+      x = (x << 1) | (digit & 1);
+    }
+    const long long k = n > 0 ? bitrev(kp, n) : 0;
+    const long long ph = (k * x) % N;  // exact phase index
+    double s, c;
+    sincospi(2.0 * (double)ph / (double)N, &s, &c);
+    out[2 * e] = c * inv;
+    out[2 * e + 1] = s * inv;
+  }
+}
+
+}  // namespace qtt

@@ -1,0 +1,1767 @@
+// Host engine and C ABI of the QTT homogenisation library (see
+// include/qtt_homog.h for the contract of every entry point).
+//
+// The engine drives sweeps over the tensor-train cores from the host: every
+// contraction is a launch of the strided batched complex GEMM, every
+// factorisation a one-CTA Householder QR or one-sided Jacobi SVD, and the
+// ranks chosen by a truncation are read back before the next core is sized.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <stdexcept>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/qtt_homog.h"
+#include "kernels.cuh"
+
+using namespace qtt;
+
+namespace {
+
+struct QttError : std::runtime_error {
+  int code;
+  QttError(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+#define QCHECK(call)                                                                      \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      throw QttError(QTT_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));      \
+  } while (0)
+
+#define QREQ(cond, msg)                                  \
+  do {                                                   \
+    if (!(cond)) throw QttError(QTT_EINVAL, (msg));      \
+  } while (0)
+
+// ------------------------------------------------------------------ workspace arena
+// First-fit allocator over the caller's device buffer, 256-byte granules,
+// neighbouring free blocks coalesced on release. Host-side bookkeeping only.
+struct Arena {
+  char* base = nullptr;
+  size_t size = 0, used = 0, peak = 0;
+  std::map<size_t, size_t> free_;   // offset -> bytes
+  std::map<size_t, size_t> taken_;  // offset -> bytes
+  void init(void* b, size_t s) {
+    base = (char*)b;
+    size = s & ~(size_t)255;
+    free_.clear();
+    taken_.clear();
+    free_[0] = size;
+    used = peak = 0;
+  }
+  void* alloc(size_t bytes) {
+    bytes = std::max<size_t>(256, (bytes + 255) & ~(size_t)255);
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= bytes) {
+        const size_t off = it->first, rem = it->second - bytes;
+        free_.erase(it);
+        if (rem) free_[off + bytes] = rem;
+        taken_[off] = bytes;
+        used += bytes;
+        peak = std::max(peak, used);
+        return base + off;
+      }
+    }
+    throw QttError(QTT_ENOMEM, "workspace exhausted: need " + std::to_string(bytes) +
+                                   " bytes, " + std::to_string(size - used) + " free");
+  }
+  // Bytes from p to the end of the allocation holding p, or -1.
+  long long extent(const void* p) const {
+    if (!p || (const char*)p < base || (const char*)p >= base + size) return -1;
+    const size_t off = (const char*)p - base;
+    auto it = taken_.upper_bound(off);
+    if (it == taken_.begin()) return -1;
+    --it;
+    if (off >= it->first + it->second) return -1;
+    return (long long)(it->first + it->second - off);
+  }
+  void release(void* p) {
+    if (!p) return;
+    const size_t off = (char*)p - base;
+    auto it = taken_.find(off);
+    if (it == taken_.end()) return;
+    size_t bytes = it->second;
+    taken_.erase(it);
+    used -= bytes;
+    size_t start = off;
+    auto nx = free_.lower_bound(off);
+    if (nx != free_.end() && nx->first == off + bytes) {
+      bytes += nx->second;
+      free_.erase(nx);
+    }
+    auto pv = free_.lower_bound(off);
+    if (pv != free_.begin()) {
+      --pv;
+      if (pv->first + pv->second == off) {
+        start = pv->first;
+        bytes += pv->second;
+        free_.erase(pv);
+      }
+    }
+    free_[start] = bytes;
+  }
+};
+
+}  // namespace
+
+struct qtt_tt;
+struct qtt_op;
+
+struct qtt_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int prec = QTT_FP64;
+  uint64_t seed = 0;
+  Arena arena;
+  std::string err;
+  uint64_t launches = 0;
+  void* pinned = nullptr;  // small host readback buffer
+  // Optional per-kernel-class timing: events recorded around launches,
+  // resolved lazily (class: 0 gemm, 1 qr, 2 svd).
+  int profiling = 0;
+  struct Ev {
+    cudaEvent_t a, b;
+    int cls;
+    double flops;
+  };
+  std::vector<Ev> evs;
+  double prof_ms[3] = {0, 0, 0};
+  double prof_flops[3] = {0, 0, 0};
+  long long prof_n[3] = {0, 0, 0};
+  std::map<std::pair<int, int>, qtt_op*> sfft_cache;                            // (n, adjoint)
+  std::map<std::tuple<int, double, double, int, double, int>, qtt_op*> gamma_cache;
+  size_t esize() const { return prec == QTT_FP64 ? 16 : 8; }
+};
+
+static void prof_flush(qtt_ctx* c) {
+  for (auto& e : c->evs) {
+    float ms = 0;
+    if (cudaEventSynchronize(e.b) == cudaSuccess && cudaEventElapsedTime(&ms, e.a, e.b) == cudaSuccess) {
+      c->prof_ms[e.cls] += ms;
+      c->prof_flops[e.cls] += e.flops;
+      c->prof_n[e.cls] += 1;
+    }
+    cudaEventDestroy(e.a);
+    cudaEventDestroy(e.b);
+  }
+  c->evs.clear();
+}
+
+struct ProfScope {
+  qtt_ctx* c;
+  qtt_ctx::Ev e{};
+  bool on;
+  ProfScope(qtt_ctx* ctx, int cls, double flops) : c(ctx), on(ctx->profiling != 0) {
+    if (!on) return;
+    e.cls = cls;
+    e.flops = flops;
+    cudaEventCreate(&e.a);
+    cudaEventCreate(&e.b);
+    cudaEventRecord(e.a, c->stream);
+  }
+  ~ProfScope() {
+    if (!on) return;
+    cudaEventRecord(e.b, c->stream);
+    c->evs.push_back(e);
+    if (c->evs.size() > 4096) prof_flush(c);
+  }
+};
+
+struct qtt_tt {
+  qtt_ctx* ctx = nullptr;
+  int L = 0;
+  int dims[QTT_MAX_CORES] = {0};
+  int ranks[QTT_MAX_CORES + 1] = {0};
+  void* core[QTT_MAX_CORES] = {nullptr};
+  long long count(int k) const { return (long long)ranks[k] * dims[k] * ranks[k + 1]; }
+};
+
+struct qtt_op {
+  qtt_ctx* ctx = nullptr;
+  int L = 0;
+  int dout[QTT_MAX_CORES] = {0};
+  int din[QTT_MAX_CORES] = {0};
+  int ranks[QTT_MAX_CORES + 1] = {0};
+  int diag[QTT_MAX_CORES] = {0};
+  void* core[QTT_MAX_CORES] = {nullptr};
+  int n = 0;
+  int has_c0 = 0;
+  double lame0[2] = {0, 0};
+  double C0[36] = {0};
+  long long count(int k) const {
+    return diag[k] ? (long long)ranks[k] * dout[k] * ranks[k + 1]
+                   : (long long)ranks[k] * dout[k] * din[k] * ranks[k + 1];
+  }
+};
+
+namespace {
+
+// ------------------------------------------------------------------ launch helpers
+
+struct Cplx {
+  double re, im;
+};
+
+struct MatRef {
+  const void* p;
+  long long rs, cs, b1, b2, b3;
+  int conj;
+};
+inline MatRef mref(const void* p, long long rs, long long cs, long long b1 = 0, long long b2 = 0,
+                   long long b3 = 0, int conj = 0) {
+  return MatRef{p, rs, cs, b1, b2, b3, conj};
+}
+
+int grid1d(long long n, int threads = 256) {
+  long long b = (n + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > 152 * 32) b = 152 * 32;
+  return (int)b;
+}
+
+template <typename R>
+struct Eng {
+  qtt_ctx* c;
+  explicit Eng(qtt_ctx* ctx) : c(ctx) {}
+  cudaStream_t st() const { return c->stream; }
+  void post() {
+    ++c->launches;
+    QCHECK(cudaGetLastError());
+  }
+  Cx<R>* alloc(long long count) { return (Cx<R>*)c->arena.alloc((size_t)count * sizeof(Cx<R>)); }
+  // Host-side launch validation: the largest element offset a strided access
+  // reaches must lie inside the workspace allocation the pointer belongs to.
+  void check_span(const void* p, long long max_off, const char* what) {
+    if (max_off < 0) return;
+    const long long ext = c->arena.extent(p);
+    if (ext < 0 || (max_off + 1) * (long long)sizeof(Cx<R>) > ext)
+      throw QttError(QTT_EINVAL, std::string("launch bounds check failed: ") + what +
+                                     " needs " + std::to_string((max_off + 1) * sizeof(Cx<R>)) +
+                                     " bytes, allocation has " + std::to_string(ext));
+  }
+  static long long span(long long n0, long long s0, long long n1 = 1, long long s1 = 0,
+                        long long n2 = 1, long long s2 = 0, long long n3 = 1, long long s3 = 0,
+                        long long n4 = 1, long long s4 = 0) {
+    if (n0 <= 0 || n1 <= 0 || n2 <= 0 || n3 <= 0 || n4 <= 0) return -1;
+    return (n0 - 1) * s0 + (n1 - 1) * s1 + (n2 - 1) * s2 + (n3 - 1) * s3 + (n4 - 1) * s4;
+  }
+  void release(void* p) { c->arena.release(p); }
+
+  // C = alpha op(A) op(B) + beta C over a (nb1, nb2, nb3) batch.
+  void gemm(int M, int N, int K, MatRef A, MatRef B, void* C, long long c_rs, long long c_cs,
+            long long c_b1, long long c_b2, long long c_b3, int nb1, int nb2, int nb3,
+            Cplx alpha = {1, 0}, Cplx beta = {0, 0}, int ksplit = 1) {
+    if (M <= 0 || N <= 0 || nb1 <= 0 || nb2 <= 0 || nb3 <= 0) return;
+    if (K <= 0) {
+      QREQ(beta.re == 0 && beta.im == 0, "gemm: K = 0 with beta != 0");
+      // C = 0
+      for (int b1 = 0; b1 < nb1; ++b1)
+        for (int b2 = 0; b2 < nb2; ++b2)
+          for (int b3 = 0; b3 < nb3; ++b3) {
+            CopyArgs a{};
+            a.nd = 2;
+            a.size[0] = M;
+            a.size[1] = N;
+            a.in_st[0] = 0;
+            a.in_st[1] = 0;
+            a.out_st[0] = c_rs;
+            a.out_st[1] = c_cs;
+            a.scale = 0.0;
+            Cx<R>* cp = (Cx<R>*)C + b1 * c_b1 + b2 * c_b2 + b3 * c_b3;
+            copy_kernel<R><<<grid1d((long long)M * N), 256, 0, st()>>>(cp, cp, a, (long long)M * N);
+            post();
+          }
+      return;
+    }
+    GemmArgs g{};
+    g.M = M;
+    g.N = N;
+    g.K = K;
+    g.A = A.p;
+    g.a_rs = A.rs;
+    g.a_cs = A.cs;
+    g.a_b1 = A.b1;
+    g.a_b2 = A.b2;
+    g.a_b3 = A.b3;
+    g.conjA = A.conj;
+    g.B = B.p;
+    g.b_rs = B.rs;
+    g.b_cs = B.cs;
+    g.b_b1 = B.b1;
+    g.b_b2 = B.b2;
+    g.b_b3 = B.b3;
+    g.conjB = B.conj;
+    g.C = C;
+    g.c_rs = c_rs;
+    g.c_cs = c_cs;
+    g.c_b1 = c_b1;
+    g.c_b2 = c_b2;
+    g.c_b3 = c_b3;
+    g.nb2 = nb2;
+    g.nb3 = nb3;
+    g.ksplit = std::max(1, ksplit);
+    g.alpha_re = alpha.re;
+    g.alpha_im = alpha.im;
+    g.beta_re = beta.re;
+    g.beta_im = beta.im;
+    if (g.ksplit > 1) QREQ(beta.re == 0 && beta.im == 0, "split-K gemm needs beta = 0");
+    QREQ(A.rs >= 0 && A.cs >= 0 && B.rs >= 0 && B.cs >= 0 && c_rs >= 0 && c_cs >= 0,
+         "gemm: negative stride");
+    check_span(A.p, span(M, A.rs, K, A.cs, nb1, A.b1, nb2, A.b2, nb3, A.b3), "gemm A");
+    check_span(B.p, span(K, B.rs, N, B.cs, nb1, B.b1, nb2, B.b2, nb3, B.b3), "gemm B");
+    check_span(C, span(M, c_rs, N, c_cs, nb1, c_b1, nb2, c_b2, nb3, c_b3), "gemm C");
+    constexpr int BM = 64, BN = 64, BK = sizeof(R) == 8 ? 8 : 16;
+    const long long per_b1 = (long long)nb2 * nb3 * g.ksplit;
+    QREQ(per_b1 <= 65535, "gemm batch too large");
+    const int chunk = (int)std::max<long long>(1, 65535 / per_b1);
+    const dim3 block(256);
+    const long long gx = (M + BM - 1) / BM, gy = (N + BN - 1) / BN;
+    QREQ(gy <= 65535, "gemm N too large");
+    for (int b0 = 0; b0 < nb1; b0 += chunk) {
+      const int nb = std::min(chunk, nb1 - b0);
+      GemmArgs h = g;
+      h.nb1 = nb;
+      h.A = (const Cx<R>*)g.A + b0 * g.a_b1;
+      h.B = (const Cx<R>*)g.B + b0 * g.b_b1;
+      h.C = (Cx<R>*)g.C + b0 * g.c_b1;
+      if (g.ksplit > 1) {
+        // zero the outputs first (atomic accumulation)
+        for (int b1 = 0; b1 < nb; ++b1)
+          for (int b2 = 0; b2 < nb2; ++b2)
+            for (int b3 = 0; b3 < nb3; ++b3) {
+              CopyArgs a{};
+              a.nd = 2;
+              a.size[0] = M;
+              a.size[1] = N;
+              a.out_st[0] = c_rs;
+              a.out_st[1] = c_cs;
+              a.scale = 0.0;
+              Cx<R>* cp = (Cx<R>*)h.C + b1 * c_b1 + b2 * c_b2 + b3 * c_b3;
+              copy_kernel<R><<<grid1d((long long)M * N), 256, 0, st()>>>(cp, cp, a,
+                                                                          (long long)M * N);
+              post();
+            }
+      }
+      const dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)(nb * per_b1));
+      ProfScope ps(c, 0, 8.0 * M * N * (double)K * nb * nb2 * nb3);
+      gemm_kernel<R, BM, BN, BK, 4, 4><<<grid, block, 0, st()>>>(h);
+      post();
+    }
+  }
+
+  // Strided copy out = scale * op(in) over an nd-D index space.
+  void copy(const void* in, void* out, int nd, const long long* size, const long long* in_st,
+            const long long* out_st, int conj = 0, double scale = 1.0) {
+    CopyArgs a{};
+    a.nd = nd;
+    long long tot = 1;
+    for (int d = 0; d < nd; ++d) {
+      a.size[d] = size[d];
+      a.in_st[d] = in_st[d];
+      a.out_st[d] = out_st[d];
+      tot *= size[d];
+    }
+    a.conj = conj;
+    a.scale = scale;
+    if (tot <= 0) return;
+    long long mi = 0, mo = 0;
+    for (int d = 0; d < nd; ++d) {
+      mi += (size[d] - 1) * in_st[d];
+      mo += (size[d] - 1) * out_st[d];
+    }
+    if (scale != 0.0) check_span(in, mi, "copy in");
+    check_span(out, mo, "copy out");
+    copy_kernel<R><<<grid1d(tot), 256, 0, st()>>>((const Cx<R>*)in, (Cx<R>*)out, a, tot);
+    post();
+  }
+
+  void zero(void* p, long long count) {
+    if (count > 0) QCHECK(cudaMemsetAsync(p, 0, (size_t)count * sizeof(Cx<R>), st()));
+  }
+
+  // Householder QR of the strided m x n matrix A: Q (m x k) and Rm (k x n),
+  // column-major, k = min(m, n).
+  void qr(int m, int n, const void* A, long long rs, long long cs, int conj, Cx<R>* Q, Cx<R>* Rm) {
+    const int k = std::min(m, n);
+    check_span(A, span(m, rs, n, cs), "qr A");
+    check_span(Q, (long long)m * k - 1, "qr Q");
+    check_span(Rm, (long long)k * n - 1, "qr R");
+    Cx<R>* W = alloc((long long)m * n);
+    R* h = (R*)c->arena.alloc(sizeof(R) * std::max(1, k));
+    Cx<R>* v0 = alloc(std::max(1, k));
+    {
+      // complex Householder QR with explicit Q: 4 x (2 m n^2 - 2 n^3 / 3) real
+      // flops for the factor plus as many for forming Q (LAPACK operation counts)
+      const double kk = k;
+      ProfScope ps(c, 1, 2.0 * 4.0 * (2.0 * m * kk * kk - 2.0 * kk * kk * kk / 3.0));
+      qr_kernel<R><<<1, 1024, 0, st()>>>(m, n, (const Cx<R>*)A, rs, cs, conj, W, Q, Rm, h, v0);
+      post();
+    }
+    release(W);
+    release(h);
+    release(v0);
+  }
+
+  // One-sided Jacobi SVD of the column-major m x n (m >= n) matrix in A
+  // (destroyed): U (m x n), sigma (n, descending), V (n x n), all
+  // column-major; returns the truncation rank for (delta2, rmax).
+  int svd(int m, int n, Cx<R>* A, Cx<R>* U, double* sigma, Cx<R>* V, double delta2, int rmax,
+          int* cap_hit, bool squares = false) {
+    QREQ(m >= n && n >= 1, "svd: needs m >= n >= 1");
+    QREQ(n <= 4096, "svd: too many columns");
+    check_span(A, (long long)m * n - 1, "svd A");
+    check_span(U, (long long)m * n - 1, "svd U");
+    check_span(V, (long long)n * n - 1, "svd V");
+    Cx<R>* Vw = alloc((long long)n * n);
+    int* perm = (int*)c->arena.alloc(sizeof(int) * n);
+    R* snorm = (R*)c->arena.alloc(sizeof(R) * n);
+    int* tr = (int*)c->arena.alloc(sizeof(int) * 4);
+    const R eps = sizeof(R) == 8 ? (R)2.220446049250313e-16 : (R)1.1920929e-7;
+    const R tol = eps * (R)std::sqrt((double)m);
+    const int sweeps = sizeof(R) == 8 ? 60 : 40;
+    {
+      // flops counted for the sweeps actually run are not known here; the
+      // profile records one sweep's count (n^2/2 pairs x (3 dots + 2
+      // rotations of length m + 2 of length n) x 8 real flops) per launch
+      ProfScope ps(c, 2, 0.5 * n * (double)n * (5.0 * m + 2.0 * n) * 8.0);
+      jacobi_svd_kernel<R><<<1, 1024, 0, st()>>>(m, n, A, Vw, sigma, perm, snorm, delta2, rmax,
+                                                   tr, sweeps, tol, squares ? 1 : 0);
+      post();
+    }
+    svd_finish_kernel<R><<<grid1d((long long)m * n + (long long)n * n), 256, 0, st()>>>(
+        m, n, A, Vw, sigma, perm, U, V);
+    post();
+    int h[4];
+    QCHECK(cudaMemcpyAsync(c->pinned, tr, sizeof(int) * 4, cudaMemcpyDeviceToHost, st()));
+    QCHECK(cudaStreamSynchronize(st()));
+    memcpy(h, c->pinned, sizeof(int) * 4);
+    release(Vw);
+    release(perm);
+    release(snorm);
+    release(tr);
+    if (cap_hit) *cap_hit = h[1];
+    return h[0];
+  }
+
+  double norm2(const void* p, long long count) {
+    double* d = (double*)c->arena.alloc(sizeof(double));
+    QCHECK(cudaMemsetAsync(d, 0, sizeof(double), st()));
+    norm2_kernel<R><<<grid1d(count), 256, 0, st()>>>((const Cx<R>*)p, count, d);
+    post();
+    QCHECK(cudaMemcpyAsync(c->pinned, d, sizeof(double), cudaMemcpyDeviceToHost, st()));
+    QCHECK(cudaStreamSynchronize(st()));
+    double v;
+    memcpy(&v, c->pinned, sizeof(double));
+    release(d);
+    return v;
+  }
+};
+
+// ------------------------------------------------------------------ TT / op helpers
+
+qtt_tt* new_tt(qtt_ctx* c, int L, const int* dims) {
+  QREQ(L >= 1 && L <= QTT_MAX_CORES, "TT core count out of range");
+  qtt_tt* t = new qtt_tt();
+  t->ctx = c;
+  t->L = L;
+  for (int k = 0; k < L; ++k) t->dims[k] = dims[k];
+  t->ranks[0] = t->ranks[L] = 1;
+  return t;
+}
+
+void free_tt(qtt_tt* t) {
+  if (!t) return;
+  for (int k = 0; k < t->L; ++k) t->ctx->arena.release(t->core[k]);
+  delete t;
+}
+
+void free_op(qtt_op* o) {
+  if (!o) return;
+  for (int k = 0; k < o->L; ++k) o->ctx->arena.release(o->core[k]);
+  delete o;
+}
+
+void set_core(qtt_tt* t, int k, void* p) {
+  t->ctx->arena.release(t->core[k]);
+  t->core[k] = p;
+}
+
+template <typename R>
+qtt_tt* clone_tt(Eng<R>& e, const qtt_tt* x) {
+  qtt_tt* y = new_tt(e.c, x->L, x->dims);
+  for (int k = 0; k <= x->L; ++k) y->ranks[k] = x->ranks[k];
+  for (int k = 0; k < x->L; ++k) {
+    y->core[k] = e.alloc(x->count(k));
+    QCHECK(cudaMemcpyAsync(y->core[k], x->core[k], x->count(k) * sizeof(Cx<R>),
+                           cudaMemcpyDeviceToDevice, e.st()));
+  }
+  return y;
+}
+
+// ------------------------------------------------------------------ rounding
+
+// Right-to-left truncated-SVD sweep of a left-orthogonal TT (Sec. 3,
+// eq. (rounding_condition_tt)); per-bond threshold delta2 = eps^2 ||x||^2 /
+// (L - 1) with ||x|| = ||last core||_F. Result is right-orthogonal.
+template <typename R>
+int round_right_to_left(Eng<R>& e, qtt_tt* x, double eps, int rmax) {
+  const int L = x->L;
+  const double nrm2 = e.norm2(x->core[L - 1], x->count(L - 1));
+  const double delta2 = L > 1 ? eps * eps * nrm2 / (double)(L - 1) : 0.0;
+  int cap_any = 0;
+  for (int k = L - 1; k >= 1; --k) {
+    const int r0 = x->ranks[k], d = x->dims[k], r1 = x->ranks[k + 1];
+    const int m = d * r1;
+    Cx<R>* core = (Cx<R>*)x->core[k];
+    int kk, cap = 0;
+    Cx<R>* newcore;
+    Cx<R>* carry;  // r0 x kk, column-major (ld r0)
+    if (m >= r0) {
+      // A = M^H (m x r0), M = core as r0 x m row-major.
+      Cx<R>* A = e.alloc((long long)m * r0);
+      const long long sz[2] = {r0, m}, ist[2] = {m, 1}, ost[2] = {m, 1};
+      e.copy(core, A, 2, sz, ist, ost, 1);  // A[j + c m] = conj(M[c, j])
+      Cx<R>* U = e.alloc((long long)m * r0);
+      Cx<R>* V = e.alloc((long long)r0 * r0);
+      double* sig = (double*)e.c->arena.alloc(sizeof(double) * r0);
+      kk = e.svd(m, r0, A, U, sig, V, delta2, rmax, &cap);
+      // M = V S U^H: new core = U[:, :kk]^H (kk x m), carry = V[:, :kk] S
+      newcore = e.alloc((long long)kk * m);
+      const long long s2[2] = {kk, m}, i2[2] = {m, 1}, o2[2] = {m, 1};
+      e.copy(U, newcore, 2, s2, i2, o2, 1);
+      carry = V;
+      scale_cols_kernel<R><<<grid1d((long long)r0 * kk), 256, 0, e.st()>>>(V, r0, kk, sig);
+      e.post();
+      e.release(A);
+      e.release(U);
+      e.release(sig);
+    } else {
+      // M tall (r0 x m): Jacobi on its columns, M = U S V^H.
+      Cx<R>* A = e.alloc((long long)r0 * m);
+      const long long sz[2] = {m, r0}, ist[2] = {1, m}, ost[2] = {r0, 1};
+      e.copy(core, A, 2, sz, ist, ost, 0);  // column-major copy of M
+      Cx<R>* U = e.alloc((long long)r0 * m);
+      Cx<R>* V = e.alloc((long long)m * m);
+      double* sig = (double*)e.c->arena.alloc(sizeof(double) * m);
+      kk = e.svd(r0, m, A, U, sig, V, delta2, rmax, &cap);
+      newcore = e.alloc((long long)kk * m);
+      const long long s2[2] = {kk, m}, i2[2] = {m, 1}, o2[2] = {m, 1};
+      e.copy(V, newcore, 2, s2, i2, o2, 1);  // V^H rows
+      carry = U;
+      scale_cols_kernel<R><<<grid1d((long long)r0 * kk), 256, 0, e.st()>>>(U, r0, kk, sig);
+      e.post();
+      e.release(A);
+      e.release(V);
+      e.release(sig);
+    }
+    cap_any |= cap;
+    // core_{k-1} (rp, dp, r0) <- core_{k-1} * carry (r0 x kk)
+    const int rp = x->ranks[k - 1], dp = x->dims[k - 1];
+    Cx<R>* prev = e.alloc((long long)rp * dp * kk);
+    e.gemm(rp * dp, kk, r0, mref(x->core[k - 1], r0, 1), mref(carry, 1, r0), prev, kk, 1, 0, 0, 0,
+           1, 1, 1);
+    e.release(carry);
+    set_core(x, k, newcore);
+    set_core(x, k - 1, prev);
+    x->ranks[k] = kk;
+  }
+  return cap_any;
+}
+
+// Left-to-right Householder QR sweep (orthogonalisation step of rounding).
+template <typename R>
+void orthogonalize_left(Eng<R>& e, qtt_tt* x) {
+  const int L = x->L;
+  for (int k = 0; k < L - 1; ++k) {
+    const int r0 = x->ranks[k], d = x->dims[k], r1 = x->ranks[k + 1];
+    const int m = r0 * d, kq = std::min(m, r1);
+    Cx<R>* Q = e.alloc((long long)m * kq);
+    Cx<R>* Rm = e.alloc((long long)kq * r1);
+    e.qr(m, r1, x->core[k], r1, 1, 0, Q, Rm);
+    Cx<R>* nc = e.alloc((long long)m * kq);
+    const long long sz[2] = {m, kq}, ist[2] = {1, m}, ost[2] = {kq, 1};
+    e.copy(Q, nc, 2, sz, ist, ost);
+    const int d2 = x->dims[k + 1], r2 = x->ranks[k + 2];
+    Cx<R>* next = e.alloc((long long)kq * d2 * r2);
+    e.gemm(kq, d2 * r2, r1, mref(Rm, 1, kq), mref(x->core[k + 1], d2 * r2, 1), next, d2 * r2, 1,
+           0, 0, 0, 1, 1, 1);
+    e.release(Q);
+    e.release(Rm);
+    set_core(x, k, nc);
+    set_core(x, k + 1, next);
+    x->ranks[k + 1] = kq;
+  }
+}
+
+template <typename R>
+int round_full(Eng<R>& e, qtt_tt* x, double eps, int rmax) {
+  orthogonalize_left(e, x);
+  return round_right_to_left(e, x, eps, rmax);
+}
+
+// ------------------------------------------------------------------ sketched product
+
+long long prod_dims(const int* d, int a, int b) {  // prod d[a..b-1], saturating
+  long long p = 1;
+  for (int i = a; i < b; ++i) {
+    p *= d[i];
+    if (p > (1ll << 40)) return 1ll << 40;
+  }
+  return p;
+}
+
+// y = A x by successive randomized compression (see the oracle's
+// tto_apply_sketched for the statement): right-to-left random sketches Psi,
+// then left-to-right QR of the sketched carries. Output left-orthogonal.
+template <typename R>
+qtt_tt* apply_sketched(Eng<R>& e, const qtt_op* A, const qtt_tt* x, int ell, int apply_id) {
+  const int L = x->L;
+  QREQ(A->L == L, "operator and TT have different core counts");
+  for (int k = 0; k < L; ++k) QREQ(A->din[k] == x->dims[k], "operator input dims mismatch");
+  int lr[QTT_MAX_CORES + 1];
+  lr[0] = lr[L] = 1;
+  for (int b = 1; b < L; ++b) {
+    long long v = std::min<long long>(ell, (long long)A->ranks[b] * x->ranks[b]);
+    v = std::min(v, prod_dims(A->dout, 0, b));
+    v = std::min(v, prod_dims(A->dout, b, L));
+    lr[b] = (int)std::max<long long>(1, v);
+  }
+  // ---- right-to-left sketches: Psi[b] has layout (s, a, l) = (x->ranks[b], A->ranks[b], lr[b])
+  std::vector<Cx<R>*> psi(L + 1, nullptr);
+  psi[L] = e.alloc(1);
+  {
+    Cx<R> one = mk<R>(1, 0);
+    QCHECK(cudaMemcpyAsync(psi[L], &one, sizeof(one), cudaMemcpyHostToDevice, e.st()));
+  }
+  for (int k = L - 1; k >= 1; --k) {
+    const int S0 = x->ranks[k], S1 = x->ranks[k + 1], A0 = A->ranks[k], A1 = A->ranks[k + 1];
+    const int L0 = lr[k], L1 = lr[k + 1], Din = A->din[k], Dout = A->dout[k];
+    const bool dg = A->diag[k];
+    Cx<R>* Om = e.alloc((long long)L0 * Dout * L1);
+    sketch_kernel<R><<<grid1d((long long)L0 * Dout * L1), 256, 0, e.st()>>>(
+        Om, (long long)L0 * Dout * L1, e.c->seed, k, apply_id);
+    e.post();
+    // S1: XP[i][s0][a1 l1] = sum_s1 X[s0, i, s1] Psi[s1, (a1 l1)]
+    Cx<R>* XP = e.alloc((long long)Din * S0 * A1 * L1);
+    e.gemm(S0, A1 * L1, S1, mref(x->core[k], (long long)Din * S1, 1, S1), mref(psi[k + 1], (long long)A1 * L1, 1),
+           XP, (long long)A1 * L1, 1, (long long)S0 * A1 * L1, 0, 0, Din, 1, 1);
+    Cx<R>* Pk = e.alloc((long long)S0 * A0 * L0);
+    if (dg) {
+      // S2: U[s0][i][a1][l0] = sum_l1 XP[i][s0][a1][l1] Om[l0, i, l1]
+      Cx<R>* U = e.alloc((long long)S0 * Din * A1 * L0);
+      e.gemm(A1, L0, L1, mref(XP, L1, 1, (long long)A1 * L1, (long long)S0 * A1 * L1),
+             mref(Om, 1, (long long)Din * L1, 0, L1), U, L0, 1, (long long)Din * A1 * L0,
+             (long long)A1 * L0, 0, S0, Din, 1);
+      // S3: Psi_k[s0][a0][l0] = sum_{(i a1)} w[a0, (i a1)] U[s0][(i a1)][l0]
+      e.gemm(A0, L0, Din * A1, mref(A->core[k], (long long)Din * A1, 1),
+             mref(U, L0, 1, (long long)Din * A1 * L0), Pk, L0, 1, (long long)A0 * L0, 0, 0, S0, 1,
+             1);
+      e.release(U);
+    } else {
+      Cx<R>* U = e.alloc((long long)S0 * Dout * Din * A1 * L0);
+      e.gemm(A1, L0, L1, mref(XP, L1, 1, (long long)A1 * L1, 0, (long long)S0 * A1 * L1),
+             mref(Om, 1, (long long)Dout * L1, 0, L1, 0), U, L0, 1,
+             (long long)Dout * Din * A1 * L0, (long long)Din * A1 * L0, (long long)A1 * L0, S0,
+             Dout, Din);
+      e.gemm(A0, L0, Dout * Din * A1, mref(A->core[k], (long long)Dout * Din * A1, 1),
+             mref(U, L0, 1, (long long)Dout * Din * A1 * L0), Pk, L0, 1, (long long)A0 * L0, 0, 0,
+             S0, 1, 1);
+      e.release(U);
+    }
+    e.release(XP);
+    e.release(Om);
+    psi[k] = Pk;
+  }
+  // ---- left-to-right compression
+  qtt_tt* y = new_tt(e.c, L, A->dout);
+  Cx<R>* C = e.alloc(1);  // carry (R, S0, A0)
+  {
+    Cx<R> one = mk<R>(1, 0);
+    QCHECK(cudaMemcpyAsync(C, &one, sizeof(one), cudaMemcpyHostToDevice, e.st()));
+  }
+  int Rr = 1;
+  for (int k = 0; k < L; ++k) {
+    const int S0 = x->ranks[k], S1 = x->ranks[k + 1], A0 = A->ranks[k], A1 = A->ranks[k + 1];
+    const int Din = A->din[k], Dout = A->dout[k];
+    const bool dg = A->diag[k];
+    // CW[r, s0, (o, i), a1] = sum_a0 C[r, s0, a0] W[a0, ...]
+    const int wcols = dg ? Din * A1 : Dout * Din * A1;
+    Cx<R>* CW = e.alloc((long long)Rr * S0 * wcols);
+    e.gemm(Rr * S0, wcols, A0, mref(C, A0, 1), mref(A->core[k], wcols, 1), CW, wcols, 1, 0, 0, 0,
+           1, 1, 1);
+    // T[o][r][s1][a1]
+    Cx<R>* T = e.alloc((long long)Dout * Rr * S1 * A1);
+    if (dg) {
+      // T[i][r] (s1 x a1) = sum_s0 X[s0, i, s1] CW[r, s0, i, a1]
+      e.gemm(S1, A1, S0, mref(x->core[k], 1, (long long)Din * S1, S1, 0),
+             mref(CW, (long long)Din * A1, 1, A1, (long long)S0 * Din * A1), T, A1, 1,
+             (long long)Rr * S1 * A1, (long long)S1 * A1, 0, Din, Rr, 1);
+    } else {
+      for (int i = 0; i < Din; ++i) {
+        // T[o][r] += sum_s0 X[s0, i, s1] CW[r, s0, o, i, a1]
+        e.gemm(S1, A1, S0, mref((const Cx<R>*)x->core[k] + (long long)i * S1, 1, (long long)Din * S1),
+               mref((const Cx<R>*)CW + (long long)i * A1, (long long)Dout * Din * A1, 1,
+                    (long long)Din * A1, (long long)S0 * Dout * Din * A1),
+               T, A1, 1, (long long)Rr * S1 * A1, (long long)S1 * A1, 0, Dout, Rr, 1, Cplx{1, 0},
+               Cplx{i == 0 ? 0.0 : 1.0, 0});
+      }
+    }
+    e.release(CW);
+    e.release(C);
+    if (k == L - 1) {
+      // Y[r][o][0] = T[o][r]
+      Cx<R>* Y = e.alloc((long long)Rr * Dout);
+      const long long sz[2] = {Rr, Dout}, ist[2] = {1, Rr}, ost[2] = {Dout, 1};
+      e.copy(T, Y, 2, sz, ist, ost);
+      y->core[k] = Y;
+      y->ranks[k] = Rr;
+      e.release(T);
+      break;
+    }
+    const int L1 = lr[k + 1];
+    const int mz = Dout * Rr;
+    Cx<R>* Z = e.alloc((long long)mz * L1);
+    e.gemm(mz, L1, S1 * A1, mref(T, (long long)S1 * A1, 1), mref(psi[k + 1], L1, 1), Z, L1, 1, 0,
+           0, 0, 1, 1, 1);
+    e.release(psi[k + 1]);
+    psi[k + 1] = nullptr;
+    const int kq = std::min(mz, L1);
+    Cx<R>* Q = e.alloc((long long)mz * kq);
+    Cx<R>* Rm = e.alloc((long long)kq * L1);
+    e.qr(mz, L1, Z, L1, 1, 0, Q, Rm);
+    e.release(Z);
+    e.release(Rm);
+    // carry' (kq, S1, A1) = Q^H T
+    Cx<R>* Cn = e.alloc((long long)kq * S1 * A1);
+    e.gemm(kq, S1 * A1, mz, mref(Q, mz, 1, 0, 0, 0, 1), mref(T, (long long)S1 * A1, 1), Cn,
+           (long long)S1 * A1, 1, 0, 0, 0, 1, 1, 1);
+    // Y[r][o][m] = Q[(o R + r) + m mz]
+    Cx<R>* Y = e.alloc((long long)Rr * Dout * kq);
+    const long long sz[3] = {Rr, Dout, kq}, ist[3] = {1, Rr, mz},
+                    ost[3] = {(long long)Dout * kq, kq, 1};
+    e.copy(Q, Y, 3, sz, ist, ost);
+    e.release(Q);
+    e.release(T);
+    y->core[k] = Y;
+    y->ranks[k] = Rr;
+    C = Cn;
+    Rr = kq;
+  }
+  y->ranks[0] = 1;
+  y->ranks[L] = 1;
+  for (int b = 0; b <= L; ++b)
+    if (psi[b]) e.release(psi[b]);
+  return y;
+}
+
+// alpha a + beta b as a TT of rank r(a) + r(b) (Table 2, "x + y").
+template <typename R>
+qtt_tt* tt_add(Eng<R>& e, const qtt_tt* a, const qtt_tt* b, double alpha, double beta) {
+  const int L = a->L;
+  QREQ(b->L == L && L >= 2, "tt_add: core counts differ or L < 2");
+  for (int k = 0; k < L; ++k) QREQ(a->dims[k] == b->dims[k], "tt_add: dims differ");
+  qtt_tt* y = new_tt(e.c, L, a->dims);
+  for (int k = 1; k < L; ++k) y->ranks[k] = a->ranks[k] + b->ranks[k];
+  for (int k = 0; k < L; ++k) {
+    const int d = a->dims[k];
+    const int ra0 = a->ranks[k], ra1 = a->ranks[k + 1], rb0 = b->ranks[k], rb1 = b->ranks[k + 1];
+    const int y0 = y->ranks[k], y1 = y->ranks[k + 1];
+    Cx<R>* Y = e.alloc((long long)y0 * d * y1);
+    e.zero(Y, (long long)y0 * d * y1);
+    // place a at (0, :, 0), b at (row off, :, col off)
+    const int boff0 = (k == 0) ? 0 : ra0;
+    const int boff1 = (k == L - 1) ? 0 : ra1;
+    const double sa = (k == 0) ? alpha : 1.0, sb = (k == 0) ? beta : 1.0;
+    {
+      const long long sz[3] = {ra0, d, ra1}, ist[3] = {(long long)d * ra1, ra1, 1},
+                      ost[3] = {(long long)d * y1, y1, 1};
+      e.copy(a->core[k], Y, 3, sz, ist, ost, 0, sa);
+    }
+    {
+      const long long sz[3] = {rb0, d, rb1}, ist[3] = {(long long)d * rb1, rb1, 1},
+                      ost[3] = {(long long)d * y1, y1, 1};
+      e.copy(b->core[k], Y + (long long)boff0 * d * y1 + boff1, 3, sz, ist, ost, 0, sb);
+    }
+    y->core[k] = Y;
+  }
+  return y;
+}
+
+// <a, b> with FP64 transfer matrices.
+template <typename R>
+void tt_dot(Eng<R>& e, const qtt_tt* a, const qtt_tt* b, double* re, double* im) {
+  Eng<double> d(e.c);
+  const int L = a->L;
+  QREQ(b->L == L, "dot: core counts differ");
+  Cx<double>* E = d.alloc(1);
+  {
+    Cx<double> one = mk<double>(1, 0);
+    QCHECK(cudaMemcpyAsync(E, &one, sizeof(one), cudaMemcpyHostToDevice, e.st()));
+  }
+  for (int k = 0; k < L; ++k) {
+    QREQ(a->dims[k] == b->dims[k], "dot: dims differ");
+    const int ra = a->ranks[k], rb = b->ranks[k], pa = a->ranks[k + 1], pb = b->ranks[k + 1],
+              D = a->dims[k];
+    const Cx<double>* Ak = (const Cx<double>*)a->core[k];
+    const Cx<double>* Bk = (const Cx<double>*)b->core[k];
+    Cx<double>* tA = nullptr;
+    Cx<double>* tB = nullptr;
+    if (sizeof(R) != 8) {
+      tA = d.alloc(a->count(k));
+      tB = d.alloc(b->count(k));
+      convert_kernel<R, double><<<grid1d(a->count(k)), 256, 0, e.st()>>>(
+          (const Cx<R>*)a->core[k], tA, a->count(k));
+      e.post();
+      convert_kernel<R, double><<<grid1d(b->count(k)), 256, 0, e.st()>>>(
+          (const Cx<R>*)b->core[k], tB, b->count(k));
+      e.post();
+      Ak = tA;
+      Bk = tB;
+    }
+    // EB[ra][i pb] = E (ra x rb) B (rb x (i pb))
+    Cx<double>* EB = d.alloc((long long)ra * D * pb);
+    d.gemm(ra, D * pb, rb, mref(E, rb, 1), mref(Bk, (long long)D * pb, 1), EB, (long long)D * pb, 1,
+           0, 0, 0, 1, 1, 1);
+    // F (pa x pb) = A^H ((ra i) x pa)^H EB ((ra i) x pb)
+    Cx<double>* F = d.alloc((long long)pa * pb);
+    d.gemm(pa, pb, ra * D, mref(Ak, 1, pa, 0, 0, 0, 1), mref(EB, pb, 1), F, pb, 1, 0, 0, 0, 1, 1, 1);
+    d.release(EB);
+    d.release(E);
+    if (tA) d.release(tA);
+    if (tB) d.release(tB);
+    E = F;
+  }
+  double h[2];
+  QCHECK(cudaMemcpyAsync(e.c->pinned, E, 16, cudaMemcpyDeviceToHost, e.st()));
+  QCHECK(cudaStreamSynchronize(e.st()));
+  memcpy(h, e.c->pinned, 16);
+  d.release(E);
+  *re = h[0];
+  *im = h[1];
+}
+
+// Grid mean of (A x): first core full (1, Dout, Din, a1), binary cores raised.
+template <typename R>
+void op_mean(Eng<R>& e, const qtt_op* A, const qtt_tt* x, std::vector<double>& out) {
+  Eng<double> d(e.c);
+  const int L = x->L;
+  QREQ(A->L == L, "mean: core counts differ");
+  QREQ(!A->diag[0], "mean: first operator core must be full");
+  for (int k = 1; k < L; ++k) QREQ(A->diag[k], "mean: binary operator cores must be raised");
+  auto to64 = [&](const void* p, long long cnt) -> Cx<double>* {
+    Cx<double>* t = d.alloc(cnt);
+    if (sizeof(R) == 8) {
+      QCHECK(cudaMemcpyAsync(t, p, cnt * 16, cudaMemcpyDeviceToDevice, e.st()));
+    } else {
+      convert_kernel<R, double><<<grid1d(cnt), 256, 0, e.st()>>>((const Cx<R>*)p, t, cnt);
+      e.post();
+    }
+    return t;
+  };
+  const int Do = A->dout[0], Di = A->din[0], a1 = A->ranks[1], s1 = x->ranks[1];
+  Cx<double>* W0 = to64(A->core[0], A->count(0));
+  Cx<double>* X0 = to64(x->core[0], x->count(0));
+  // V[I][a1][s1] = sum_J W0[I, J, a1] X0[J, s1]
+  Cx<double>* V = d.alloc((long long)Do * a1 * s1);
+  d.gemm(a1, s1, Di, mref(W0, 1, a1, (long long)Di * a1), mref(X0, s1, 1), V, s1, 1,
+         (long long)a1 * s1, 0, 0, Do, 1, 1);
+  d.release(W0);
+  d.release(X0);
+  int Ar = a1, Sr = s1;
+  for (int k = 1; k < L; ++k) {
+    const int D = x->dims[k], B = A->ranks[k + 1], T = x->ranks[k + 1];
+    Cx<double>* Wk = to64(A->core[k], A->count(k));
+    Cx<double>* Xk = to64(x->core[k], x->count(k));
+    // VX[I][a][i t] = V[I][a][s] X[s, (i t)]
+    Cx<double>* VX = d.alloc((long long)Do * Ar * D * T);
+    d.gemm(Do * Ar, D * T, Sr, mref(V, Sr, 1), mref(Xk, (long long)D * T, 1), VX, (long long)D * T,
+           1, 0, 0, 0, 1, 1, 1);
+    // V'[I][b][t] = 1/2 sum_{(a i)} w[(a i), b] VX[I][(a i)][t]
+    Cx<double>* Vn = d.alloc((long long)Do * B * T);
+    d.gemm(B, T, Ar * D, mref(Wk, 1, B), mref(VX, T, 1, (long long)Ar * D * T), Vn, T, 1,
+           (long long)B * T, 0, 0, Do, 1, 1, Cplx{0.5, 0});
+    d.release(VX);
+    d.release(V);
+    d.release(Wk);
+    d.release(Xk);
+    V = Vn;
+    Ar = B;
+    Sr = T;
+  }
+  out.assign(2 * Do, 0.0);
+  std::vector<double> h(2 * Do);
+  QCHECK(cudaMemcpyAsync(e.c->pinned, V, 16 * Do, cudaMemcpyDeviceToHost, e.st()));
+  QCHECK(cudaStreamSynchronize(e.st()));
+  memcpy(h.data(), e.c->pinned, 16 * Do);
+  d.release(V);
+  out = h;
+}
+
+// ------------------------------------------------------------------ TT-SVD (preprocessing, FP64)
+
+// TT-SVD of a dense complex tensor T (dims[0..L-1], row-major) right to left:
+// at core j the unfolding M (P x c), c = d_j r_{j+1}, gives the Gram matrix
+// G = M^H M; its eigenvectors (one-sided Jacobi of G) V and eigenvalues
+// lambda = sigma^2 decide the rank by the tail rule, core j = V[:, :k]^H and
+// the carry is M V[:, :k]. T is consumed (overwritten).
+std::vector<Cx<double>*> tt_svd_device(Eng<double>& e, Cx<double>* T, const std::vector<int>& dims,
+                                       double eps, int rmax, std::vector<int>& ranks) {
+  const int L = (int)dims.size();
+  std::vector<Cx<double>*> cores(L, nullptr);
+  ranks.assign(L + 1, 1);
+  Cx<double>* M = T;
+  bool own_M = false;
+  double delta2 = 0;
+  for (int j = L - 1; j >= 1; --j) {
+    const int c = dims[j] * ranks[j + 1];
+    const long long P = prod_dims(dims.data(), 0, j);
+    QREQ(P < (1ll << 31), "TT-SVD unfolding too large");
+    Cx<double>* G = e.alloc((long long)c * c);
+    const int ks = (int)std::min<long long>(std::max<long long>(1, P / 8192), 4096 / std::max(1, (c / 64 + 1) * (c / 64 + 1)));
+    // G column-major (the Jacobi kernel's layout): G[a + b c] = sum_p conj(M[p, a]) M[p, b]
+    e.gemm(c, c, (int)P, mref(M, 1, c, 0, 0, 0, 1), mref(M, c, 1), G, 1, c, 0, 0, 0, 1, 1, 1,
+           Cplx{1, 0}, Cplx{0, 0}, std::max(1, ks));
+    if (j == L - 1) {
+      // ||T||^2 = trace(G)
+      Cx<double>* dg = e.alloc(c);
+      const long long sz[1] = {c}, ist[1] = {(long long)c + 1}, ost[1] = {1};
+      e.copy(G, dg, 1, sz, ist, ost);
+      // trace = sum Re(G_ii); G_ii >= 0 so sum sqrt(|G_ii|^2)
+      std::vector<double> h(2 * c);
+      QCHECK(cudaMemcpyAsync(h.data(), dg, 16 * (size_t)c, cudaMemcpyDeviceToHost, e.st()));
+      QCHECK(cudaStreamSynchronize(e.st()));
+      double t = 0;
+      for (int i = 0; i < c; ++i) t += h[2 * i];
+      delta2 = L > 1 ? eps * eps * t / (double)(L - 1) : 0.0;
+      e.release(dg);
+    }
+    Cx<double>* U = e.alloc((long long)c * c);
+    Cx<double>* V = e.alloc((long long)c * c);
+    double* sig = (double*)e.c->arena.alloc(sizeof(double) * c);
+    int cap = 0;
+    const int kk = e.svd(c, c, G, U, sig, V, delta2, rmax, &cap, true);
+    e.release(G);
+    e.release(U);
+    e.release(sig);
+    // core j = V[:, :kk]^H  (kk x c) = (kk, d_j, r_{j+1})
+    Cx<double>* core = e.alloc((long long)kk * c);
+    const long long sz[2] = {kk, c}, ist[2] = {c, 1}, ost[2] = {c, 1};
+    e.copy(V, core, 2, sz, ist, ost, 1);
+    cores[j] = core;
+    ranks[j] = kk;
+    // carry M V[:, :kk] (P x kk)
+    Cx<double>* Mn = e.alloc(P * kk);
+    e.gemm((int)P, kk, c, mref(M, c, 1), mref(V, 1, c), Mn, kk, 1, 0, 0, 0, 1, 1, 1);
+    e.release(V);
+    if (own_M) e.release(M);
+    M = Mn;
+    own_M = true;
+  }
+  if (!own_M) {
+    Cx<double>* c0 = e.alloc((long long)dims[0] * ranks[1]);
+    QCHECK(cudaMemcpyAsync(c0, M, 16 * (size_t)dims[0] * ranks[1], cudaMemcpyDeviceToDevice,
+                           e.st()));
+    M = c0;
+  }
+  cores[0] = M;
+  return cores;
+}
+
+// Copy FP64 device cores into an op of the context's precision.
+template <typename R>
+void *to_prec(Eng<R>& e, Cx<double>* p, long long cnt) {
+  if (sizeof(R) == 8) return p;
+  Cx<R>* q = e.alloc(cnt);
+  convert_kernel<double, R><<<grid1d(cnt), 256, 0, e.st()>>>(p, q, cnt);
+  e.post();
+  e.release(p);
+  return q;
+}
+
+// ------------------------------------------------------------------ C0 and stiffness
+
+void lame_of(double E, double nu, double& lam, double& mu) {
+  lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+  mu = E / (2.0 * (1.0 + nu));
+}
+
+void voigt_stiffness(double lam, double mu, double* C) {
+  for (int i = 0; i < 36; ++i) C[i] = 0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) C[i * 6 + j] = lam + (i == j ? 2.0 * mu : 0.0);
+  for (int i = 3; i < 6; ++i) C[i * 6 + i] = mu;
+}
+
+}  // namespace
+
+// ================================================================== C ABI
+
+#define API_BEGIN(ctx)      \
+  qtt_ctx* c_ = (ctx);      \
+  try {
+#define API_END                                      \
+  }                                                  \
+  catch (const QttError& ex) {                       \
+    if (c_) c_->err = ex.what();                     \
+    return ex.code;                                  \
+  }                                                  \
+  catch (const std::exception& ex) {                 \
+    if (c_) c_->err = ex.what();                     \
+    return QTT_EINVAL;                               \
+  }
+
+#define DISPATCH(ctx, FN, ...)                               \
+  ((ctx)->prec == QTT_FP64 ? FN<double>(__VA_ARGS__) : FN<float>(__VA_ARGS__))
+
+namespace {
+
+template <typename R>
+qtt_tt* op_apply_impl(qtt_ctx* c, const qtt_op* op, const qtt_tt* in, double eps, int rmax,
+                      int oversample, int apply_id, int* cap) {
+  Eng<R> e(c);
+  qtt_tt* y = apply_sketched<R>(e, op, in, rmax + oversample, apply_id);
+  *cap = round_right_to_left<R>(e, y, eps, rmax);
+  return y;
+}
+
+template <typename R>
+int round_impl(qtt_ctx* c, qtt_tt* x, double eps, int rmax) {
+  Eng<R> e(c);
+  return round_full<R>(e, x, eps, rmax);
+}
+
+template <typename R>
+void dot_impl(qtt_ctx* c, const qtt_tt* a, const qtt_tt* b, double* re, double* im) {
+  Eng<R> e(c);
+  tt_dot<R>(e, a, b, re, im);
+}
+
+template <typename R>
+void mean_impl(qtt_ctx* c, const qtt_op* op, const qtt_tt* x, std::vector<double>& out) {
+  Eng<R> e(c);
+  op_mean<R>(e, op, x, out);
+}
+
+// Build an operator from FP64 device cores.
+template <typename R>
+qtt_op* op_from_fp64(qtt_ctx* c, std::vector<Cx<double>*>& cores, const std::vector<int>& ranks,
+                     const std::vector<int>& dout, const std::vector<int>& din,
+                     const std::vector<int>& diag) {
+  Eng<R> e(c);
+  qtt_op* o = new qtt_op();
+  o->ctx = c;
+  o->L = (int)cores.size();
+  for (int k = 0; k < o->L; ++k) {
+    o->dout[k] = dout[k];
+    o->din[k] = din[k];
+    o->diag[k] = diag[k];
+  }
+  for (int k = 0; k <= o->L; ++k) o->ranks[k] = ranks[k];
+  for (int k = 0; k < o->L; ++k) o->core[k] = to_prec<R>(e, cores[k], o->count(k));
+  return o;
+}
+
+qtt_op* build_sfft(qtt_ctx* c, int n, int adjoint, double eps) {
+  QREQ(n >= 1 && 3 * n + 1 <= QTT_MAX_CORES, "sfft: n out of range");
+  Eng<double> e(c);
+  const long long N = 1ll << n;
+  Cx<double>* T = e.alloc(N * N);
+  sfft_tensor_kernel<<<grid1d(N * N), 256, 0, e.st()>>>((double*)T, n);
+  e.post();
+  std::vector<int> dims(n, 4), ranks;
+  std::vector<Cx<double>*> ax = tt_svd_device(e, T, dims, eps, 1 << 30, ranks);
+  e.release(T);
+  // assemble: Voigt identity core, then the axis MPO three times
+  const int L = 3 * n + 1;
+  std::vector<Cx<double>*> cores(L);
+  std::vector<int> R(L + 1, 1), dout(L, 2), din(L, 2), diag(L, 0);
+  dout[0] = din[0] = 6;
+  Cx<double>* I6 = e.alloc(36);
+  {
+    std::vector<double> h(72, 0.0);
+    for (int i = 0; i < 6; ++i) h[2 * (i * 6 + i)] = 1.0;
+    QCHECK(cudaMemcpyAsync(I6, h.data(), 72 * 8, cudaMemcpyHostToDevice, e.st()));
+    QCHECK(cudaStreamSynchronize(e.st()));
+  }
+  cores[0] = I6;
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < n; ++b) {
+      const int k = 1 + a * n + b;
+      const long long cnt = (long long)ranks[b] * 4 * ranks[b + 1];
+      Cx<double>* p = e.alloc(cnt);
+      if (!adjoint) {
+        QCHECK(cudaMemcpyAsync(p, ax[b], cnt * 16, cudaMemcpyDeviceToDevice, e.st()));
+      } else {
+        // W^H core: (f, o, i, f') <- conj(W(f, i, o, f'))
+        const long long sz[4] = {ranks[b], 2, 2, ranks[b + 1]};
+        const long long ist[4] = {4ll * ranks[b + 1], ranks[b + 1], 2ll * ranks[b + 1], 1};
+        const long long ost[4] = {4ll * ranks[b + 1], 2ll * ranks[b + 1], ranks[b + 1], 1};
+        e.copy(ax[b], p, 4, sz, ist, ost, 1);
+      }
+      cores[k] = p;
+      R[k] = ranks[b];
+      R[k + 1] = ranks[b + 1];
+    }
+  for (auto p : ax) e.release(p);
+  qtt_op* o = c->prec == QTT_FP64 ? op_from_fp64<double>(c, cores, R, dout, din, diag)
+                                  : op_from_fp64<float>(c, cores, R, dout, din, diag);
+  o->n = n;
+  return o;
+}
+
+// Raised operator from a dense (36, 2^bits) FP64 complex field with
+// broadcast axes (axis a contributes nbits[a] cores from the field or n
+// identity cores when broadcast).
+qtt_op* raised_from_field(qtt_ctx* c, Cx<double>* F, int n, const int bcast[3], double eps,
+                          int rmax) {
+  Eng<double> e(c);
+  int bits = 0;
+  for (int a = 0; a < 3; ++a) bits += bcast[a] ? 0 : n;
+  std::vector<int> dims(1 + bits, 2), ranks;
+  dims[0] = 36;
+  std::vector<Cx<double>*> tc = tt_svd_device(e, F, dims, eps, rmax, ranks);
+  const int L = 3 * n + 1;
+  std::vector<Cx<double>*> cores(L);
+  std::vector<int> R(L + 1, 1), dout(L, 2), din(L, 2), diag(L, 1);
+  dout[0] = din[0] = 6;
+  diag[0] = 0;
+  cores[0] = tc[0];
+  R[1] = ranks[1];
+  int src = 1, k = 1;
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < n; ++b, ++k) {
+      if (bcast[a]) {
+        const int r = R[k];
+        Cx<double>* I = e.alloc((long long)r * 2 * r);
+        e.zero(I, (long long)r * 2 * r);
+        // C[alpha, i, alpha] = 1
+        std::vector<double> one = {1.0, 0.0};
+        Cx<double>* d1 = e.alloc(1);
+        QCHECK(cudaMemcpyAsync(d1, one.data(), 16, cudaMemcpyHostToDevice, e.st()));
+        const long long sz[2] = {r, 2}, ist[2] = {0, 0}, ost[2] = {2ll * r + 1, r};
+        e.copy(d1, I, 2, sz, ist, ost);
+        QCHECK(cudaStreamSynchronize(e.st()));
+        e.release(d1);
+        cores[k] = I;
+        R[k + 1] = r;
+      } else {
+        cores[k] = tc[src];
+        R[k + 1] = ranks[src + 1];
+        ++src;
+      }
+    }
+  return c->prec == QTT_FP64 ? op_from_fp64<double>(c, cores, R, dout, din, diag)
+                             : op_from_fp64<float>(c, cores, R, dout, din, diag);
+}
+
+qtt_op* build_gamma(qtt_ctx* c, int n, double lam0, double mu0, int scheme, double eps, int rmax) {
+  QREQ(scheme == 0, "only the Direct scheme (0) is implemented");
+  QREQ(n >= 1 && n <= 8, "gamma: n must be in 1..8");
+  QREQ(mu0 > 0 && lam0 + 2 * mu0 > 0, "gamma: reference medium not positive definite");
+  Eng<double> e(c);
+  const long long N3 = 1ll << (3 * n);
+  Cx<double>* F = e.alloc(36 * N3);
+  gamma_field_kernel<<<grid1d(N3), 256, 0, e.st()>>>(F, n, lam0, mu0);
+  e.post();
+  const int bc[3] = {0, 0, 0};
+  qtt_op* o = raised_from_field(c, F, n, bc, eps, rmax);
+  e.release(F);
+  o->n = n;
+  o->has_c0 = 1;
+  o->lame0[0] = lam0;
+  o->lame0[1] = mu0;
+  voigt_stiffness(lam0, mu0, o->C0);
+  return o;
+}
+
+qtt_op* cached_sfft(qtt_ctx* c, int n, int adjoint) {
+  auto key = std::make_pair(n, adjoint);
+  auto it = c->sfft_cache.find(key);
+  if (it != c->sfft_cache.end()) return it->second;
+  qtt_op* o = build_sfft(c, n, adjoint, 1e-14);
+  c->sfft_cache[key] = o;
+  return o;
+}
+
+qtt_op* cached_gamma(qtt_ctx* c, int n, double lam0, double mu0, int scheme, double eps, int rmax) {
+  auto key = std::make_tuple(n, lam0, mu0, scheme, eps, rmax);
+  auto it = c->gamma_cache.find(key);
+  if (it != c->gamma_cache.end()) return it->second;
+  qtt_op* o = build_gamma(c, n, lam0, mu0, scheme, eps, rmax);
+  c->gamma_cache[key] = o;
+  return o;
+}
+
+// E field as a rank-1 controlled QTT: Voigt core E sqrt(2)^(3n), binary
+// cores (1, 1)/sqrt(2).
+template <typename R>
+qtt_tt* e_field(qtt_ctx* c, int L, const int* dims, const double* Ev) {
+  Eng<R> e(c);
+  qtt_tt* t = new_tt(c, L, dims);
+  for (int k = 0; k <= L; ++k) t->ranks[k] = 1;
+  double scale = 1.0;
+  for (int k = 1; k < L; ++k) scale *= std::sqrt((double)dims[k]);
+  for (int k = 0; k < L; ++k) {
+    std::vector<Cx<R>> h(dims[k]);
+    for (int i = 0; i < dims[k]; ++i)
+      h[i] = (k == 0) ? mk<R>((R)(Ev[i] * scale), 0) : mk<R>((R)(1.0 / std::sqrt((double)dims[k])), 0);
+    t->core[k] = e.alloc(dims[k]);
+    QCHECK(cudaMemcpyAsync(t->core[k], h.data(), sizeof(Cx<R>) * dims[k], cudaMemcpyHostToDevice,
+                           e.st()));
+    QCHECK(cudaStreamSynchronize(e.st()));
+  }
+  return t;
+}
+
+template <typename R>
+int max_rank(const qtt_tt* t) {
+  int m = 1;
+  for (int k = 0; k <= t->L; ++k) m = std::max(m, t->ranks[k]);
+  return m;
+}
+
+// Alg. 2, one load case.
+template <typename R>
+int solve_impl(qtt_ctx* c, const qtt_op* dC, const qtt_op* S, const qtt_op* Sh, const qtt_op* G,
+               const double* C0, const double* Ev, const qtt_solve_params* p, double* sig,
+               qtt_solve_info* info, int apply_base) {
+  Eng<R> e(c);
+  const auto t0 = std::chrono::steady_clock::now();
+  const int L = dC->L;
+  qtt_tt* Ett = e_field<R>(c, L, dC->dout, Ev);
+  double nE2 = 0;
+  for (int i = 0; i < 6; ++i) nE2 += Ev[i] * Ev[i];
+  double cells = 1.0;
+  for (int k = 1; k < L; ++k) cells *= dC->dout[k];
+  const double normE = std::sqrt(nE2 * cells);
+  QREQ(normE > 0, "ls_solve: E = 0");
+  qtt_tt* x = clone_tt<R>(e, Ett);
+  const int ell = p->rmax + p->oversample;
+  int cap = 0, maxr = 1, it = 0, status = QTT_OK;
+  double rel = 0;
+  for (it = 1; it <= p->max_iter; ++it) {
+    const int t0id = apply_base + 4 * (it - 1);
+    qtt_tt* tau = apply_sketched<R>(e, dC, x, ell, t0id);
+    cap |= round_right_to_left<R>(e, tau, p->eps_tt, p->rmax);
+    qtt_tt* tauh = apply_sketched<R>(e, S, tau, ell, t0id + 1);
+    cap |= round_right_to_left<R>(e, tauh, p->eps_tt, p->rmax);
+    qtt_tt* epsh = apply_sketched<R>(e, G, tauh, ell, t0id + 2);
+    cap |= round_right_to_left<R>(e, epsh, p->eps_tt, p->rmax);
+    qtt_tt* yv = apply_sketched<R>(e, Sh, epsh, ell, t0id + 3);
+    qtt_tt* xn = tt_add<R>(e, Ett, yv, 1.0, -1.0);
+    cap |= round_full<R>(e, xn, p->eps_tt, p->rmax);
+    maxr = std::max({maxr, max_rank<R>(tau), max_rank<R>(tauh), max_rank<R>(epsh), max_rank<R>(xn)});
+    // ||xn - x||^2 = ||xn||^2 + ||x||^2 - 2 Re <xn, x>
+    double a2r, a2i, b2r, b2i, abr, abi;
+    tt_dot<R>(e, xn, xn, &a2r, &a2i);
+    tt_dot<R>(e, x, x, &b2r, &b2i);
+    tt_dot<R>(e, xn, x, &abr, &abi);
+    const double d2 = std::max(0.0, a2r + b2r - 2.0 * abr);
+    rel = std::sqrt(d2) / normE;
+    free_tt(tau);
+    free_tt(tauh);
+    free_tt(epsh);
+    free_tt(yv);
+    free_tt(x);
+    x = xn;
+    if (!std::isfinite(rel)) {
+      free_tt(x);
+      free_tt(Ett);
+      throw QttError(QTT_ENAN, "ls_solve: non-finite residual");
+    }
+    if (rel < p->tol) break;
+  }
+  if (it > p->max_iter) {
+    it = p->max_iter;
+    status = QTT_WNOCONV;
+  }
+  std::vector<double> m;
+  op_mean<R>(e, dC, x, m);
+  double leak = 0;
+  for (int i = 0; i < 6; ++i) {
+    double c0e = 0;
+    for (int j = 0; j < 6; ++j) c0e += C0[i * 6 + j] * Ev[j];
+    sig[2 * i] = c0e + m[2 * i];
+    sig[2 * i + 1] = m[2 * i + 1];
+    leak = std::max(leak, std::fabs(m[2 * i + 1]));
+  }
+  free_tt(x);
+  free_tt(Ett);
+  if (info) {
+    info->iters = it;
+    info->residual = rel;
+    info->max_rank = maxr;
+    info->rank_cap_hit = cap;
+    info->imag_leak = leak;
+    info->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  if (status == QTT_OK && cap) status = QTT_WRANKCAP;
+  return status;
+}
+
+}  // namespace
+
+extern "C" {
+
+int qtt_ctx_create(qtt_ctx_t* out, int device, void* cuda_stream, int precision, void* workspace,
+                   size_t workspace_bytes, uint64_t seed) {
+  if (!out) return QTT_EINVAL;
+  *out = nullptr;
+  if (precision != QTT_FP64 && precision != QTT_FP32) return QTT_EINVAL;
+  if (!workspace || workspace_bytes < (1u << 20) || ((uintptr_t)workspace & 255)) return QTT_EINVAL;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return QTT_EINVAL;
+  if (cudaSetDevice(device) != cudaSuccess) return QTT_ECUDA;
+  qtt_ctx* c = new qtt_ctx();
+  c->device = device;
+  c->stream = (cudaStream_t)cuda_stream;
+  c->prec = precision;
+  c->seed = seed;
+  c->arena.init(workspace, workspace_bytes);
+  if (cudaMallocHost(&c->pinned, 1 << 16) != cudaSuccess) {
+    delete c;
+    return QTT_ECUDA;
+  }
+  *out = c;
+  return QTT_OK;
+}
+
+void qtt_ctx_destroy(qtt_ctx_t c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  prof_flush(c);
+  for (auto& kv : c->sfft_cache) free_op(kv.second);
+  for (auto& kv : c->gamma_cache) free_op(kv.second);
+  if (c->pinned) cudaFreeHost(c->pinned);
+  delete c;
+}
+
+const char* qtt_last_error(qtt_ctx_t c) { return c ? c->err.c_str() : "null context"; }
+
+int qtt_ctx_set_profiling(qtt_ctx_t c, int on) {
+  if (!c) return QTT_EINVAL;
+  if (!on) prof_flush(c);
+  c->profiling = on ? 1 : 0;
+  return QTT_OK;
+}
+
+int qtt_ctx_profile(qtt_ctx_t c, int reset, double* out) {
+  if (!c || !out) return QTT_EINVAL;
+  prof_flush(c);
+  for (int i = 0; i < 3; ++i) {
+    out[3 * i] = (double)c->prof_n[i];
+    out[3 * i + 1] = c->prof_ms[i];
+    out[3 * i + 2] = c->prof_flops[i];
+  }
+  if (reset)
+    for (int i = 0; i < 3; ++i) c->prof_n[i] = 0, c->prof_ms[i] = 0, c->prof_flops[i] = 0;
+  return QTT_OK;
+}
+size_t qtt_ctx_bytes_in_use(qtt_ctx_t c) { return c ? c->arena.used : 0; }
+size_t qtt_ctx_bytes_peak(qtt_ctx_t c) { return c ? c->arena.peak : 0; }
+uint64_t qtt_ctx_launches(qtt_ctx_t c) { return c ? c->launches : 0; }
+
+int qtt_tt_create(qtt_ctx_t ctx, int L, const int* dims, const int* ranks, const double* cores,
+                  qtt_tt_t* out) {
+  API_BEGIN(ctx)
+  QREQ(ctx && out && dims && ranks && cores, "qtt_tt_create: null argument");
+  QREQ(ranks[0] == 1 && ranks[L] == 1, "qtt_tt_create: boundary ranks must be 1");
+  qtt_tt* t = new_tt(ctx, L, dims);
+  long long off = 0;
+  const size_t es = ctx->esize();
+  for (int k = 0; k <= L; ++k) {
+    QREQ(ranks[k] >= 1, "qtt_tt_create: ranks must be >= 1");
+    t->ranks[k] = ranks[k];
+  }
+  for (int k = 0; k < L; ++k) {
+    QREQ(dims[k] >= 1, "qtt_tt_create: dims must be >= 1");
+    const long long cnt = t->count(k);
+    t->core[k] = ctx->arena.alloc(cnt * es);
+    if (ctx->prec == QTT_FP64) {
+      QCHECK(cudaMemcpyAsync(t->core[k], cores + 2 * off, cnt * 16, cudaMemcpyHostToDevice,
+                             ctx->stream));
+    } else {
+      std::vector<float> h(2 * cnt);
+      for (long long i = 0; i < 2 * cnt; ++i) h[i] = (float)cores[2 * off + i];
+      QCHECK(cudaMemcpyAsync(t->core[k], h.data(), cnt * 8, cudaMemcpyHostToDevice, ctx->stream));
+      QCHECK(cudaStreamSynchronize(ctx->stream));
+    }
+    off += cnt;
+  }
+  QCHECK(cudaStreamSynchronize(ctx->stream));
+  *out = t;
+  return QTT_OK;
+  API_END
+}
+
+int qtt_tt_from_dense(qtt_ctx_t ctx, int L, const int* dims, const double* dense, double eps,
+                      int rmax, qtt_tt_t* out) {
+  API_BEGIN(ctx)
+  QREQ(ctx && dims && dense && out, "qtt_tt_from_dense: null argument");
+  QREQ(L >= 1 && L <= QTT_MAX_CORES && eps >= 0 && rmax >= 1, "qtt_tt_from_dense: bad arguments");
+  long long tot = 1;
+  for (int k = 0; k < L; ++k) {
+    QREQ(dims[k] >= 1, "qtt_tt_from_dense: dims must be >= 1");
+    tot *= dims[k];
+    QREQ(tot < (1ll << 34), "qtt_tt_from_dense: tensor too large");
+  }
+  Eng<double> e(ctx);
+  Cx<double>* T = e.alloc(tot);
+  QCHECK(cudaMemcpyAsync(T, dense, (size_t)tot * 16, cudaMemcpyHostToDevice, ctx->stream));
+  std::vector<int> dv(dims, dims + L), ranks;
+  std::vector<Cx<double>*> cores = tt_svd_device(e, T, dv, eps, rmax, ranks);
+  e.release(T);
+  qtt_tt* t = new_tt(ctx, L, dims);
+  for (int k = 0; k <= L; ++k) t->ranks[k] = ranks[k];
+  if (ctx->prec == QTT_FP64) {
+    for (int k = 0; k < L; ++k) t->core[k] = cores[k];
+  } else {
+    Eng<float> f(ctx);
+    for (int k = 0; k < L; ++k) t->core[k] = to_prec<float>(f, cores[k], t->count(k));
+  }
+  QCHECK(cudaStreamSynchronize(ctx->stream));
+  *out = t;
+  return QTT_OK;
+  API_END
+}
+
+int qtt_tt_shape(qtt_tt_t t, int* L, int* dims, int* ranks) {
+  if (!t || !L) return QTT_EINVAL;
+  *L = t->L;
+  for (int k = 0; k < t->L; ++k)
+    if (dims) dims[k] = t->dims[k];
+  for (int k = 0; k <= t->L; ++k)
+    if (ranks) ranks[k] = t->ranks[k];
+  return QTT_OK;
+}
+
+int qtt_tt_export(qtt_ctx_t ctx, qtt_tt_t t, double* cores) {
+  API_BEGIN(ctx)
+  QREQ(ctx && t && cores, "qtt_tt_export: null argument");
+  long long off = 0;
+  for (int k = 0; k < t->L; ++k) {
+    const long long cnt = t->count(k);
+    if (ctx->prec == QTT_FP64) {
+      QCHECK(cudaMemcpyAsync(cores + 2 * off, t->core[k], cnt * 16, cudaMemcpyDeviceToHost,
+                             ctx->stream));
+    } else {
+      std::vector<float> h(2 * cnt);
+      QCHECK(cudaMemcpyAsync(h.data(), t->core[k], cnt * 8, cudaMemcpyDeviceToHost, ctx->stream));
+      QCHECK(cudaStreamSynchronize(ctx->stream));
+      for (long long i = 0; i < 2 * cnt; ++i) cores[2 * off + i] = h[i];
+    }
+    off += cnt;
+  }
+  QCHECK(cudaStreamSynchronize(ctx->stream));
+  return QTT_OK;
+  API_END
+}
+
+void qtt_tt_free(qtt_tt_t t) { free_tt(t); }
+
+int qtt_op_create(qtt_ctx_t ctx, int L, const int* d_out, const int* d_in, const int* ranks,
+                  const int* diag, const double* cores, qtt_op_t* out) {
+  API_BEGIN(ctx)
+  QREQ(ctx && out && d_out && d_in && ranks && diag && cores, "qtt_op_create: null argument");
+  QREQ(L >= 1 && L <= QTT_MAX_CORES, "qtt_op_create: L out of range");
+  QREQ(ranks[0] == 1 && ranks[L] == 1, "qtt_op_create: boundary ranks must be 1");
+  qtt_op* o = new qtt_op();
+  o->ctx = ctx;
+  o->L = L;
+  for (int k = 0; k <= L; ++k) o->ranks[k] = ranks[k];
+  for (int k = 0; k < L; ++k) {
+    o->dout[k] = d_out[k];
+    o->din[k] = d_in[k];
+    o->diag[k] = diag[k] ? 1 : 0;
+    if (o->diag[k] && d_out[k] != d_in[k]) {
+      delete o;
+      throw QttError(QTT_EINVAL, "qtt_op_create: diagonal core needs d_out == d_in");
+    }
+  }
+  o->n = (L - 1) / 3;
+  long long off = 0;
+  const size_t es = ctx->esize();
+  for (int k = 0; k < L; ++k) {
+    const long long cnt = o->count(k);
+    o->core[k] = ctx->arena.alloc(cnt * es);
+    if (ctx->prec == QTT_FP64) {
+      QCHECK(cudaMemcpyAsync(o->core[k], cores + 2 * off, cnt * 16, cudaMemcpyHostToDevice,
+                             ctx->stream));
+    } else {
+      std::vector<float> h(2 * cnt);
+      for (long long i = 0; i < 2 * cnt; ++i) h[i] = (float)cores[2 * off + i];
+      QCHECK(cudaMemcpyAsync(o->core[k], h.data(), cnt * 8, cudaMemcpyHostToDevice, ctx->stream));
+      QCHECK(cudaStreamSynchronize(ctx->stream));
+    }
+    off += cnt;
+  }
+  QCHECK(cudaStreamSynchronize(ctx->stream));
+  *out = o;
+  return QTT_OK;
+  API_END
+}
+
+int qtt_op_shape(qtt_op_t o, int* L, int* d_out, int* d_in, int* ranks, int* diag) {
+  if (!o || !L) return QTT_EINVAL;
+  *L = o->L;
+  for (int k = 0; k < o->L; ++k) {
+    if (d_out) d_out[k] = o->dout[k];
+    if (d_in) d_in[k] = o->din[k];
+    if (diag) diag[k] = o->diag[k];
+  }
+  for (int k = 0; k <= o->L; ++k)
+    if (ranks) ranks[k] = o->ranks[k];
+  return QTT_OK;
+}
+
+int qtt_op_export(qtt_ctx_t ctx, qtt_op_t o, double* cores) {
+  API_BEGIN(ctx)
+  QREQ(ctx && o && cores, "qtt_op_export: null argument");
+  long long off = 0;
+  for (int k = 0; k < o->L; ++k) {
+    const long long cnt = o->count(k);
+    if (ctx->prec == QTT_FP64) {
+      QCHECK(cudaMemcpyAsync(cores + 2 * off, o->core[k], cnt * 16, cudaMemcpyDeviceToHost,
+                             ctx->stream));
+    } else {
+      std::vector<float> h(2 * cnt);
+      QCHECK(cudaMemcpyAsync(h.data(), o->core[k], cnt * 8, cudaMemcpyDeviceToHost, ctx->stream));
+      QCHECK(cudaStreamSynchronize(ctx->stream));
+      for (long long i = 0; i < 2 * cnt; ++i) cores[2 * off + i] = h[i];
+    }
+    off += cnt;
+  }
+  QCHECK(cudaStreamSynchronize(ctx->stream));
+  return QTT_OK;
+  API_END
+}
+
+void qtt_op_free(qtt_op_t o) {
+  if (!o) return;
+  // cached operators are owned by their context
+  for (auto& kv : o->ctx->sfft_cache)
+    if (kv.second == o) return;
+  for (auto& kv : o->ctx->gamma_cache)
+    if (kv.second == o) return;
+  free_op(o);
+}
+
+int qtt_from_phase_field(qtt_ctx_t ctx, const uint8_t* phase, const int shape[3], int n,
+                         int nphase, const double* E, const double* nu, const double* lame0,
+                         double eps_tt, int rmax, qtt_op_t* dC) {
+  API_BEGIN(ctx)
+  QREQ(ctx && phase && shape && E && nu && dC, "qtt_from_phase_field: null argument");
+  QREQ(n >= 1 && 3 * n + 1 <= QTT_MAX_CORES, "qtt_from_phase_field: n out of range");
+  QREQ(nphase >= 1 && nphase <= 255, "qtt_from_phase_field: nphase out of range");
+  const long long N = 1ll << n;
+  int bc[3];
+  long long cells = 1;
+  for (int a = 0; a < 3; ++a) {
+    QREQ(shape[a] == 1 || shape[a] == N, "qtt_from_phase_field: extents must be 1 or 2^n");
+    bc[a] = shape[a] == 1;
+    cells *= shape[a];
+  }
+  double lam0, mu0;
+  if (lame0) {
+    lam0 = lame0[0];
+    mu0 = lame0[1];
+  } else {
+    double lmin = 1e300, lmax = -1e300, mmin = 1e300, mmax = -1e300;
+    for (int p = 0; p < nphase; ++p) {
+      double l, m;
+      lame_of(E[p], nu[p], l, m);
+      lmin = std::min(lmin, l);
+      lmax = std::max(lmax, l);
+      mmin = std::min(mmin, m);
+      mmax = std::max(mmax, m);
+    }
+    lam0 = 0.5 * (lmin + lmax);
+    mu0 = 0.5 * (mmin + mmax);
+  }
+  double C0[36];
+  voigt_stiffness(lam0, mu0, C0);
+  std::vector<double> dCh(36 * nphase);
+  for (int p = 0; p < nphase; ++p) {
+    double l, m, Cp[36];
+    lame_of(E[p], nu[p], l, m);
+    voigt_stiffness(l, m, Cp);
+    for (int i = 0; i < 36; ++i) dCh[p * 36 + i] = Cp[i] - C0[i];
+  }
+  Eng<double> e(ctx);
+  uint8_t* dph = (uint8_t*)ctx->arena.alloc(cells);
+  double* ddc = (double*)ctx->arena.alloc(sizeof(double) * 36 * nphase);
+  QCHECK(cudaMemcpyAsync(dph, phase, cells, cudaMemcpyHostToDevice, ctx->stream));
+  QCHECK(cudaMemcpyAsync(ddc, dCh.data(), sizeof(double) * 36 * nphase, cudaMemcpyHostToDevice,
+                         ctx->stream));
+  Cx<double>* F = e.alloc(36 * cells);
+  stiffness_field_kernel<<<grid1d(cells), 256, 0, ctx->stream>>>(dph, cells, ddc, nphase, F);
+  e.post();
+  QCHECK(cudaStreamSynchronize(ctx->stream));
+  ctx->arena.release(dph);
+  ctx->arena.release(ddc);
+  qtt_op* o = raised_from_field(ctx, F, n, bc, eps_tt, rmax);
+  e.release(F);
+  o->n = n;
+  o->has_c0 = 1;
+  o->lame0[0] = lam0;
+  o->lame0[1] = mu0;
+  memcpy(o->C0, C0, sizeof(C0));
+  *dC = o;
+  return QTT_OK;
+  API_END
+}
+
+int qtt_sfft_operator(qtt_ctx_t ctx, int n, int adjoint, double eps, qtt_op_t* out) {
+  API_BEGIN(ctx)
+  QREQ(ctx && out, "qtt_sfft_operator: null argument");
+  *out = build_sfft(ctx, n, adjoint ? 1 : 0, eps);
+  return QTT_OK;
+  API_END
+}
+
+int qtt_gamma_operator(qtt_ctx_t ctx, int n, double lambda0, double mu0, int scheme,
+                       double eps_tt, int rmax, qtt_op_t* out) {
+  API_BEGIN(ctx)
+  QREQ(ctx && out, "qtt_gamma_operator: null argument");
+  *out = build_gamma(ctx, n, lambda0, mu0, scheme, eps_tt, rmax);
+  return QTT_OK;
+  API_END
+}
+
+int qtt_op_apply(qtt_ctx_t ctx, qtt_op_t op, qtt_tt_t in, double eps_tt, int rmax, int oversample,
+                 int apply_id, qtt_tt_t* out) {
+  API_BEGIN(ctx)
+  QREQ(ctx && op && in && out, "qtt_op_apply: null argument");
+  QREQ(rmax >= 1 && oversample >= 0 && eps_tt >= 0, "qtt_op_apply: bad tolerance/rank");
+  int cap = 0;
+  *out = DISPATCH(ctx, op_apply_impl, ctx, op, in, eps_tt, rmax, oversample, apply_id, &cap);
+  return cap ? QTT_WRANKCAP : QTT_OK;
+  API_END
+}
+
+static int cubic_n(const qtt_tt* t) {
+  QREQ((t->L - 1) % 3 == 0 && t->L >= 4, "TT is not a controlled QTT of a cubic grid");
+  return (t->L - 1) / 3;
+}
+
+int sfft_apply(qtt_ctx_t ctx, qtt_tt_t in, double eps_tt, int rmax, qtt_tt_t* out) {
+  API_BEGIN(ctx)
+  QREQ(ctx && in && out, "sfft_apply: null argument");
+  qtt_op* S = cached_sfft(ctx, cubic_n(in), 0);
+  int cap = 0;
+  *out = DISPATCH(ctx, op_apply_impl, ctx, S, in, eps_tt, rmax, 16, 1, &cap);
+  return cap ? QTT_WRANKCAP : QTT_OK;
+  API_END
+}
+
+int isfft_apply(qtt_ctx_t ctx, qtt_tt_t in, double eps_tt, int rmax, qtt_tt_t* out) {
+  API_BEGIN(ctx)
+  QREQ(ctx && in && out, "isfft_apply: null argument");
+  qtt_op* S = cached_sfft(ctx, cubic_n(in), 1);
+  int cap = 0;
+  *out = DISPATCH(ctx, op_apply_impl, ctx, S, in, eps_tt, rmax, 16, 3, &cap);
+  return cap ? QTT_WRANKCAP : QTT_OK;
+  API_END
+}
+
+int gamma0_apply(qtt_ctx_t ctx, const int n[3], double lambda0, double mu0, int scheme,
+                 qtt_tt_t in, double eps_tt, int rmax, qtt_tt_t* out) {
+  API_BEGIN(ctx)
+  QREQ(ctx && n && in && out, "gamma0_apply: null argument");
+  QREQ(n[0] == n[1] && n[1] == n[2] && n[0] == cubic_n(in), "gamma0_apply: grid mismatch");
+  qtt_op* G = cached_gamma(ctx, n[0], lambda0, mu0, scheme, eps_tt, 1 << 30);
+  int cap = 0;
+  *out = DISPATCH(ctx, op_apply_impl, ctx, G, in, eps_tt, rmax, 16, 2, &cap);
+  return cap ? QTT_WRANKCAP : QTT_OK;
+  API_END
+}
+
+int tt_round(qtt_ctx_t ctx, qtt_tt_t inout, double eps_tt, int rmax) {
+  API_BEGIN(ctx)
+  QREQ(ctx && inout, "tt_round: null argument");
+  QREQ(rmax >= 1 && eps_tt >= 0, "tt_round: bad tolerance/rank");
+  const int cap = DISPATCH(ctx, round_impl, ctx, inout, eps_tt, rmax);
+  return cap ? QTT_WRANKCAP : QTT_OK;
+  API_END
+}
+
+int qtt_tt_dot(qtt_ctx_t ctx, qtt_tt_t a, qtt_tt_t b, double* re, double* im) {
+  API_BEGIN(ctx)
+  QREQ(ctx && a && b && re && im, "qtt_tt_dot: null argument");
+  DISPATCH(ctx, dot_impl, ctx, a, b, re, im);
+  return QTT_OK;
+  API_END
+}
+
+int qtt_op_mean_apply(qtt_ctx_t ctx, qtt_op_t op, qtt_tt_t x, double* out) {
+  API_BEGIN(ctx)
+  QREQ(ctx && op && x && out, "qtt_op_mean_apply: null argument");
+  std::vector<double> m;
+  DISPATCH(ctx, mean_impl, ctx, op, x, m);
+  memcpy(out, m.data(), sizeof(double) * m.size());
+  return QTT_OK;
+  API_END
+}
+
+int ls_solve_ops(qtt_ctx_t ctx, qtt_op_t dC, qtt_op_t S, qtt_op_t Sh, qtt_op_t gamma,
+                 const double C0[36], const double E_voigt[6], const qtt_solve_params* p,
+                 double sigma_bar[12], qtt_solve_info* info) {
+  API_BEGIN(ctx)
+  QREQ(ctx && dC && S && Sh && gamma && C0 && E_voigt && p && sigma_bar,
+       "ls_solve_ops: null argument");
+  QREQ(p->tol > 0 && p->max_iter >= 1 && p->rmax >= 1 && p->eps_tt >= 0 && p->oversample >= 0,
+       "ls_solve_ops: bad parameters");
+  return DISPATCH(ctx, solve_impl, ctx, dC, S, Sh, gamma, C0, E_voigt, p, sigma_bar, info, 0);
+  API_END
+}
+
+int ls_solve(qtt_ctx_t ctx, qtt_op_t dC, const double E_voigt[6], const qtt_solve_params* p,
+             double sigma_bar[12], qtt_solve_info* info) {
+  API_BEGIN(ctx)
+  QREQ(ctx && dC && E_voigt && p && sigma_bar, "ls_solve: null argument");
+  QREQ(dC->has_c0, "ls_solve: dC must come from qtt_from_phase_field");
+  const int n = dC->n;
+  qtt_op* S = cached_sfft(ctx, n, 0);
+  qtt_op* Sh = cached_sfft(ctx, n, 1);
+  qtt_op* G = cached_gamma(ctx, n, dC->lame0[0], dC->lame0[1], p->scheme, p->eps_tt, 1 << 30);
+  return DISPATCH(ctx, solve_impl, ctx, dC, S, Sh, G, dC->C0, E_voigt, p, sigma_bar, info, 0);
+  API_END
+}
+
+int ls_solve_ceff(qtt_ctx_t ctx, qtt_op_t dC, const qtt_solve_params* p, const int* loads,
+                  int nloads, double* Ceff, qtt_solve_info* info) {
+  API_BEGIN(ctx)
+  QREQ(ctx && dC && p && Ceff, "ls_solve_ceff: null argument");
+  int all[6] = {0, 1, 2, 3, 4, 5};
+  if (!loads) {
+    loads = all;
+    nloads = 6;
+  }
+  QREQ(nloads >= 1 && nloads <= 6, "ls_solve_ceff: nloads out of range");
+  for (int i = 0; i < 36; ++i) Ceff[i] = 0;
+  int worst = QTT_OK;
+  for (int l = 0; l < nloads; ++l) {
+    const int k = loads[l];
+    QREQ(k >= 0 && k < 6, "ls_solve_ceff: load index out of range");
+    double Ev[6] = {0, 0, 0, 0, 0, 0};
+    Ev[k] = 1.0;
+    double sig[12];
+    const int st = ls_solve(ctx, dC, Ev, p, sig, info ? info + l : nullptr);
+    if (st < 0) return st;
+    worst = std::max(worst, st);
+    for (int i = 0; i < 6; ++i) Ceff[k * 6 + i] = sig[2 * i];
+  }
+  return worst;
+  API_END
+}
+
+}  // extern "C"

@@ -1,0 +1,385 @@
+"""Python binding of the C ABI in include/qtt_homog.h (argument marshalling
+only; every step runs in the CUDA library).
+
+Device memory for a context is one torch uint8 tensor handed to the library
+as its workspace; the context's work is ordered on a torch CUDA stream. TT and
+operator cores cross the boundary as lists of complex128 numpy arrays: a TT
+core has shape (r_{k-1}, d_k, r_k); an operator core (a_{k-1}, d_out, d_in,
+a_k), or (a_{k-1}, d, a_k) when raised-diagonal.
+
+Importing this module loads ``libqtt_homog.so`` from the package directory and
+raises ImportError if it has not been built (``__graft_entry__.build()``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libqtt_homog.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "qtt_homog.h")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"CUDA library not built: {LIB_PATH} (run __graft_entry__.build())")
+lib = C.CDLL(LIB_PATH)
+
+QTT_OK, QTT_EINVAL, QTT_ENOMEM, QTT_ECUDA, QTT_ENAN, QTT_ETIMEOUT = 0, -1, -2, -3, -4, -5
+QTT_WRANKCAP, QTT_WNOCONV = 1, 2
+QTT_FP64, QTT_FP32 = 0, 1
+MAXC = 64
+
+_p = C.c_void_p
+_i = C.c_int
+_d = C.c_double
+_ip = C.POINTER(C.c_int)
+_dp = C.POINTER(C.c_double)
+
+
+class SolveParams(C.Structure):
+    _fields_ = [("tol", _d), ("max_iter", _i), ("eps_tt", _d), ("rmax", _i), ("scheme", _i),
+                ("oversample", _i)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("iters", _i), ("residual", _d), ("max_rank", _i), ("rank_cap_hit", _i),
+                ("imag_leak", _d), ("ms", _d)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+def _sig(name, res, args):
+    f = getattr(lib, name)
+    f.restype = res
+    f.argtypes = args
+    return f
+
+
+_sig("qtt_ctx_create", _i, [C.POINTER(_p), _i, _p, _i, _p, C.c_size_t, C.c_uint64])
+_sig("qtt_ctx_destroy", None, [_p])
+_sig("qtt_last_error", C.c_char_p, [_p])
+_sig("qtt_ctx_bytes_in_use", C.c_size_t, [_p])
+_sig("qtt_ctx_bytes_peak", C.c_size_t, [_p])
+_sig("qtt_ctx_launches", C.c_uint64, [_p])
+_sig("qtt_ctx_set_profiling", _i, [_p, _i])
+_sig("qtt_ctx_profile", _i, [_p, _i, _dp])
+_sig("qtt_tt_create", _i, [_p, _i, _ip, _ip, _dp, C.POINTER(_p)])
+_sig("qtt_tt_from_dense", _i, [_p, _i, _ip, _dp, _d, _i, C.POINTER(_p)])
+_sig("qtt_tt_shape", _i, [_p, _ip, _ip, _ip])
+_sig("qtt_tt_export", _i, [_p, _p, _dp])
+_sig("qtt_tt_free", None, [_p])
+_sig("qtt_op_create", _i, [_p, _i, _ip, _ip, _ip, _ip, _dp, C.POINTER(_p)])
+_sig("qtt_op_shape", _i, [_p, _ip, _ip, _ip, _ip, _ip])
+_sig("qtt_op_export", _i, [_p, _p, _dp])
+_sig("qtt_op_free", None, [_p])
+_sig("qtt_from_phase_field", _i, [_p, C.POINTER(C.c_uint8), _ip, _i, _i, _dp, _dp, _dp, _d, _i,
+                                   C.POINTER(_p)])
+_sig("qtt_sfft_operator", _i, [_p, _i, _i, _d, C.POINTER(_p)])
+_sig("qtt_gamma_operator", _i, [_p, _i, _d, _d, _i, _d, _i, C.POINTER(_p)])
+_sig("qtt_op_apply", _i, [_p, _p, _p, _d, _i, _i, _i, C.POINTER(_p)])
+_sig("sfft_apply", _i, [_p, _p, _d, _i, C.POINTER(_p)])
+_sig("isfft_apply", _i, [_p, _p, _d, _i, C.POINTER(_p)])
+_sig("gamma0_apply", _i, [_p, _ip, _d, _d, _i, _p, _d, _i, C.POINTER(_p)])
+_sig("tt_round", _i, [_p, _p, _d, _i])
+_sig("qtt_tt_dot", _i, [_p, _p, _p, _dp, _dp])
+_sig("qtt_op_mean_apply", _i, [_p, _p, _p, _dp])
+_sig("ls_solve_ops", _i, [_p, _p, _p, _p, _p, _dp, _dp, C.POINTER(SolveParams), _dp,
+                          C.POINTER(SolveInfo)])
+_sig("ls_solve", _i, [_p, _p, _dp, C.POINTER(SolveParams), _dp, C.POINTER(SolveInfo)])
+_sig("ls_solve_ceff", _i, [_p, _p, C.POINTER(SolveParams), _ip, _i, _dp, C.POINTER(SolveInfo)])
+
+
+def header_functions(path: str = HEADER):
+    """Names of the functions declared in the C header."""
+    txt = open(path).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:[A-Za-z_][\w\s\*]*?)\b([a-z_][a-z0-9_]*)\s*\(",
+                                 txt, flags=re.M)) - {"if", "while", "for", "return"})
+
+
+class QttError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"qtt error {code}: {msg}")
+        self.code = code
+
+
+def _ints(v):
+    a = (C.c_int * max(1, len(v)))(*[int(x) for x in v])
+    return a
+
+
+def _cplx_flat(cores):
+    return np.ascontiguousarray(np.concatenate(
+        [np.asarray(c, dtype=np.complex128).reshape(-1) for c in cores]).view(np.float64))
+
+
+class Context:
+    """A library context on a CUDA device with a torch-allocated workspace."""
+
+    def __init__(self, device: int = 0, precision: int = QTT_FP64, workspace_bytes: int = 1 << 30,
+                 seed: int = 2412, stream=None):
+        import torch
+        self.torch = torch
+        self.device = device
+        self.precision = precision
+        self.seed = seed
+        self.ws = torch.empty(int(workspace_bytes), dtype=torch.uint8, device=f"cuda:{device}")
+        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        h = _p()
+        rc = lib.qtt_ctx_create(C.byref(h), device, _p(self.stream.cuda_stream), precision,
+                                _p(self.ws.data_ptr()), int(workspace_bytes), C.c_uint64(seed))
+        if rc != 0:
+            raise QttError(rc, "qtt_ctx_create failed")
+        self.h = h
+
+    def check(self, rc, allow_warn=True):
+        if rc < 0 or (rc > 0 and not allow_warn):
+            raise QttError(rc, lib.qtt_last_error(self.h).decode())
+        return rc
+
+    def close(self):
+        """Destroy the context; handles still alive become inert (their
+        device memory went with the workspace)."""
+        if getattr(self, "h", None):
+            lib.qtt_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def bytes_in_use(self):
+        return lib.qtt_ctx_bytes_in_use(self.h)
+
+    def bytes_peak(self):
+        return lib.qtt_ctx_bytes_peak(self.h)
+
+    def launches(self):
+        return lib.qtt_ctx_launches(self.h)
+
+    def set_profiling(self, on: bool):
+        self.check(lib.qtt_ctx_set_profiling(self.h, int(on)))
+
+    def profile(self, reset: bool = False):
+        """{class: (launches, total_ms, algorithmic_flops)} for gemm, qr, svd."""
+        out = np.zeros(9)
+        self.check(lib.qtt_ctx_profile(self.h, int(reset), out.ctypes.data_as(_dp)))
+        return {name: (int(out[3 * i]), float(out[3 * i + 1]), float(out[3 * i + 2]))
+                for i, name in enumerate(("gemm", "qr", "svd"))}
+
+    # ------------------------------------------------------------ handles
+    def tt(self, cores):
+        dims = [c.shape[1] for c in cores]
+        ranks = [c.shape[0] for c in cores] + [cores[-1].shape[2]]
+        flat = _cplx_flat(cores)
+        h = _p()
+        self.check(lib.qtt_tt_create(self.h, len(cores), _ints(dims), _ints(ranks),
+                                     flat.ctypes.data_as(_dp), C.byref(h)))
+        return TT(self, h)
+
+    def tt_from_dense(self, T, eps=0.0, rmax=1 << 30):
+        """qtt_tt_from_dense: TT-SVD of a dense tensor on the device."""
+        T = np.ascontiguousarray(T, dtype=np.complex128)
+        flat = T.reshape(-1).view(np.float64)
+        h = _p()
+        self.check(lib.qtt_tt_from_dense(self.h, T.ndim, _ints(T.shape), flat.ctypes.data_as(_dp),
+                                         eps, rmax, C.byref(h)))
+        return TT(self, h)
+
+    def op(self, cores, diag=None):
+        L = len(cores)
+        if diag is None:
+            diag = [c.ndim == 3 for c in cores]
+        dout = [c.shape[1] for c in cores]
+        din = [c.shape[1] if dg else c.shape[2] for c, dg in zip(cores, diag)]
+        ranks = [c.shape[0] for c in cores] + [cores[-1].shape[-1]]
+        flat = _cplx_flat(cores)
+        h = _p()
+        self.check(lib.qtt_op_create(self.h, L, _ints(dout), _ints(din), _ints(ranks),
+                                     _ints([int(d) for d in diag]), flat.ctypes.data_as(_dp),
+                                     C.byref(h)))
+        return Op(self, h)
+
+
+class TT:
+    def __init__(self, ctx: Context, h):
+        self.ctx, self.h = ctx, h
+
+    def shape(self):
+        L = C.c_int()
+        dims = (C.c_int * MAXC)()
+        ranks = (C.c_int * (MAXC + 1))()
+        lib.qtt_tt_shape(self.h, C.byref(L), dims, ranks)
+        return list(dims[:L.value]), list(ranks[:L.value + 1])
+
+    def cores(self):
+        dims, ranks = self.shape()
+        tot = sum(ranks[k] * dims[k] * ranks[k + 1] for k in range(len(dims)))
+        buf = np.empty(2 * tot, dtype=np.float64)
+        self.ctx.check(lib.qtt_tt_export(self.ctx.h, self.h, buf.ctypes.data_as(_dp)))
+        z = buf.view(np.complex128)
+        out, off = [], 0
+        for k in range(len(dims)):
+            n = ranks[k] * dims[k] * ranks[k + 1]
+            out.append(z[off:off + n].reshape(ranks[k], dims[k], ranks[k + 1]).copy())
+            off += n
+        return out
+
+    def free(self):
+        if self.h and self.ctx.h:
+            lib.qtt_tt_free(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Op:
+    def __init__(self, ctx: Context, h, owned: bool = True):
+        self.ctx, self.h, self.owned = ctx, h, owned
+
+    def shape(self):
+        L = C.c_int()
+        a = [(C.c_int * (MAXC + 1))() for _ in range(4)]
+        lib.qtt_op_shape(self.h, C.byref(L), a[0], a[1], a[2], a[3])
+        n = L.value
+        return list(a[0][:n]), list(a[1][:n]), list(a[2][:n + 1]), list(a[3][:n])
+
+    def cores(self):
+        dout, din, ranks, diag = self.shape()
+        sizes = [ranks[k] * dout[k] * (1 if diag[k] else din[k]) * ranks[k + 1]
+                 for k in range(len(dout))]
+        buf = np.empty(2 * sum(sizes), dtype=np.float64)
+        self.ctx.check(lib.qtt_op_export(self.ctx.h, self.h, buf.ctypes.data_as(_dp)))
+        z = buf.view(np.complex128)
+        out, off = [], 0
+        for k, n in enumerate(sizes):
+            shp = ((ranks[k], dout[k], ranks[k + 1]) if diag[k]
+                   else (ranks[k], dout[k], din[k], ranks[k + 1]))
+            out.append(z[off:off + n].reshape(shp).copy())
+            off += n
+        return out
+
+    def free(self):
+        if self.h and self.owned and self.ctx.h:
+            lib.qtt_op_free(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------- entry points (C names)
+
+def qtt_from_phase_field(ctx: Context, phase, n, E, nu, lame0=None, eps_tt=1e-6, rmax=1 << 30):
+    ph = np.ascontiguousarray(phase, dtype=np.uint8)
+    shape = list(ph.shape)
+    Ea = np.asarray(E, dtype=np.float64)
+    nua = np.asarray(nu, dtype=np.float64)
+    l0 = None if lame0 is None else np.asarray(lame0, dtype=np.float64)
+    h = _p()
+    ctx.check(lib.qtt_from_phase_field(ctx.h, ph.ctypes.data_as(C.POINTER(C.c_uint8)),
+                                       _ints(shape), n, len(Ea), Ea.ctypes.data_as(_dp),
+                                       nua.ctypes.data_as(_dp),
+                                       None if l0 is None else l0.ctypes.data_as(_dp),
+                                       eps_tt, rmax, C.byref(h)))
+    return Op(ctx, h)
+
+
+def qtt_sfft_operator(ctx: Context, n, adjoint=False, eps=1e-14):
+    h = _p()
+    ctx.check(lib.qtt_sfft_operator(ctx.h, n, int(adjoint), eps, C.byref(h)))
+    return Op(ctx, h)
+
+
+def qtt_gamma_operator(ctx: Context, n, lam0, mu0, scheme=0, eps_tt=1e-6, rmax=1 << 30):
+    h = _p()
+    ctx.check(lib.qtt_gamma_operator(ctx.h, n, lam0, mu0, scheme, eps_tt, rmax, C.byref(h)))
+    return Op(ctx, h)
+
+
+def qtt_op_apply(ctx: Context, op: Op, x: TT, eps_tt, rmax, oversample=16, apply_id=0):
+    h = _p()
+    rc = ctx.check(lib.qtt_op_apply(ctx.h, op.h, x.h, eps_tt, rmax, oversample, apply_id,
+                                    C.byref(h)))
+    return TT(ctx, h), rc
+
+
+def sfft_apply(ctx: Context, x: TT, eps_tt, rmax):
+    h = _p()
+    rc = ctx.check(lib.sfft_apply(ctx.h, x.h, eps_tt, rmax, C.byref(h)))
+    return TT(ctx, h), rc
+
+
+def isfft_apply(ctx: Context, x: TT, eps_tt, rmax):
+    h = _p()
+    rc = ctx.check(lib.isfft_apply(ctx.h, x.h, eps_tt, rmax, C.byref(h)))
+    return TT(ctx, h), rc
+
+
+def gamma0_apply(ctx: Context, n, lam0, mu0, x: TT, eps_tt, rmax, scheme=0):
+    h = _p()
+    rc = ctx.check(lib.gamma0_apply(ctx.h, _ints([n, n, n]), lam0, mu0, scheme, x.h, eps_tt, rmax,
+                                    C.byref(h)))
+    return TT(ctx, h), rc
+
+
+def tt_round(ctx: Context, x: TT, eps_tt, rmax):
+    return ctx.check(lib.tt_round(ctx.h, x.h, eps_tt, rmax))
+
+
+def qtt_tt_dot(ctx: Context, a: TT, b: TT) -> complex:
+    re, im = C.c_double(), C.c_double()
+    ctx.check(lib.qtt_tt_dot(ctx.h, a.h, b.h, C.byref(re), C.byref(im)))
+    return complex(re.value, im.value)
+
+
+def qtt_op_mean_apply(ctx: Context, op: Op, x: TT):
+    dout = op.shape()[0][0]
+    buf = np.zeros(2 * dout)
+    ctx.check(lib.qtt_op_mean_apply(ctx.h, op.h, x.h, buf.ctypes.data_as(_dp)))
+    return buf.view(np.complex128).copy()
+
+
+def solve_params(tol=1e-6, max_iter=5000, eps_tt=1e-8, rmax=64, scheme=0, oversample=16):
+    return SolveParams(tol, max_iter, eps_tt, rmax, scheme, oversample)
+
+
+def ls_solve_ops(ctx: Context, dC: Op, S: Op, Sh: Op, G: Op, C0, E_voigt, params: SolveParams):
+    C0a = np.ascontiguousarray(C0, dtype=np.float64).reshape(36)
+    Ea = np.ascontiguousarray(E_voigt, dtype=np.float64)
+    sig = np.zeros(12)
+    info = SolveInfo()
+    rc = ctx.check(lib.ls_solve_ops(ctx.h, dC.h, S.h, Sh.h, G.h, C0a.ctypes.data_as(_dp),
+                                    Ea.ctypes.data_as(_dp), C.byref(params),
+                                    sig.ctypes.data_as(_dp), C.byref(info)))
+    return sig.view(np.complex128).copy(), info.as_dict(), rc
+
+
+def ls_solve(ctx: Context, dC: Op, E_voigt, params: SolveParams):
+    Ea = np.ascontiguousarray(E_voigt, dtype=np.float64)
+    sig = np.zeros(12)
+    info = SolveInfo()
+    rc = ctx.check(lib.ls_solve(ctx.h, dC.h, Ea.ctypes.data_as(_dp), C.byref(params),
+                                sig.ctypes.data_as(_dp), C.byref(info)))
+    return sig.view(np.complex128).copy(), info.as_dict(), rc
+
+
+def ls_solve_ceff(ctx: Context, dC: Op, params: SolveParams, loads=None):
+    loads = list(range(6)) if loads is None else list(loads)
+    Ceff = np.zeros(36)
+    infos = (SolveInfo * len(loads))()
+    rc = ctx.check(lib.ls_solve_ceff(ctx.h, dC.h, C.byref(params), _ints(loads), len(loads),
+                                     Ceff.ctypes.data_as(_dp), infos))
+    return Ceff.reshape(6, 6).T.copy(), [i.as_dict() for i in infos], rc

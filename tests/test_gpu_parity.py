@@ -1,0 +1,212 @@
+"""GPU parity: every C-ABI call against the oracle on the same seeded inputs.
+
+FP64 mode: results agree with the oracle to rounding (1e-10 relative on
+gauge-invariant quantities: dense reconstructions, norms, C_eff). The random
+sketches are generated from the same Philox stream on both sides."""
+import numpy as np
+import pytest
+
+from oracle import dense, qtt as oq
+from paper_2412_11566_gb300 import synth
+from tests._helpers import from_lib_op, random_tt, to_lib_op
+
+pytestmark = pytest.mark.gpu
+
+SEED = 2412
+
+
+@pytest.fixture(scope="module")
+def Q(lib_built):
+    return lib_built
+
+
+@pytest.fixture(scope="module")
+def ctx64(Q):
+    c = Q.Context(0, Q.QTT_FP64, 1 << 30, seed=SEED)
+    yield c
+    c.close()
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300)
+
+
+def qtt_dims(n):
+    return [6] + [2] * (3 * n)
+
+
+def test_tt_roundtrip(Q, ctx64):
+    rng = np.random.default_rng(0)
+    x = random_tt(rng, qtt_dims(2), [1, 3, 5, 4, 6, 3, 2, 1])
+    t = ctx64.tt(x)
+    y = t.cores()
+    for a, b in zip(x, y):
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("n,ranks", [(2, [1, 6, 9, 12, 10, 7, 2, 1]), (3, [1, 6, 12, 20, 17, 14, 11, 8, 4, 2, 1])])
+def test_round_vs_oracle(Q, ctx64, n, ranks):
+    rng = np.random.default_rng(n)
+    x = random_tt(rng, qtt_dims(n), ranks)
+    full = oq.tt_full(x)
+    for eps, rmax in [(1e-12, 1000), (1e-2, 1000), (0.3, 1000), (1e-12, 5)]:
+        t = ctx64.tt(x)
+        rc = Q.tt_round(ctx64, t, eps, rmax)
+        y = t.cores()
+        ref, cap = oq.tt_round(x, eps, rmax)
+        assert [c.shape for c in y] == [c.shape for c in ref]
+        assert rc == (Q.QTT_WRANKCAP if cap else 0)
+        assert rel(oq.tt_full(y), oq.tt_full(ref)) < 1e-10
+        if rmax == 1000:
+            assert rel(oq.tt_full(y), full) <= eps * (1 + 1e-9)
+        # right-orthogonal result
+        for c in y[1:]:
+            M = c.reshape(c.shape[0], -1)
+            assert np.abs(M @ M.conj().T - np.eye(M.shape[0])).max() < 1e-11
+
+
+def test_dot_and_norm(Q, ctx64):
+    rng = np.random.default_rng(5)
+    a = random_tt(rng, qtt_dims(2), [1, 4, 6, 5, 6, 4, 3, 1])
+    b = random_tt(rng, qtt_dims(2), [1, 3, 5, 7, 5, 4, 2, 1])
+    got = Q.qtt_tt_dot(ctx64, ctx64.tt(a), ctx64.tt(b))
+    ref = np.vdot(oq.tt_full(a), oq.tt_full(b))
+    assert abs(got - ref) < 1e-11 * abs(ref)
+
+
+@pytest.mark.parametrize("n", [2, 3])
+def test_sketched_apply_vs_oracle(Q, ctx64, n):
+    rng = np.random.default_rng(10 + n)
+    lam0, mu0 = 2.0, 1.0
+    G = oq.gamma_qtt(n, lam0, mu0, 1e-12)
+    S = oq.sfft_operator(n)
+    x = random_tt(rng, qtt_dims(n), [1] + [min(6 * 2 ** k, 2 ** (3 * n - k), 9) for k in range(3 * n)] + [1])
+    x, _ = oq.tt_round(x, 1e-14, 1000)
+    tx = ctx64.tt(x)
+    for op, name in [(G, "gamma"), (S, "sfft")]:
+        cores, diag = to_lib_op(op)
+        top = ctx64.op(cores, diag)
+        for rmax, eps in [(200, 1e-12), (12, 1e-12), (200, 1e-3)]:
+            y, rc = Q.qtt_op_apply(ctx64, top, tx, eps, rmax, 16, apply_id=7)
+            ref = oq.tto_apply_sketched(op, x, rmax + 16, SEED, 7)
+            ref, cap = oq.tt_round(ref, eps, rmax, assume_left_orth=True)
+            yc = y.cores()
+            assert [c.shape for c in yc] == [c.shape for c in ref], name
+            assert rel(oq.tt_full(yc), oq.tt_full(ref)) < 1e-10, (name, rmax, eps)
+            if rmax == 200 and eps == 1e-12:
+                exact = oq.tto_full(op) @ oq.tt_full(x).reshape(-1)
+                assert rel(oq.tt_full(yc).reshape(-1), exact) < 1e-10
+
+
+@pytest.mark.parametrize("n", [2, 3])
+def test_sfft_operator_vs_oracle(Q, ctx64, n):
+    for adj in (False, True):
+        op = Q.qtt_sfft_operator(ctx64, n, adj, 1e-14)
+        cores, diag = op.cores(), op.shape()[3]
+        ref = oq.sfft_operator(n, 1e-14, adjoint=adj)
+        assert rel(oq.tto_full(from_lib_op(cores, diag)), oq.tto_full(ref)) < 1e-12
+
+
+@pytest.mark.parametrize("n", [2, 3])
+def test_gamma_operator_vs_oracle(Q, ctx64, n):
+    lam0, mu0 = 3.5, 1.25
+    op = Q.qtt_gamma_operator(ctx64, n, lam0, mu0, 0, 1e-12)
+    cores, diag = op.cores(), op.shape()[3]
+    G = oq.tto_full(from_lib_op(cores, diag))
+    ref = oq.tto_full(oq.gamma_qtt(n, lam0, mu0, 1e-12))
+    assert rel(G, ref) < 1e-9
+
+
+def test_stiffness_operator_vs_oracle(Q, ctx64):
+    n = 3
+    ph = synth.centred_sphere(n, 0.3)
+    E, nu = (1.0, 10.0), (0.3, 0.25)
+    lam0 = dense.reference_lame(E, nu)
+    op = Q.qtt_from_phase_field(ctx64, ph, n, E, nu, None, 1e-12)
+    got = oq.tto_full(from_lib_op(op.cores(), op.shape()[3]))
+    ref = oq.tto_full(oq.stiffness_qtt(ph, n, E, nu, lam0, 1e-12))
+    assert rel(got, ref) < 1e-10
+
+
+def test_stiffness_operator_broadcast_axis(Q, ctx64):
+    n = 3
+    ph = synth.laminate(n, 2)          # shape (1, 1, 8): broadcast x1, x2
+    E, nu = (1.0, 5.0), (0.3, 0.3)
+    lam0 = dense.reference_lame(E, nu)
+    op = Q.qtt_from_phase_field(ctx64, ph, n, E, nu, None, 1e-12)
+    got = oq.tto_full(from_lib_op(op.cores(), op.shape()[3]))
+    ref = oq.tto_full(oq.stiffness_qtt(synth.broadcast_dense(ph, n), n, E, nu, lam0, 1e-12))
+    assert rel(got, ref) < 1e-10
+
+
+def test_mean_vs_dense(Q, ctx64):
+    n = 2
+    rng = np.random.default_rng(3)
+    ph = synth.centred_sphere(n, 0.3)
+    E, nu = (1.0, 4.0), (0.3, 0.2)
+    lam0 = dense.reference_lame(E, nu)
+    dC = oq.stiffness_qtt(ph, n, E, nu, lam0, 1e-12)
+    x = random_tt(rng, qtt_dims(n), [1, 6, 5, 4, 6, 4, 2, 1])
+    cores, diag = to_lib_op(dC)
+    got = Q.qtt_op_mean_apply(ctx64, ctx64.op(cores, diag), ctx64.tt(x))
+    ref = (oq.tto_full(dC) @ oq.tt_full(x).reshape(-1)).reshape(6, -1).mean(axis=1)
+    assert np.abs(got - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+def tie_free_tol(history, m):
+    """A stop tolerance between the residuals of iterations m-1 and m: both
+    sides then stop after exactly m iterations (the GPU's residual uses FP64
+    inner products, whose cancellation floor is ~1e-8 relative, so a tolerance
+    within that band of a residual could flip the decision)."""
+    return float(np.sqrt(history[m - 2] * history[m - 1]))
+
+
+@pytest.mark.parametrize("n,load,m", [(2, 0, 20), (2, 4, 12), (3, 0, 8), (3, 3, 6)])
+def test_ls_solve_ops_vs_qtt_oracle(Q, ctx64, n, load, m):
+    ph = synth.centred_sphere(n, 0.3)
+    E, nu = (1.0, 10.0), (0.3, 0.3)
+    lam0 = dense.reference_lame(E, nu)
+    eps, rmax = 1e-8, 24
+    dC = oq.stiffness_qtt(ph, n, E, nu, lam0, 1e-12)
+    G = oq.gamma_qtt(n, *lam0, 1e-12)
+    S, Sh = oq.sfft_operator(n), oq.sfft_operator(n, adjoint=True)
+    C0 = dense.stiffness_voigt(*lam0)
+    Ev = np.eye(6)[load]
+    ref = oq.ls_solve(dC, G, S, Sh, Ev, n, 1e-300, eps, rmax, max_iter=m, lame0=lam0, seed=SEED)
+    tol = tie_free_tol(ref["history"], m)
+    dc, dd = to_lib_op(dC)
+    gc, gd = to_lib_op(G)
+    sig, info, rc = Q.ls_solve_ops(ctx64, ctx64.op(dc, dd), ctx64.op(S), ctx64.op(Sh),
+                                   ctx64.op(gc, gd), C0, Ev, Q.solve_params(tol, 500, eps, rmax))
+    assert info["iters"] == m
+    assert abs(info["residual"] - ref["history"][-1]) < 1e-6 * ref["history"][-1] + 1e-12
+    assert np.abs(sig - ref["sigma_bar"]).max() < 1e-10 * np.abs(ref["sigma_bar"]).max()
+
+
+def test_ls_solve_vs_dense_oracle(Q, ctx64):
+    """Operators built on the device (phase field, SFFT, Green) and the full
+    solve against the dense FFT scheme (Alg. 1)."""
+    n = 3
+    ph = synth.centred_sphere(n, 0.3)
+    E, nu = (1.0, 10.0), (0.3, 0.3)
+    dC = Q.qtt_from_phase_field(ctx64, ph, n, E, nu, None, 1e-10)
+    C, infos, rc = Q.ls_solve_ceff(ctx64, dC, Q.solve_params(1e-6, 500, 1e-9, 64), loads=[0, 3])
+    Cd, imag, its = dense.ceff(ph, E, nu, tol=1e-6, loads=[0, 3])
+    for k in (0, 3):
+        assert np.abs(C[:, k] - Cd[:, k]).max() < 1e-5 * np.abs(Cd).max()
+
+
+def test_fp32_mode_vs_dense_oracle(Q):
+    """FP32 mode (complex64 cores, FP32 contractions and factorisations, FP64
+    norms and C_eff average) against the tightly converged dense oracle: the
+    C_eff column must be within 1e-4 relative."""
+    ctx = Q.Context(0, Q.QTT_FP32, 1 << 30, seed=SEED)
+    n = 3
+    ph = synth.centred_sphere(n, 0.3)
+    E, nu = (1.0, 10.0), (0.3, 0.3)
+    dC = Q.qtt_from_phase_field(ctx, ph, n, E, nu, None, 1e-6)
+    C, infos, rc = Q.ls_solve_ceff(ctx, dC, Q.solve_params(1e-6, 500, 1e-6, 64), loads=[0, 3])
+    Cd, imag, its = dense.ceff(ph, E, nu, tol=1e-10, loads=[0, 3])
+    for k in (0, 3):
+        assert np.abs(C[:, k] - Cd[:, k]).max() < 1e-4 * np.abs(Cd).max()
+    ctx.close()
