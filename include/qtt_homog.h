@@ -89,6 +89,7 @@ uint64_t qtt_ctx_launches(qtt_ctx_t ctx);
  * c in (0 gemm, 1 qr, 2 svd) out[3c] = launches, out[3c+1] = total ms,
  * out[3c+2] = algorithmic real flops (GEMM: 8 M N K per complex product;
  * QR: 8 (2 m n^2 - 2 n^3/3); SVD: one Jacobi sweep's count per launch);
+ * out[9] = Jacobi sweeps run over all SVD launches (10 doubles in all);
  * reset = 1 clears the counters. */
 int qtt_ctx_set_profiling(qtt_ctx_t ctx, int on);
 int qtt_ctx_profile(qtt_ctx_t ctx, int reset, double* out);
@@ -204,9 +205,19 @@ int ls_solve(qtt_ctx_t ctx, qtt_op_t dC, const double E_voigt[6],
              const qtt_solve_params* p, double sigma_bar[12], qtt_solve_info* info);
 /* C_eff column by column (Sec. 2): column k = Re sigma_bar for E = e_k, for
  * the load cases listed in loads[nloads] (NULL = all six). Ceff is 36 doubles,
- * column-major (Ceff[k*6 + i] = C_eff[i][k]); info has nloads entries. */
+ * column-major (Ceff[k*6 + i] = C_eff[i][k]); info has nloads entries. Up to
+ * qtt_ctx_set_concurrency load cases run side by side, each on its own CUDA
+ * stream and host thread with a private slice of the workspace (the
+ * operators are shared); the call returns when all are done. */
 int ls_solve_ceff(qtt_ctx_t ctx, qtt_op_t dC, const qtt_solve_params* p, const int* loads,
                   int nloads, double* Ceff, qtt_solve_info* info);
+/* Jacobi SVD stopping rule: a column pair counts as orthogonal when
+ * |a_p^H a_q| <= tol_scale sqrt(m) eps |a_p| |a_q| (eps of the working
+ * precision; default tol_scale 1); max_sweeps_fp32 caps the sweeps in FP32
+ * mode (default 40; FP64 mode uses 60). */
+int qtt_ctx_set_jacobi(qtt_ctx_t ctx, double tol_scale, int max_sweeps_fp32);
+/* Number of load cases ls_solve_ceff solves concurrently (1..6, default 1). */
+int qtt_ctx_set_concurrency(qtt_ctx_t ctx, int concurrent_loads);
 
 #ifdef __cplusplus
 }

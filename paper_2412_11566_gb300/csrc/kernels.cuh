@@ -6,6 +6,7 @@
 // tensor-train sweeps without explicit transposes.
 #pragma once
 
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -194,7 +195,11 @@ __device__ R block_sum(R v, R* sh) {
 // Q is accumulated backwards from [I; 0]. W (m x n) is workspace.
 template <typename R>
 __global__ void qr_kernel(int m, int n, const Cx<R>* __restrict__ A, long long rs, long long cs,
-                          int conjA, Cx<R>* W, Cx<R>* Q, Cx<R>* Rm, R* hbuf, Cx<R>* vhead) {
+                          int conjA, Cx<R>* Wg, Cx<R>* Q, Cx<R>* Rm, R* hbuf, Cx<R>* vhead,
+                          int use_smem) {
+  // the working copy lives in dynamic shared memory when it fits
+  extern __shared__ __align__(16) unsigned char qr_dyn[];
+  Cx<R>* W = use_smem ? (Cx<R>*)qr_dyn : Wg;
   __shared__ R red[32];
   __shared__ Cx<R> s_v0;
   __shared__ R s_h;
@@ -295,14 +300,25 @@ __global__ void qr_kernel(int m, int n, const Cx<R>* __restrict__ A, long long r
 template <typename R>
 __global__ void jacobi_svd_kernel(int m, int n, Cx<R>* A, Cx<R>* V, double* sigma,
                                   int* perm, R* snorm, double delta2, int rmax, int* trunc,
-                                  int max_sweeps, R tol, int values_are_squares) {
+                                  int max_sweeps, R tol, int values_are_squares, int use_smem,
+                                  int want_v) {
+  // the column data lives in dynamic shared memory when it fits (copied in
+  // here, copied back to A before the columns are read out)
+  extern __shared__ __align__(16) unsigned char jac_dyn[];
+  Cx<R>* const Ag = A;
+  if (use_smem) {
+    A = (Cx<R>*)jac_dyn;
+    for (long long e = threadIdx.x; e < (long long)m * n; e += blockDim.x) A[e] = Ag[e];
+    __syncthreads();
+  }
   __shared__ int s_rot;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
-  for (long long e = tid; e < (long long)n * n; e += nt) {
-    const int i = (int)(e % n), j = (int)(e / n);
-    V[e] = mk<R>(i == j ? (R)1 : (R)0, 0);
-  }
+  if (want_v)
+    for (long long e = tid; e < (long long)n * n; e += nt) {
+      const int i = (int)(e % n), j = (int)(e / n);
+      V[e] = mk<R>(i == j ? (R)1 : (R)0, 0);
+    }
   __shared__ R s_red[32];
   R f2 = 0;
   for (long long e = tid; e < (long long)m * n; e += nt) f2 += cabs2(A[e]);
@@ -363,12 +379,14 @@ __global__ void jacobi_svd_kernel(int m, int n, Cx<R>* A, Cx<R>* V, double* sigm
           ap[i] = mk<R>(c * x.x - s * y.x, c * x.y - s * y.y);
           aq[i] = mk<R>(s * x.x + c * y.x, s * x.y + c * y.y);
         }
-        Cx<R>* vp = V + (long long)p * n;
-        Cx<R>* vq = V + (long long)q * n;
-        for (int i = lane; i < n; i += 32) {
-          const Cx<R> x = vp[i], y = cmul(ec, vq[i]);
-          vp[i] = mk<R>(c * x.x - s * y.x, c * x.y - s * y.y);
-          vq[i] = mk<R>(s * x.x + c * y.x, s * x.y + c * y.y);
+        if (want_v) {
+          Cx<R>* vp = V + (long long)p * n;
+          Cx<R>* vq = V + (long long)q * n;
+          for (int i = lane; i < n; i += 32) {
+            const Cx<R> x = vp[i], y = cmul(ec, vq[i]);
+            vp[i] = mk<R>(c * x.x - s * y.x, c * x.y - s * y.y);
+            vq[i] = mk<R>(s * x.x + c * y.x, s * x.y + c * y.y);
+          }
         }
         if (lane == 0) s_rot = 1;
       }
@@ -385,12 +403,14 @@ __global__ void jacobi_svd_kernel(int m, int n, Cx<R>* A, Cx<R>* V, double* sigm
     if (lane == 0) snorm[j] = sqrt(s2);
   }
   __syncthreads();
-  // rank of each column in descending order (ties by index)
+  // rank of each column in descending order (ties by index); a NaN norm
+  // sorts last and raises trunc[4], so the ranks stay a permutation
   for (int j = tid; j < n; j += nt) {
-    const R sj = snorm[j];
+    const R sj = isnan(snorm[j]) ? (R)-1 : snorm[j];
+    if (isnan(snorm[j])) trunc[4] = 1;
     int rk = 0;
     for (int i = 0; i < n; ++i) {
-      const R si = snorm[i];
+      const R si = isnan(snorm[i]) ? (R)-1 : snorm[i];
       rk += (si > sj) || (si == sj && i < j);
     }
     perm[rk] = j;
@@ -417,27 +437,167 @@ __global__ void jacobi_svd_kernel(int m, int n, Cx<R>* A, Cx<R>* V, double* sigm
     trunc[2] = sweep;
   }
   __syncthreads();
-  for (int j = tid; j < n; j += nt) sigma[j] = (double)snorm[perm[j]];
+  for (int j = tid; j < n; j += nt) {
+    const R v = snorm[perm[j]];
+    sigma[j] = isnan(v) ? 0.0 : (double)v;
+  }
+  if (use_smem)
+    for (long long e = tid; e < (long long)m * n; e += nt) Ag[e] = A[e];
   __syncthreads();
+}
+
+// Multi-CTA one-sided Jacobi for matrices too large for one CTA's shared
+// memory (cooperative launch: all CTAs resident). Same rotations and
+// round-robin ordering as jacobi_svd_kernel; the n/2 disjoint pairs of a
+// round are spread over the warps of the whole grid, grid.sync() separates
+// rounds, and flags[sweep] (zeroed by the host, max_sweeps entries) records
+// whether any warp rotated in that sweep. Writes the column norms to snorm;
+// jacobi_finish_kernel sorts them and picks the truncation rank.
+template <typename R>
+__global__ void jacobi_grid_kernel(int m, int n, Cx<R>* A, Cx<R>* V, R* snorm, int* flags,
+                                   int max_sweeps, R tol, R negl, int* sweeps_out, int want_v) {
+  namespace cg = cooperative_groups;
+  cg::grid_group grid = cg::this_grid();
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  if (want_v)
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < (long long)n * n;
+         e += (long long)gridDim.x * blockDim.x) {
+      const int i = (int)(e % n), j = (int)(e / n);
+      V[e] = mk<R>(i == j ? (R)1 : (R)0, 0);
+    }
+  grid.sync();
+  const int np = (n + 1) & ~1;
+  const int mp = np - 1;
+  int sweep = 0;
+  for (sweep = 0; sweep < max_sweeps && np > 1; ++sweep) {
+    for (int r = 0; r < mp; ++r) {
+      for (int pi = gw; pi < np / 2; pi += nwarps) {
+        int p, q;
+        if (pi == 0) {
+          p = 0;
+          q = (r % mp) + 1;
+        } else {
+          p = ((r + pi) % mp) + 1;
+          q = ((r + mp - pi) % mp) + 1;
+        }
+        if (p >= n || q >= n) continue;
+        Cx<R>* ap = A + (long long)p * m;
+        Cx<R>* aq = A + (long long)q * m;
+        R app = 0, aqq = 0;
+        Cx<R> apq = mk<R>(0, 0);
+        for (int i = lane; i < m; i += 32) {
+          const Cx<R> x = ap[i], y = aq[i];
+          app += cabs2(x);
+          aqq += cabs2(y);
+          apq = cadd(apq, cmulc(x, y));
+        }
+        app = warp_sum(app);
+        aqq = warp_sum(aqq);
+        apq = warp_sum(apq);
+        if (app <= negl || aqq <= negl) continue;
+        const R g = hypot(apq.x, apq.y);
+        if (!(g > tol * sqrt(app) * sqrt(aqq))) continue;
+        const Cx<R> e = mk<R>(apq.x / g, apq.y / g);
+        const R zeta = (aqq - app) / ((R)2 * g);
+        const R t = (zeta >= (R)0 ? (R)1 : (R)-1) / (fabs(zeta) + sqrt((R)1 + zeta * zeta));
+        const R c = (R)1 / sqrt((R)1 + t * t);
+        const R s = c * t;
+        const Cx<R> ec = cconj(e);
+        for (int i = lane; i < m; i += 32) {
+          const Cx<R> x = ap[i], y = cmul(ec, aq[i]);
+          ap[i] = mk<R>(c * x.x - s * y.x, c * x.y - s * y.y);
+          aq[i] = mk<R>(s * x.x + c * y.x, s * x.y + c * y.y);
+        }
+        if (want_v) {
+          Cx<R>* vp = V + (long long)p * n;
+          Cx<R>* vq = V + (long long)q * n;
+          for (int i = lane; i < n; i += 32) {
+            const Cx<R> x = vp[i], y = cmul(ec, vq[i]);
+            vp[i] = mk<R>(c * x.x - s * y.x, c * x.y - s * y.y);
+            vq[i] = mk<R>(s * x.x + c * y.x, s * x.y + c * y.y);
+          }
+        }
+        if (lane == 0) atomicExch(&flags[sweep], 1);
+      }
+      grid.sync();
+    }
+    if (atomicAdd(&flags[sweep], 0) == 0) break;  // uniform: read after the last grid.sync
+  }
+  for (int j = gw; j < n; j += nwarps) {
+    R s2 = 0;
+    const Cx<R>* a = A + (long long)j * m;
+    for (int i = lane; i < m; i += 32) s2 += cabs2(a[i]);
+    s2 = warp_sum(s2);
+    if (lane == 0) snorm[j] = sqrt(s2);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *sweeps_out = sweep;
+}
+
+// Sort column norms descending (ties by index) into sigma/perm and pick the
+// truncation rank (same rule as jacobi_svd_kernel). One CTA.
+template <typename R>
+__global__ void jacobi_finish_kernel(int n, const R* snorm, double* sigma, int* perm,
+                                     double delta2, int rmax, int* trunc,
+                                     int values_are_squares, const int* sweeps) {
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const R sj = isnan(snorm[j]) ? (R)-1 : snorm[j];
+    if (isnan(snorm[j])) trunc[4] = 1;
+    int rk = 0;
+    for (int i = 0; i < n; ++i) {
+      const R si = isnan(snorm[i]) ? (R)-1 : snorm[i];
+      rk += (si > sj) || (si == sj && i < j);
+    }
+    perm[rk] = j;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tail = 0;
+    for (int j = n - 1; j >= 0; --j) {
+      const double s = (double)snorm[perm[j]];
+      tail += values_are_squares ? s : s * s;
+      sigma[j] = tail;
+    }
+    int k = n;
+    for (int j = 1; j < n; ++j)
+      if (sigma[j] <= delta2) {
+        k = j;
+        break;
+      }
+    trunc[1] = (k > rmax) ? 1 : 0;
+    trunc[0] = k < rmax ? k : rmax;
+    trunc[2] = *sweeps;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const R v = snorm[perm[j]];
+    sigma[j] = isnan(v) ? 0.0 : (double)v;
+  }
 }
 
 // Reorders/normalises columns after jacobi_svd_kernel: Uout[:, j] =
 // A[:, perm[j]] / sigma_j (0 when sigma_j == 0), Vout[:, j] = V[:, perm[j]].
 template <typename R>
 __global__ void svd_finish_kernel(int m, int n, const Cx<R>* A, const Cx<R>* V, const double* sigma,
-                                  const int* perm, Cx<R>* Uout, Cx<R>* Vout) {
-  const long long tot = (long long)m * n + (long long)n * n;
+                                  const int* perm, Cx<R>* Uout, Cx<R>* Vout, int* err, int want_v) {
+  const long long tot = (long long)m * n + (want_v ? (long long)n * n : 0ll);
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
        e += (long long)gridDim.x * blockDim.x) {
+    const int pj = perm[(e < (long long)m * n) ? (int)(e / m) : (int)((e - (long long)m * n) / n)];
+    if (pj < 0 || pj >= n) {  // data-dependent index: check, record, skip
+      atomicExch(err, 1);
+      continue;
+    }
     if (e < (long long)m * n) {
       const int i = (int)(e % m), j = (int)(e / m);
       const double s = sigma[j];
-      const Cx<R> a = A[(long long)perm[j] * m + i];
+      const Cx<R> a = A[(long long)pj * m + i];
       Uout[e] = s > 0 ? mk<R>((R)(a.x / s), (R)(a.y / s)) : mk<R>(0, 0);
     } else {
       const long long f = e - (long long)m * n;
-      const int i = (int)(f % n), j = (int)(f / n);
-      Vout[f] = V[(long long)perm[j] * n + i];
+      const int i = (int)(f % n);
+      Vout[f] = V[(long long)pj * n + i];
     }
   }
 }
@@ -504,6 +664,18 @@ __global__ void norm2_kernel(const Cx<R>* __restrict__ x, long long n, double* o
     s += (double)x[e].x * x[e].x + (double)x[e].y * x[e].y;
   s = warp_sum(s);
   if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
+}
+
+// x /= sqrt(*nrm2) (no-op when the norm is 0): keeps the random sketch
+// environments at unit scale; only their range matters downstream.
+template <typename R>
+__global__ void scale_inv_norm_kernel(Cx<R>* x, long long n, const double* nrm2) {
+  const double s2 = *nrm2;
+  if (!(s2 > 0.0)) return;
+  const R inv = (R)(1.0 / sqrt(s2));
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x)
+    x[e] = cscale(x[e], inv);
 }
 
 // ------------------------------------------------------------------ Philox sketches
@@ -611,6 +783,42 @@ __global__ void stiffness_field_kernel(const uint8_t* phase, long long cells, co
     int p = phase[c];
     if (p >= nphase) p = nphase - 1;
     for (int P = 0; P < 36; ++P) out[(long long)P * cells + c] = mk<double>(dC[p * 36 + P], 0.0);
+  }
+}
+
+// Squared column norms (FP64) of a row-major P x c matrix, accumulated into
+// out[c] (zeroed by the caller); each CTA sums a slab of rows in shared memory.
+template <typename R>
+__global__ void colnorm2_kernel(const Cx<R>* __restrict__ M, long long P, int c, double* out) {
+  extern __shared__ double cn_acc[];
+  for (int j = threadIdx.x; j < c; j += blockDim.x) cn_acc[j] = 0;
+  __syncthreads();
+  const long long tot = P * c;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const Cx<R> v = M[e];
+    atomicAdd(&cn_acc[e % c], (double)v.x * v.x + (double)v.y * v.y);
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < c; j += blockDim.x) atomicAdd(&out[j], cn_acc[j]);
+}
+
+// dst[r * k + a] = src[r * c + idx[a]] for a row-major P x c source.
+template <typename R>
+__global__ void gather_cols_kernel(const Cx<R>* __restrict__ src, long long P, int c,
+                                   const int* __restrict__ idx, int k, Cx<R>* __restrict__ dst,
+                                   int* err) {
+  const long long tot = P * k;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long r = e / k;
+    const int a = (int)(e % k);
+    const int j = idx[a];
+    if (j < 0 || j >= c) {  // data-dependent index: check, record, skip
+      atomicExch(err, 1);
+      continue;
+    }
+    dst[e] = src[r * c + j];
   }
 }
 

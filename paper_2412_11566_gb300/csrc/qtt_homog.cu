@@ -12,7 +12,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <map>
+#include <mutex>
+#include <thread>
 #include <stdexcept>
 #include <string>
 #include <tuple>
@@ -48,6 +51,7 @@ struct QttError : std::runtime_error {
 struct Arena {
   char* base = nullptr;
   size_t size = 0, used = 0, peak = 0;
+  std::mutex mu;  // lanes own separate arenas; the lock guards misuse
   std::map<size_t, size_t> free_;   // offset -> bytes
   std::map<size_t, size_t> taken_;  // offset -> bytes
   void init(void* b, size_t s) {
@@ -59,10 +63,13 @@ struct Arena {
     used = peak = 0;
   }
   void* alloc(size_t bytes) {
+    std::lock_guard<std::mutex> g(mu);
     bytes = std::max<size_t>(256, (bytes + 255) & ~(size_t)255);
     for (auto it = free_.begin(); it != free_.end(); ++it) {
       if (it->second >= bytes) {
         const size_t off = it->first, rem = it->second - bytes;
+        if (off + bytes > size)
+          throw QttError(QTT_EINVAL, "workspace allocator state corrupted");
         free_.erase(it);
         if (rem) free_[off + bytes] = rem;
         taken_[off] = bytes;
@@ -75,7 +82,8 @@ struct Arena {
                                    " bytes, " + std::to_string(size - used) + " free");
   }
   // Bytes from p to the end of the allocation holding p, or -1.
-  long long extent(const void* p) const {
+  long long extent(const void* p) {
+    std::lock_guard<std::mutex> g(mu);
     if (!p || (const char*)p < base || (const char*)p >= base + size) return -1;
     const size_t off = (const char*)p - base;
     auto it = taken_.upper_bound(off);
@@ -86,6 +94,7 @@ struct Arena {
   }
   void release(void* p) {
     if (!p) return;
+    std::lock_guard<std::mutex> g(mu);
     const size_t off = (char*)p - base;
     auto it = taken_.find(off);
     if (it == taken_.end()) return;
@@ -111,6 +120,15 @@ struct Arena {
   }
 };
 
+// An execution lane: a stream, the arena its temporaries come from, and a
+// pinned host buffer for small readbacks. Work on one lane is stream-ordered,
+// so arena memory released on a lane can be reused by that lane at once.
+struct Lane {
+  Arena* arena = nullptr;
+  cudaStream_t stream = nullptr;
+  void* pinned = nullptr;
+};
+
 }  // namespace
 
 struct qtt_tt;
@@ -122,8 +140,13 @@ struct qtt_ctx {
   int prec = QTT_FP64;
   uint64_t seed = 0;
   Arena arena;
+  Lane lane0;  // the context's own stream and arena
   std::string err;
-  uint64_t launches = 0;
+  std::atomic<uint64_t> launches{0};
+  std::mutex prof_mu;
+  int concurrent_loads = 1;  // load cases of ls_solve_ceff run side by side
+  double jacobi_tol_scale = 1.0;   // Jacobi stop: |a_p^H a_q| <= scale sqrt(m) eps |a_p||a_q|
+  int jacobi_max_sweeps32 = 40;    // sweep cap in FP32 mode
   void* pinned = nullptr;  // small host readback buffer
   // Optional per-kernel-class timing: events recorded around launches,
   // resolved lazily (class: 0 gemm, 1 qr, 2 svd).
@@ -135,6 +158,7 @@ struct qtt_ctx {
   };
   std::vector<Ev> evs;
   double prof_ms[3] = {0, 0, 0};
+  double prof_sweeps = 0;  // Jacobi sweeps run (sum over SVD launches)
   double prof_flops[3] = {0, 0, 0};
   long long prof_n[3] = {0, 0, 0};
   std::map<std::pair<int, int>, qtt_op*> sfft_cache;                            // (n, adjoint)
@@ -160,17 +184,20 @@ struct ProfScope {
   qtt_ctx* c;
   qtt_ctx::Ev e{};
   bool on;
-  ProfScope(qtt_ctx* ctx, int cls, double flops) : c(ctx), on(ctx->profiling != 0) {
+  cudaStream_t s;
+  ProfScope(qtt_ctx* ctx, cudaStream_t stream, int cls, double flops)
+      : c(ctx), on(ctx->profiling != 0), s(stream) {
     if (!on) return;
     e.cls = cls;
     e.flops = flops;
     cudaEventCreate(&e.a);
     cudaEventCreate(&e.b);
-    cudaEventRecord(e.a, c->stream);
+    cudaEventRecord(e.a, s);
   }
   ~ProfScope() {
     if (!on) return;
-    cudaEventRecord(e.b, c->stream);
+    cudaEventRecord(e.b, s);
+    std::lock_guard<std::mutex> g(c->prof_mu);
     c->evs.push_back(e);
     if (c->evs.size() > 4096) prof_flush(c);
   }
@@ -178,6 +205,7 @@ struct ProfScope {
 
 struct qtt_tt {
   qtt_ctx* ctx = nullptr;
+  Arena* arena = nullptr;  // where the cores live
   int L = 0;
   int dims[QTT_MAX_CORES] = {0};
   int ranks[QTT_MAX_CORES + 1] = {0};
@@ -231,18 +259,35 @@ int grid1d(long long n, int threads = 256) {
 template <typename R>
 struct Eng {
   qtt_ctx* c;
-  explicit Eng(qtt_ctx* ctx) : c(ctx) {}
-  cudaStream_t st() const { return c->stream; }
-  void post() {
+  Lane* ln;
+  explicit Eng(qtt_ctx* ctx, Lane* lane = nullptr) : c(ctx), ln(lane ? lane : &ctx->lane0) {}
+  cudaStream_t st() const { return ln->stream; }
+  // After every launch: count it and surface launch errors. With the
+  // environment variable QTT_SYNC_EACH_LAUNCH=1 the stream is synchronised
+  // too, so that an execution fault is reported against the kernel (name and
+  // line of the launch) that caused it.
+  void post(const char* what = nullptr, int line = 0) {
     ++c->launches;
     QCHECK(cudaGetLastError());
+    static const bool sync_each = [] {
+      const char* v = getenv("QTT_SYNC_EACH_LAUNCH");
+      return v && v[0] == '1';
+    }();
+    if (sync_each) {
+      const cudaError_t e = cudaStreamSynchronize(st());
+      if (e != cudaSuccess)
+        throw QttError(QTT_ECUDA, std::string("kernel fault after launch ") +
+                                      (what ? what : "?") + " (line " + std::to_string(line) +
+                                      "): " + cudaGetErrorString(e));
+    }
   }
-  Cx<R>* alloc(long long count) { return (Cx<R>*)c->arena.alloc((size_t)count * sizeof(Cx<R>)); }
+  Cx<R>* alloc(long long count) { return (Cx<R>*)ln->arena->alloc((size_t)count * sizeof(Cx<R>)); }
   // Host-side launch validation: the largest element offset a strided access
   // reaches must lie inside the workspace allocation the pointer belongs to.
   void check_span(const void* p, long long max_off, const char* what) {
     if (max_off < 0) return;
-    const long long ext = c->arena.extent(p);
+    long long ext = ln->arena->extent(p);
+    if (ext < 0 && ln->arena != &c->arena) ext = c->arena.extent(p);  // shared operators
     if (ext < 0 || (max_off + 1) * (long long)sizeof(Cx<R>) > ext)
       throw QttError(QTT_EINVAL, std::string("launch bounds check failed: ") + what +
                                      " needs " + std::to_string((max_off + 1) * sizeof(Cx<R>)) +
@@ -254,7 +299,7 @@ struct Eng {
     if (n0 <= 0 || n1 <= 0 || n2 <= 0 || n3 <= 0 || n4 <= 0) return -1;
     return (n0 - 1) * s0 + (n1 - 1) * s1 + (n2 - 1) * s2 + (n3 - 1) * s3 + (n4 - 1) * s4;
   }
-  void release(void* p) { c->arena.release(p); }
+  void release(void* p) { ln->arena->release(p); }
 
   // C = alpha op(A) op(B) + beta C over a (nb1, nb2, nb3) batch.
   void gemm(int M, int N, int K, MatRef A, MatRef B, void* C, long long c_rs, long long c_cs,
@@ -278,7 +323,7 @@ struct Eng {
             a.scale = 0.0;
             Cx<R>* cp = (Cx<R>*)C + b1 * c_b1 + b2 * c_b2 + b3 * c_b3;
             copy_kernel<R><<<grid1d((long long)M * N), 256, 0, st()>>>(cp, cp, a, (long long)M * N);
-            post();
+            post("copy_kernel", __LINE__);
           }
       return;
     }
@@ -348,13 +393,13 @@ struct Eng {
               Cx<R>* cp = (Cx<R>*)h.C + b1 * c_b1 + b2 * c_b2 + b3 * c_b3;
               copy_kernel<R><<<grid1d((long long)M * N), 256, 0, st()>>>(cp, cp, a,
                                                                           (long long)M * N);
-              post();
+              post("copy_kernel", __LINE__);
             }
       }
       const dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)(nb * per_b1));
-      ProfScope ps(c, 0, 8.0 * M * N * (double)K * nb * nb2 * nb3);
+      ProfScope ps(c, st(), 0, 8.0 * M * N * (double)K * nb * nb2 * nb3);
       gemm_kernel<R, BM, BN, BK, 4, 4><<<grid, block, 0, st()>>>(h);
-      post();
+      post("gemm_kernel", __LINE__);
     }
   }
 
@@ -381,11 +426,27 @@ struct Eng {
     if (scale != 0.0) check_span(in, mi, "copy in");
     check_span(out, mo, "copy out");
     copy_kernel<R><<<grid1d(tot), 256, 0, st()>>>((const Cx<R>*)in, (Cx<R>*)out, a, tot);
-    post();
+    post("copy_kernel", __LINE__);
   }
 
   void zero(void* p, long long count) {
     if (count > 0) QCHECK(cudaMemsetAsync(p, 0, (size_t)count * sizeof(Cx<R>), st()));
+  }
+
+  // Largest dynamic shared-memory allocation a one-CTA factorisation may
+  // use on this device (opt-in limit minus the kernels' static needs).
+  static size_t smem_cap() {
+    static const size_t cap = [] {  // initialised once, thread-safe
+      int dev = 0, v = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+      const size_t c = v > 2048 ? (size_t)v - 2048 : 0;
+      cudaFuncSetAttribute(qr_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c);
+      cudaFuncSetAttribute(jacobi_svd_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)c);
+      return c;
+    }();
+    return cap;
   }
 
   // Householder QR of the strided m x n matrix A: Q (m x k) and Rm (k x n),
@@ -396,15 +457,18 @@ struct Eng {
     check_span(Q, (long long)m * k - 1, "qr Q");
     check_span(Rm, (long long)k * n - 1, "qr R");
     Cx<R>* W = alloc((long long)m * n);
-    R* h = (R*)c->arena.alloc(sizeof(R) * std::max(1, k));
+    R* h = (R*)ln->arena->alloc(sizeof(R) * std::max(1, k));
     Cx<R>* v0 = alloc(std::max(1, k));
     {
       // complex Householder QR with explicit Q: 4 x (2 m n^2 - 2 n^3 / 3) real
       // flops for the factor plus as many for forming Q (LAPACK operation counts)
       const double kk = k;
-      ProfScope ps(c, 1, 2.0 * 4.0 * (2.0 * m * kk * kk - 2.0 * kk * kk * kk / 3.0));
-      qr_kernel<R><<<1, 1024, 0, st()>>>(m, n, (const Cx<R>*)A, rs, cs, conj, W, Q, Rm, h, v0);
-      post();
+      ProfScope ps(c, st(), 1, 2.0 * 4.0 * (2.0 * m * kk * kk - 2.0 * kk * kk * kk / 3.0));
+      const size_t bytes = (size_t)m * n * sizeof(Cx<R>);
+      const bool sm = bytes <= smem_cap();
+      qr_kernel<R><<<1, 1024, sm ? bytes : 0, st()>>>(m, n, (const Cx<R>*)A, rs, cs, conj, W, Q,
+                                                       Rm, h, v0, sm ? 1 : 0);
+      post("qr_kernel", __LINE__);
     }
     release(W);
     release(h);
@@ -414,53 +478,116 @@ struct Eng {
   // One-sided Jacobi SVD of the column-major m x n (m >= n) matrix in A
   // (destroyed): U (m x n), sigma (n, descending), V (n x n), all
   // column-major; returns the truncation rank for (delta2, rmax).
+  // SVD of a tall m x n matrix: Householder QR first, then Jacobi on the
+  // n x n triangular factor (which then fits shared memory far more often),
+  // U = Q U_R. Same contract as svd_direct.
+  // V == nullptr: the right singular vectors are not accumulated (cheaper
+  // rotations); the caller forms what it needs from U by a GEMM.
   int svd(int m, int n, Cx<R>* A, Cx<R>* U, double* sigma, Cx<R>* V, double delta2, int rmax,
           int* cap_hit, bool squares = false) {
+    if (squares || m <= n + n / 4) return svd_direct(m, n, A, U, sigma, V, delta2, rmax, cap_hit, squares);
+    Cx<R>* Q = alloc((long long)m * n);
+    Cx<R>* Rf = alloc((long long)n * n);
+    qr(m, n, A, 1, m, 0, Q, Rf);
+    Cx<R>* UR = alloc((long long)n * n);
+    const int k = svd_direct(n, n, Rf, UR, sigma, V, delta2, rmax, cap_hit, false);
+    gemm(m, n, n, mref(Q, 1, m), mref(UR, 1, n), U, 1, m, 0, 0, 0, 1, 1, 1);
+    release(Q);
+    release(Rf);
+    release(UR);
+    return k;
+  }
+
+  int svd_direct(int m, int n, Cx<R>* A, Cx<R>* U, double* sigma, Cx<R>* V, double delta2,
+                 int rmax, int* cap_hit, bool squares = false) {
     QREQ(m >= n && n >= 1, "svd: needs m >= n >= 1");
     QREQ(n <= 4096, "svd: too many columns");
     check_span(A, (long long)m * n - 1, "svd A");
     check_span(U, (long long)m * n - 1, "svd U");
-    check_span(V, (long long)n * n - 1, "svd V");
-    Cx<R>* Vw = alloc((long long)n * n);
-    int* perm = (int*)c->arena.alloc(sizeof(int) * n);
-    R* snorm = (R*)c->arena.alloc(sizeof(R) * n);
-    int* tr = (int*)c->arena.alloc(sizeof(int) * 4);
+    const bool want_v = V != nullptr;
+    if (want_v) check_span(V, (long long)n * n - 1, "svd V");
+    Cx<R>* Vw = want_v ? alloc((long long)n * n) : nullptr;
+    int* perm = (int*)ln->arena->alloc(sizeof(int) * n);
+    R* snorm = (R*)ln->arena->alloc(sizeof(R) * n);
+    int* tr = (int*)ln->arena->alloc(sizeof(int) * 8);
+    QCHECK(cudaMemsetAsync(tr, 0, sizeof(int) * 8, st()));
     const R eps = sizeof(R) == 8 ? (R)2.220446049250313e-16 : (R)1.1920929e-7;
-    const R tol = eps * (R)std::sqrt((double)m);
-    const int sweeps = sizeof(R) == 8 ? 60 : 40;
+    const R tol = eps * (R)std::sqrt((double)m) * (R)c->jacobi_tol_scale;
+    const int sweeps = sizeof(R) == 8 ? 60 : c->jacobi_max_sweeps32;
     {
       // flops counted for the sweeps actually run are not known here; the
       // profile records one sweep's count (n^2/2 pairs x (3 dots + 2
       // rotations of length m + 2 of length n) x 8 real flops) per launch
-      ProfScope ps(c, 2, 0.5 * n * (double)n * (5.0 * m + 2.0 * n) * 8.0);
-      jacobi_svd_kernel<R><<<1, 1024, 0, st()>>>(m, n, A, Vw, sigma, perm, snorm, delta2, rmax,
-                                                   tr, sweeps, tol, squares ? 1 : 0);
-      post();
+      ProfScope ps(c, st(), 2, 0.5 * n * (double)n * (5.0 * m + 2.0 * n) * 8.0);
+      const size_t bytes = (size_t)m * n * sizeof(Cx<R>);
+      const bool sm = bytes <= smem_cap();
+      if (sm || n < 64) {
+        jacobi_svd_kernel<R><<<1, 1024, sm ? bytes : 0, st()>>>(
+            m, n, A, Vw, sigma, perm, snorm, delta2, rmax, tr, sweeps, tol, squares ? 1 : 0,
+            sm ? 1 : 0, want_v ? 1 : 0);
+        post("jacobi_svd_kernel", __LINE__);
+      } else {
+        // too large for one CTA's shared memory: spread each round's pairs
+        // over the whole GPU (cooperative launch, grid-wide barriers)
+        int dev = 0, nsm = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        const int threads = 128;
+        QCHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_grid_kernel<R>,
+                                                             threads, 0));
+        const int want = ((n + 1) / 2 + (threads / 32) - 1) / (threads / 32);
+        const int blocks = std::max(1, std::min(want, nsm * std::max(1, per_sm)));
+        int* flags = (int*)ln->arena->alloc(sizeof(int) * (sweeps + 1));
+        QCHECK(cudaMemsetAsync(flags, 0, sizeof(int) * (sweeps + 1), st()));
+        const R eps_r = sizeof(R) == 8 ? (R)2.220446049250313e-16 : (R)1.1920929e-7;
+        R f2 = (R)norm2(A, (long long)m * n);
+        R negl = eps_r * eps_r * f2;
+        int mm = m, nn = n, ms = sweeps;
+        R tl = tol;
+        int* swp = tr + 3;
+        int wv = want_v ? 1 : 0;
+        void* args[] = {&mm, &nn, &A, &Vw, &snorm, &flags, &ms, &tl, &negl, &swp, &wv};
+        QCHECK(cudaLaunchCooperativeKernel((void*)jacobi_grid_kernel<R>, dim3(blocks),
+                                           dim3(threads), args, 0, st()));
+        post("jacobi_grid_kernel", __LINE__);
+        jacobi_finish_kernel<R><<<1, 256, 0, st()>>>(n, snorm, sigma, perm, delta2, rmax, tr,
+                                                     squares ? 1 : 0, swp);
+        post("jacobi_finish_kernel", __LINE__);
+        ln->arena->release(flags);
+      }
     }
-    svd_finish_kernel<R><<<grid1d((long long)m * n + (long long)n * n), 256, 0, st()>>>(
-        m, n, A, Vw, sigma, perm, U, V);
-    post();
-    int h[4];
-    QCHECK(cudaMemcpyAsync(c->pinned, tr, sizeof(int) * 4, cudaMemcpyDeviceToHost, st()));
+    svd_finish_kernel<R><<<grid1d((long long)m * n + (want_v ? (long long)n * n : 0)), 256, 0, st()>>>(
+        m, n, A, Vw, sigma, perm, U, V, tr + 5, want_v ? 1 : 0);
+    post("svd_finish_kernel", __LINE__);
+    int h[8];
+    QCHECK(cudaMemcpyAsync(ln->pinned, tr, sizeof(int) * 8, cudaMemcpyDeviceToHost, st()));
     QCHECK(cudaStreamSynchronize(st()));
-    memcpy(h, c->pinned, sizeof(int) * 4);
-    release(Vw);
+    memcpy(h, ln->pinned, sizeof(int) * 8);
+    if (Vw) release(Vw);
     release(perm);
     release(snorm);
     release(tr);
+    if (h[4]) throw QttError(QTT_ENAN, "svd: NaN in the singular values");
+    if (h[5]) throw QttError(QTT_EINVAL, "svd: permutation out of range (kernel skipped access)");
     if (cap_hit) *cap_hit = h[1];
+    if (c->profiling) {
+      // the launch was counted with one sweep; add the further sweeps run
+      std::lock_guard<std::mutex> g(c->prof_mu);
+      if (h[2] > 1) c->prof_flops[2] += (h[2] - 1) * 0.5 * n * (double)n * (5.0 * m + 2.0 * n) * 8.0;
+      c->prof_sweeps += h[2];
+    }
     return h[0];
   }
 
   double norm2(const void* p, long long count) {
-    double* d = (double*)c->arena.alloc(sizeof(double));
+    double* d = (double*)ln->arena->alloc(sizeof(double));
     QCHECK(cudaMemsetAsync(d, 0, sizeof(double), st()));
     norm2_kernel<R><<<grid1d(count), 256, 0, st()>>>((const Cx<R>*)p, count, d);
-    post();
-    QCHECK(cudaMemcpyAsync(c->pinned, d, sizeof(double), cudaMemcpyDeviceToHost, st()));
+    post("norm2_kernel", __LINE__);
+    QCHECK(cudaMemcpyAsync(ln->pinned, d, sizeof(double), cudaMemcpyDeviceToHost, st()));
     QCHECK(cudaStreamSynchronize(st()));
     double v;
-    memcpy(&v, c->pinned, sizeof(double));
+    memcpy(&v, ln->pinned, sizeof(double));
     release(d);
     return v;
   }
@@ -468,10 +595,11 @@ struct Eng {
 
 // ------------------------------------------------------------------ TT / op helpers
 
-qtt_tt* new_tt(qtt_ctx* c, int L, const int* dims) {
+qtt_tt* new_tt(qtt_ctx* c, Arena* a, int L, const int* dims) {
   QREQ(L >= 1 && L <= QTT_MAX_CORES, "TT core count out of range");
   qtt_tt* t = new qtt_tt();
   t->ctx = c;
+  t->arena = a;
   t->L = L;
   for (int k = 0; k < L; ++k) t->dims[k] = dims[k];
   t->ranks[0] = t->ranks[L] = 1;
@@ -480,7 +608,7 @@ qtt_tt* new_tt(qtt_ctx* c, int L, const int* dims) {
 
 void free_tt(qtt_tt* t) {
   if (!t) return;
-  for (int k = 0; k < t->L; ++k) t->ctx->arena.release(t->core[k]);
+  for (int k = 0; k < t->L; ++k) t->arena->release(t->core[k]);
   delete t;
 }
 
@@ -491,13 +619,13 @@ void free_op(qtt_op* o) {
 }
 
 void set_core(qtt_tt* t, int k, void* p) {
-  t->ctx->arena.release(t->core[k]);
+  t->arena->release(t->core[k]);
   t->core[k] = p;
 }
 
 template <typename R>
 qtt_tt* clone_tt(Eng<R>& e, const qtt_tt* x) {
-  qtt_tt* y = new_tt(e.c, x->L, x->dims);
+  qtt_tt* y = new_tt(e.c, e.ln->arena, x->L, x->dims);
   for (int k = 0; k <= x->L; ++k) y->ranks[k] = x->ranks[k];
   for (int k = 0; k < x->L; ++k) {
     y->core[k] = e.alloc(x->count(k));
@@ -526,24 +654,23 @@ int round_right_to_left(Eng<R>& e, qtt_tt* x, double eps, int rmax) {
     Cx<R>* newcore;
     Cx<R>* carry;  // r0 x kk, column-major (ld r0)
     if (m >= r0) {
-      // A = M^H (m x r0), M = core as r0 x m row-major.
+      // A = M^H (m x r0), M = core as r0 x m row-major. A = U S V^H gives
+      // M = V S U^H: new core = U[:, :kk]^H and carry = V S = M U[:, :kk],
+      // formed by a GEMM (no rotation accumulation of V needed).
       Cx<R>* A = e.alloc((long long)m * r0);
       const long long sz[2] = {r0, m}, ist[2] = {m, 1}, ost[2] = {m, 1};
       e.copy(core, A, 2, sz, ist, ost, 1);  // A[j + c m] = conj(M[c, j])
       Cx<R>* U = e.alloc((long long)m * r0);
-      Cx<R>* V = e.alloc((long long)r0 * r0);
-      double* sig = (double*)e.c->arena.alloc(sizeof(double) * r0);
-      kk = e.svd(m, r0, A, U, sig, V, delta2, rmax, &cap);
-      // M = V S U^H: new core = U[:, :kk]^H (kk x m), carry = V[:, :kk] S
+      double* sig = (double*)e.ln->arena->alloc(sizeof(double) * r0);
+      kk = e.svd(m, r0, A, U, sig, nullptr, delta2, rmax, &cap);
       newcore = e.alloc((long long)kk * m);
       const long long s2[2] = {kk, m}, i2[2] = {m, 1}, o2[2] = {m, 1};
       e.copy(U, newcore, 2, s2, i2, o2, 1);
-      carry = V;
-      scale_cols_kernel<R><<<grid1d((long long)r0 * kk), 256, 0, e.st()>>>(V, r0, kk, sig);
-      e.post();
+      carry = e.alloc((long long)r0 * kk);  // column-major r0 x kk
+      e.gemm(r0, kk, m, mref(core, m, 1), mref(U, 1, m), carry, 1, r0, 0, 0, 0, 1, 1, 1);
       e.release(A);
       e.release(U);
-      e.release(sig);
+      e.ln->arena->release(sig);
     } else {
       // M tall (r0 x m): Jacobi on its columns, M = U S V^H.
       Cx<R>* A = e.alloc((long long)r0 * m);
@@ -551,14 +678,14 @@ int round_right_to_left(Eng<R>& e, qtt_tt* x, double eps, int rmax) {
       e.copy(core, A, 2, sz, ist, ost, 0);  // column-major copy of M
       Cx<R>* U = e.alloc((long long)r0 * m);
       Cx<R>* V = e.alloc((long long)m * m);
-      double* sig = (double*)e.c->arena.alloc(sizeof(double) * m);
+      double* sig = (double*)e.ln->arena->alloc(sizeof(double) * m);
       kk = e.svd(r0, m, A, U, sig, V, delta2, rmax, &cap);
       newcore = e.alloc((long long)kk * m);
       const long long s2[2] = {kk, m}, i2[2] = {m, 1}, o2[2] = {m, 1};
       e.copy(V, newcore, 2, s2, i2, o2, 1);  // V^H rows
       carry = U;
       scale_cols_kernel<R><<<grid1d((long long)r0 * kk), 256, 0, e.st()>>>(U, r0, kk, sig);
-      e.post();
+      e.post("scale_cols_kernel", __LINE__);
       e.release(A);
       e.release(V);
       e.release(sig);
@@ -649,7 +776,7 @@ qtt_tt* apply_sketched(Eng<R>& e, const qtt_op* A, const qtt_tt* x, int ell, int
     Cx<R>* Om = e.alloc((long long)L0 * Dout * L1);
     sketch_kernel<R><<<grid1d((long long)L0 * Dout * L1), 256, 0, e.st()>>>(
         Om, (long long)L0 * Dout * L1, e.c->seed, k, apply_id);
-    e.post();
+    e.post("sketch_kernel", __LINE__);
     // S1: XP[i][s0][a1 l1] = sum_s1 X[s0, i, s1] Psi[s1, (a1 l1)]
     Cx<R>* XP = e.alloc((long long)Din * S0 * A1 * L1);
     e.gemm(S0, A1 * L1, S1, mref(x->core[k], (long long)Din * S1, 1, S1), mref(psi[k + 1], (long long)A1 * L1, 1),
@@ -679,10 +806,23 @@ qtt_tt* apply_sketched(Eng<R>& e, const qtt_op* A, const qtt_tt* x, int ell, int
     }
     e.release(XP);
     e.release(Om);
+    {
+      // Psi_k grows like sqrt(ell) per core (a product of random sketches):
+      // rescale it to unit norm on the device. The compression below uses
+      // only the range of T Psi, so the result does not change.
+      const long long cnt = (long long)S0 * A0 * L0;
+      double* nrm = (double*)e.ln->arena->alloc(sizeof(double));
+      QCHECK(cudaMemsetAsync(nrm, 0, sizeof(double), e.st()));
+      norm2_kernel<R><<<grid1d(cnt), 256, 0, e.st()>>>(Pk, cnt, nrm);
+      e.post("norm2_kernel", __LINE__);
+      scale_inv_norm_kernel<R><<<grid1d(cnt), 256, 0, e.st()>>>(Pk, cnt, nrm);
+      e.post("scale_inv_norm_kernel", __LINE__);
+      e.ln->arena->release(nrm);
+    }
     psi[k] = Pk;
   }
   // ---- left-to-right compression
-  qtt_tt* y = new_tt(e.c, L, A->dout);
+  qtt_tt* y = new_tt(e.c, e.ln->arena, L, A->dout);
   Cx<R>* C = e.alloc(1);  // carry (R, S0, A0)
   {
     Cx<R> one = mk<R>(1, 0);
@@ -769,7 +909,7 @@ qtt_tt* tt_add(Eng<R>& e, const qtt_tt* a, const qtt_tt* b, double alpha, double
   const int L = a->L;
   QREQ(b->L == L && L >= 2, "tt_add: core counts differ or L < 2");
   for (int k = 0; k < L; ++k) QREQ(a->dims[k] == b->dims[k], "tt_add: dims differ");
-  qtt_tt* y = new_tt(e.c, L, a->dims);
+  qtt_tt* y = new_tt(e.c, e.ln->arena, L, a->dims);
   for (int k = 1; k < L; ++k) y->ranks[k] = a->ranks[k] + b->ranks[k];
   for (int k = 0; k < L; ++k) {
     const int d = a->dims[k];
@@ -799,7 +939,7 @@ qtt_tt* tt_add(Eng<R>& e, const qtt_tt* a, const qtt_tt* b, double alpha, double
 // <a, b> with FP64 transfer matrices.
 template <typename R>
 void tt_dot(Eng<R>& e, const qtt_tt* a, const qtt_tt* b, double* re, double* im) {
-  Eng<double> d(e.c);
+  Eng<double> d(e.c, e.ln);  // same lane: stream and arena of the caller
   const int L = a->L;
   QREQ(b->L == L, "dot: core counts differ");
   Cx<double>* E = d.alloc(1);
@@ -820,10 +960,10 @@ void tt_dot(Eng<R>& e, const qtt_tt* a, const qtt_tt* b, double* re, double* im)
       tB = d.alloc(b->count(k));
       convert_kernel<R, double><<<grid1d(a->count(k)), 256, 0, e.st()>>>(
           (const Cx<R>*)a->core[k], tA, a->count(k));
-      e.post();
+      e.post("convert_kernel", __LINE__);
       convert_kernel<R, double><<<grid1d(b->count(k)), 256, 0, e.st()>>>(
           (const Cx<R>*)b->core[k], tB, b->count(k));
-      e.post();
+      e.post("convert_kernel", __LINE__);
       Ak = tA;
       Bk = tB;
     }
@@ -841,9 +981,9 @@ void tt_dot(Eng<R>& e, const qtt_tt* a, const qtt_tt* b, double* re, double* im)
     E = F;
   }
   double h[2];
-  QCHECK(cudaMemcpyAsync(e.c->pinned, E, 16, cudaMemcpyDeviceToHost, e.st()));
+  QCHECK(cudaMemcpyAsync(e.ln->pinned, E, 16, cudaMemcpyDeviceToHost, e.st()));
   QCHECK(cudaStreamSynchronize(e.st()));
-  memcpy(h, e.c->pinned, 16);
+  memcpy(h, e.ln->pinned, 16);
   d.release(E);
   *re = h[0];
   *im = h[1];
@@ -852,7 +992,7 @@ void tt_dot(Eng<R>& e, const qtt_tt* a, const qtt_tt* b, double* re, double* im)
 // Grid mean of (A x): first core full (1, Dout, Din, a1), binary cores raised.
 template <typename R>
 void op_mean(Eng<R>& e, const qtt_op* A, const qtt_tt* x, std::vector<double>& out) {
-  Eng<double> d(e.c);
+  Eng<double> d(e.c, e.ln);  // same lane: stream and arena of the caller
   const int L = x->L;
   QREQ(A->L == L, "mean: core counts differ");
   QREQ(!A->diag[0], "mean: first operator core must be full");
@@ -863,7 +1003,7 @@ void op_mean(Eng<R>& e, const qtt_op* A, const qtt_tt* x, std::vector<double>& o
       QCHECK(cudaMemcpyAsync(t, p, cnt * 16, cudaMemcpyDeviceToDevice, e.st()));
     } else {
       convert_kernel<R, double><<<grid1d(cnt), 256, 0, e.st()>>>((const Cx<R>*)p, t, cnt);
-      e.post();
+      e.post("convert_kernel", __LINE__);
     }
     return t;
   };
@@ -899,9 +1039,9 @@ void op_mean(Eng<R>& e, const qtt_op* A, const qtt_tt* x, std::vector<double>& o
   }
   out.assign(2 * Do, 0.0);
   std::vector<double> h(2 * Do);
-  QCHECK(cudaMemcpyAsync(e.c->pinned, V, 16 * Do, cudaMemcpyDeviceToHost, e.st()));
+  QCHECK(cudaMemcpyAsync(e.ln->pinned, V, 16 * Do, cudaMemcpyDeviceToHost, e.st()));
   QCHECK(cudaStreamSynchronize(e.st()));
-  memcpy(h.data(), e.c->pinned, 16 * Do);
+  memcpy(h.data(), e.ln->pinned, 16 * Do);
   d.release(V);
   out = h;
 }
@@ -921,47 +1061,142 @@ std::vector<Cx<double>*> tt_svd_device(Eng<double>& e, Cx<double>* T, const std:
   Cx<double>* M = T;
   bool own_M = false;
   double delta2 = 0;
+  {
+    long long tot = 1;
+    for (int d : dims) tot *= d;
+    delta2 = L > 1 ? eps * eps * e.norm2(T, tot) / (double)(L - 1) : 0.0;
+  }
   for (int j = L - 1; j >= 1; --j) {
     const int c = dims[j] * ranks[j + 1];
     const long long P = prod_dims(dims.data(), 0, j);
     QREQ(P < (1ll << 31), "TT-SVD unfolding too large");
+    if (8.0 * (double)P * c * std::min<double>(P, c) < 2e9) {
+      // Small unfolding: accurate SVD of M itself (QR + one-sided Jacobi; no
+      // squared condition number). M = U S V^H, core j = V[:, :kk]^H, carry
+      // = U[:, :kk] S (row-major P x kk for the next reshape).
+      const int m0 = (int)std::max<long long>(P, c), n0 = (int)std::min<long long>(P, c);
+      Cx<double>* A = e.alloc((long long)P * c);
+      Cx<double>* Uw = e.alloc((long long)m0 * n0);
+      Cx<double>* Vw = e.alloc((long long)n0 * n0);
+      double* sg = (double*)e.ln->arena->alloc(sizeof(double) * n0);
+      int cap = 0, kk;
+      Cx<double>* core;
+      Cx<double>* Mn = e.alloc(P * std::min<long long>(P, c));
+      if (P >= c) {
+        const long long sz[2] = {P, c}, ist[2] = {c, 1}, ost[2] = {1, P};
+        e.copy(M, A, 2, sz, ist, ost);  // column-major copy
+        kk = e.svd((int)P, c, A, Uw, sg, Vw, delta2, rmax, &cap);
+        core = e.alloc((long long)kk * c);
+        const long long s2[2] = {kk, c}, i2[2] = {c, 1}, o2[2] = {c, 1};
+        e.copy(Vw, core, 2, s2, i2, o2, 1);  // V[:, :kk]^H
+        scale_cols_kernel<double><<<grid1d(P * kk), 256, 0, e.st()>>>(Uw, (int)P, kk, sg);
+        e.post("scale_cols_kernel", __LINE__);
+        const long long s3[2] = {P, kk}, i3[2] = {1, P}, o3[2] = {kk, 1};
+        e.copy(Uw, Mn, 2, s3, i3, o3);
+      } else {
+        // wide: A = M^H (c x P), M^H = U' S V'^H -> M = V' S U'^H
+        const long long sz[2] = {P, c}, ist[2] = {c, 1}, ost[2] = {c, 1};
+        e.copy(M, A, 2, sz, ist, ost, 1);  // A[jc + p c] = conj(M[p, jc])
+        kk = e.svd(c, (int)P, A, Uw, sg, Vw, delta2, rmax, &cap);
+        core = e.alloc((long long)kk * c);
+        const long long s2[2] = {kk, c}, i2[2] = {c, 1}, o2[2] = {c, 1};
+        e.copy(Uw, core, 2, s2, i2, o2, 1);  // U'[:, :kk]^H
+        scale_cols_kernel<double><<<grid1d(P * kk), 256, 0, e.st()>>>(Vw, (int)P, kk, sg);
+        e.post("scale_cols_kernel", __LINE__);
+        const long long s3[2] = {P, kk}, i3[2] = {1, P}, o3[2] = {kk, 1};
+        e.copy(Vw, Mn, 2, s3, i3, o3);
+      }
+      e.release(A);
+      e.release(Uw);
+      e.release(Vw);
+      e.ln->arena->release(sg);
+      cores[j] = core;
+      ranks[j] = kk;
+      if (own_M) e.release(M);
+      M = Mn;
+      own_M = true;
+      continue;
+    }
+    if (c > 4096)
+      throw QttError(QTT_EINVAL, "TT-SVD: bond " + std::to_string(j) + " of " +
+                                     std::to_string(L) + " too wide (c = " + std::to_string(c) +
+                                     ", dims[j] = " + std::to_string(dims[j]) +
+                                     ", eps = " + std::to_string(eps) + ")");
+    // eigenvectors V of the Gram matrix G = M^H M (column-major for the
+    // Jacobi kernel)
     Cx<double>* G = e.alloc((long long)c * c);
-    const int ks = (int)std::min<long long>(std::max<long long>(1, P / 8192), 4096 / std::max(1, (c / 64 + 1) * (c / 64 + 1)));
-    // G column-major (the Jacobi kernel's layout): G[a + b c] = sum_p conj(M[p, a]) M[p, b]
+    const int ks = (int)std::min<long long>(std::max<long long>(1, P / 8192),
+                                            4096 / std::max(1, (c / 64 + 1) * (c / 64 + 1)));
     e.gemm(c, c, (int)P, mref(M, 1, c, 0, 0, 0, 1), mref(M, c, 1), G, 1, c, 0, 0, 0, 1, 1, 1,
            Cplx{1, 0}, Cplx{0, 0}, std::max(1, ks));
-    if (j == L - 1) {
-      // ||T||^2 = trace(G)
-      Cx<double>* dg = e.alloc(c);
-      const long long sz[1] = {c}, ist[1] = {(long long)c + 1}, ost[1] = {1};
-      e.copy(G, dg, 1, sz, ist, ost);
-      // trace = sum Re(G_ii); G_ii >= 0 so sum sqrt(|G_ii|^2)
-      std::vector<double> h(2 * c);
-      QCHECK(cudaMemcpyAsync(h.data(), dg, 16 * (size_t)c, cudaMemcpyDeviceToHost, e.st()));
-      QCHECK(cudaStreamSynchronize(e.st()));
-      double t = 0;
-      for (int i = 0; i < c; ++i) t += h[2 * i];
-      delta2 = L > 1 ? eps * eps * t / (double)(L - 1) : 0.0;
-      e.release(dg);
-    }
     Cx<double>* U = e.alloc((long long)c * c);
     Cx<double>* V = e.alloc((long long)c * c);
-    double* sig = (double*)e.c->arena.alloc(sizeof(double) * c);
+    double* sig = (double*)e.ln->arena->alloc(sizeof(double) * c);
     int cap = 0;
-    const int kk = e.svd(c, c, G, U, sig, V, delta2, rmax, &cap, true);
+    e.svd(c, c, G, U, sig, V, 0.0, c, &cap, true);
     e.release(G);
     e.release(U);
     e.release(sig);
-    // core j = V[:, :kk]^H  (kk x c) = (kk, d_j, r_{j+1})
+    // MV (P x c): its column norms are the singular values to working
+    // accuracy (the Gram eigenvalues carry noise ~ c eps lambda_max, which
+    // would swamp the tail threshold for wide bonds); they decide the rank.
+    Cx<double>* MV = e.alloc(P * c);
+    e.gemm((int)P, c, c, mref(M, c, 1), mref(V, 1, c), MV, c, 1, 0, 0, 0, 1, 1, 1);
+    double* cn = (double*)e.ln->arena->alloc(sizeof(double) * c);
+    QCHECK(cudaMemsetAsync(cn, 0, sizeof(double) * c, e.st()));
+    colnorm2_kernel<double><<<grid1d(P * c), 256, sizeof(double) * c, e.st()>>>(MV, P, c, cn);
+    e.post("colnorm2_kernel", __LINE__);
+    std::vector<double> h(c);
+    QCHECK(cudaMemcpyAsync(e.ln->pinned, cn, sizeof(double) * c, cudaMemcpyDeviceToHost, e.st()));
+    QCHECK(cudaStreamSynchronize(e.st()));
+    memcpy(h.data(), e.ln->pinned, sizeof(double) * c);
+    e.ln->arena->release(cn);
+    std::vector<int> perm(c);
+    for (int i = 0; i < c; ++i) perm[i] = i;
+    std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return h[a] > h[b]; });
+    int kk = c;
+    double tail = 0;
+    std::vector<double> tails(c + 1, 0.0);
+    for (int i = c - 1; i >= 0; --i) tails[i] = (tail += h[perm[i]]);
+    for (int i = 1; i < c; ++i)
+      if (tails[i] <= delta2) {
+        kk = i;
+        break;
+      }
+    kk = std::max(1, std::min(kk, rmax));
+    int* didx = (int*)e.ln->arena->alloc(sizeof(int) * kk);
+    memcpy(e.ln->pinned, perm.data(), sizeof(int) * kk);  // pinned staging (kk <= 4096)
+    QCHECK(cudaMemcpyAsync(didx, e.ln->pinned, sizeof(int) * kk, cudaMemcpyHostToDevice, e.st()));
+    // core j = V[:, perm[:kk]]^H (kk x c): gather rows of V^H
+    Cx<double>* VH = e.alloc((long long)c * c);
+    {
+      const long long sz[2] = {c, c}, ist[2] = {c, 1}, ost[2] = {c, 1};
+      e.copy(V, VH, 2, sz, ist, ost, 1);  // VH[a][b] = conj(V[b, a]) (row a = column a of V)
+    }
     Cx<double>* core = e.alloc((long long)kk * c);
-    const long long sz[2] = {kk, c}, ist[2] = {c, 1}, ost[2] = {c, 1};
-    e.copy(V, core, 2, sz, ist, ost, 1);
+    for (int a = 0; a < kk; ++a)  // rows perm[0..kk) of VH
+      QCHECK(cudaMemcpyAsync(core + (long long)a * c, VH + (long long)perm[a] * c,
+                             sizeof(Cx<double>) * c, cudaMemcpyDeviceToDevice, e.st()));
+    e.release(VH);
+    e.release(V);
     cores[j] = core;
     ranks[j] = kk;
-    // carry M V[:, :kk] (P x kk)
+    // carry = MV[:, perm[:kk]] (P x kk)
     Cx<double>* Mn = e.alloc(P * kk);
-    e.gemm((int)P, kk, c, mref(M, c, 1), mref(V, 1, c), Mn, kk, 1, 0, 0, 0, 1, 1, 1);
-    e.release(V);
+    int* gerr = (int*)e.ln->arena->alloc(sizeof(int));
+    QCHECK(cudaMemsetAsync(gerr, 0, sizeof(int), e.st()));
+    gather_cols_kernel<double><<<grid1d(P * kk), 256, 0, e.st()>>>(MV, P, c, didx, kk, Mn, gerr);
+    e.post("gather_cols_kernel", __LINE__);
+    {
+      int hg = 0;
+      QCHECK(cudaMemcpyAsync(e.ln->pinned, gerr, sizeof(int), cudaMemcpyDeviceToHost, e.st()));
+      QCHECK(cudaStreamSynchronize(e.st()));
+      memcpy(&hg, e.ln->pinned, sizeof(int));
+      e.ln->arena->release(gerr);
+      if (hg) throw QttError(QTT_EINVAL, "TT-SVD: column index out of range (kernel skipped access)");
+    }
+    e.ln->arena->release(didx);
+    e.release(MV);
     if (own_M) e.release(M);
     M = Mn;
     own_M = true;
@@ -982,7 +1217,7 @@ void *to_prec(Eng<R>& e, Cx<double>* p, long long cnt) {
   if (sizeof(R) == 8) return p;
   Cx<R>* q = e.alloc(cnt);
   convert_kernel<double, R><<<grid1d(cnt), 256, 0, e.st()>>>(p, q, cnt);
-  e.post();
+  e.post("convert_kernel", __LINE__);
   e.release(p);
   return q;
 }
@@ -1076,7 +1311,7 @@ qtt_op* build_sfft(qtt_ctx* c, int n, int adjoint, double eps) {
   const long long N = 1ll << n;
   Cx<double>* T = e.alloc(N * N);
   sfft_tensor_kernel<<<grid1d(N * N), 256, 0, e.st()>>>((double*)T, n);
-  e.post();
+  e.post("sfft_tensor_kernel", __LINE__);
   std::vector<int> dims(n, 4), ranks;
   std::vector<Cx<double>*> ax = tt_svd_device(e, T, dims, eps, 1 << 30, ranks);
   e.release(T);
@@ -1171,7 +1406,7 @@ qtt_op* build_gamma(qtt_ctx* c, int n, double lam0, double mu0, int scheme, doub
   const long long N3 = 1ll << (3 * n);
   Cx<double>* F = e.alloc(36 * N3);
   gamma_field_kernel<<<grid1d(N3), 256, 0, e.st()>>>(F, n, lam0, mu0);
-  e.post();
+  e.post("gamma_field_kernel", __LINE__);
   const int bc[3] = {0, 0, 0};
   qtt_op* o = raised_from_field(c, F, n, bc, eps, rmax);
   e.release(F);
@@ -1204,9 +1439,9 @@ qtt_op* cached_gamma(qtt_ctx* c, int n, double lam0, double mu0, int scheme, dou
 // E field as a rank-1 controlled QTT: Voigt core E sqrt(2)^(3n), binary
 // cores (1, 1)/sqrt(2).
 template <typename R>
-qtt_tt* e_field(qtt_ctx* c, int L, const int* dims, const double* Ev) {
-  Eng<R> e(c);
-  qtt_tt* t = new_tt(c, L, dims);
+qtt_tt* e_field(qtt_ctx* c, Lane* ln, int L, const int* dims, const double* Ev) {
+  Eng<R> e(c, ln);
+  qtt_tt* t = new_tt(c, e.ln->arena, L, dims);
   for (int k = 0; k <= L; ++k) t->ranks[k] = 1;
   double scale = 1.0;
   for (int k = 1; k < L; ++k) scale *= std::sqrt((double)dims[k]);
@@ -1233,11 +1468,11 @@ int max_rank(const qtt_tt* t) {
 template <typename R>
 int solve_impl(qtt_ctx* c, const qtt_op* dC, const qtt_op* S, const qtt_op* Sh, const qtt_op* G,
                const double* C0, const double* Ev, const qtt_solve_params* p, double* sig,
-               qtt_solve_info* info, int apply_base) {
-  Eng<R> e(c);
+               qtt_solve_info* info, int apply_base, Lane* lane = nullptr) {
+  Eng<R> e(c, lane);
   const auto t0 = std::chrono::steady_clock::now();
   const int L = dC->L;
-  qtt_tt* Ett = e_field<R>(c, L, dC->dout, Ev);
+  qtt_tt* Ett = e_field<R>(c, e.ln, L, dC->dout, Ev);
   double nE2 = 0;
   for (int i = 0; i < 6; ++i) nE2 += Ev[i] * Ev[i];
   double cells = 1.0;
@@ -1331,6 +1566,9 @@ int qtt_ctx_create(qtt_ctx_t* out, int device, void* cuda_stream, int precision,
     delete c;
     return QTT_ECUDA;
   }
+  c->lane0.arena = &c->arena;
+  c->lane0.stream = c->stream;
+  c->lane0.pinned = c->pinned;
   *out = c;
   return QTT_OK;
 }
@@ -1349,6 +1587,7 @@ const char* qtt_last_error(qtt_ctx_t c) { return c ? c->err.c_str() : "null cont
 
 int qtt_ctx_set_profiling(qtt_ctx_t c, int on) {
   if (!c) return QTT_EINVAL;
+  std::lock_guard<std::mutex> g(c->prof_mu);
   if (!on) prof_flush(c);
   c->profiling = on ? 1 : 0;
   return QTT_OK;
@@ -1356,26 +1595,30 @@ int qtt_ctx_set_profiling(qtt_ctx_t c, int on) {
 
 int qtt_ctx_profile(qtt_ctx_t c, int reset, double* out) {
   if (!c || !out) return QTT_EINVAL;
+  std::lock_guard<std::mutex> g(c->prof_mu);
   prof_flush(c);
   for (int i = 0; i < 3; ++i) {
     out[3 * i] = (double)c->prof_n[i];
     out[3 * i + 1] = c->prof_ms[i];
     out[3 * i + 2] = c->prof_flops[i];
   }
-  if (reset)
+  out[9] = c->prof_sweeps;
+  if (reset) {
     for (int i = 0; i < 3; ++i) c->prof_n[i] = 0, c->prof_ms[i] = 0, c->prof_flops[i] = 0;
+    c->prof_sweeps = 0;
+  }
   return QTT_OK;
 }
 size_t qtt_ctx_bytes_in_use(qtt_ctx_t c) { return c ? c->arena.used : 0; }
 size_t qtt_ctx_bytes_peak(qtt_ctx_t c) { return c ? c->arena.peak : 0; }
-uint64_t qtt_ctx_launches(qtt_ctx_t c) { return c ? c->launches : 0; }
+uint64_t qtt_ctx_launches(qtt_ctx_t c) { return c ? c->launches.load() : 0; }
 
 int qtt_tt_create(qtt_ctx_t ctx, int L, const int* dims, const int* ranks, const double* cores,
                   qtt_tt_t* out) {
   API_BEGIN(ctx)
   QREQ(ctx && out && dims && ranks && cores, "qtt_tt_create: null argument");
   QREQ(ranks[0] == 1 && ranks[L] == 1, "qtt_tt_create: boundary ranks must be 1");
-  qtt_tt* t = new_tt(ctx, L, dims);
+  qtt_tt* t = new_tt(ctx, &ctx->arena, L, dims);
   long long off = 0;
   const size_t es = ctx->esize();
   for (int k = 0; k <= L; ++k) {
@@ -1420,7 +1663,7 @@ int qtt_tt_from_dense(qtt_ctx_t ctx, int L, const int* dims, const double* dense
   std::vector<int> dv(dims, dims + L), ranks;
   std::vector<Cx<double>*> cores = tt_svd_device(e, T, dv, eps, rmax, ranks);
   e.release(T);
-  qtt_tt* t = new_tt(ctx, L, dims);
+  qtt_tt* t = new_tt(ctx, &ctx->arena, L, dims);
   for (int k = 0; k <= L; ++k) t->ranks[k] = ranks[k];
   if (ctx->prec == QTT_FP64) {
     for (int k = 0; k < L; ++k) t->core[k] = cores[k];
@@ -1604,7 +1847,7 @@ int qtt_from_phase_field(qtt_ctx_t ctx, const uint8_t* phase, const int shape[3]
                          ctx->stream));
   Cx<double>* F = e.alloc(36 * cells);
   stiffness_field_kernel<<<grid1d(cells), 256, 0, ctx->stream>>>(dph, cells, ddc, nphase, F);
-  e.post();
+  e.post("stiffness_field_kernel", __LINE__);
   QCHECK(cudaStreamSynchronize(ctx->stream));
   ctx->arena.release(dph);
   ctx->arena.release(ddc);
@@ -1741,27 +1984,105 @@ int ls_solve_ceff(qtt_ctx_t ctx, qtt_op_t dC, const qtt_solve_params* p, const i
                   int nloads, double* Ceff, qtt_solve_info* info) {
   API_BEGIN(ctx)
   QREQ(ctx && dC && p && Ceff, "ls_solve_ceff: null argument");
+  QREQ(dC->has_c0, "ls_solve_ceff: dC must come from qtt_from_phase_field");
   int all[6] = {0, 1, 2, 3, 4, 5};
   if (!loads) {
     loads = all;
     nloads = 6;
   }
   QREQ(nloads >= 1 && nloads <= 6, "ls_solve_ceff: nloads out of range");
+  for (int l = 0; l < nloads; ++l) QREQ(loads[l] >= 0 && loads[l] < 6, "ls_solve_ceff: bad load");
   for (int i = 0; i < 36; ++i) Ceff[i] = 0;
+  const int n = dC->n;
+  qtt_op* S = cached_sfft(ctx, n, 0);
+  qtt_op* Sh = cached_sfft(ctx, n, 1);
+  qtt_op* G = cached_gamma(ctx, n, dC->lame0[0], dC->lame0[1], p->scheme, p->eps_tt, 1 << 30);
+  QCHECK(cudaStreamSynchronize(ctx->stream));
+  const int nl = std::max(1, std::min(ctx->concurrent_loads, nloads));
+  // One lane per concurrently solved load: own stream, own slice of the
+  // workspace (so that no lane reuses memory another lane's kernels still
+  // touch), own pinned readback buffer. Operators are shared read-only.
+  std::vector<Lane> lanes(nl);
+  std::vector<Arena> arenas(nl);
+  std::vector<void*> blocks(nl, nullptr);
+  if (nl > 1) {
+    size_t freeb = 0;
+    {
+      std::lock_guard<std::mutex> g(ctx->arena.mu);
+      for (auto& kv : ctx->arena.free_) freeb = std::max(freeb, kv.second);
+    }
+    const size_t slice = ((freeb / nl) & ~(size_t)255) - 4096;
+    QREQ(slice >= (64u << 20), "ls_solve_ceff: workspace too small for concurrent loads");
+    for (int l = 0; l < nl; ++l) {
+      blocks[l] = ctx->arena.alloc(slice);
+      arenas[l].init(blocks[l], slice);
+      lanes[l].arena = &arenas[l];
+      QCHECK(cudaStreamCreateWithFlags(&lanes[l].stream, cudaStreamNonBlocking));
+      QCHECK(cudaMallocHost(&lanes[l].pinned, 1 << 16));
+    }
+  } else {
+    lanes[0] = ctx->lane0;
+  }
+  std::vector<int> status(nloads, QTT_OK);
+  std::vector<std::string> errs(nloads);
+  std::vector<std::vector<double>> sig(nloads, std::vector<double>(12, 0.0));
+  std::vector<qtt_solve_info> inf(nloads);
+  std::atomic<int> next{0};
+  auto worker = [&](int lane_id) {
+    cudaSetDevice(ctx->device);
+    for (int l = next++; l < nloads; l = next++) {
+      double Ev[6] = {0, 0, 0, 0, 0, 0};
+      Ev[loads[l]] = 1.0;
+      try {
+        status[l] = DISPATCH(ctx, solve_impl, ctx, dC, S, Sh, G, dC->C0, Ev, p, sig[l].data(),
+                             &inf[l], 0, &lanes[lane_id]);
+      } catch (const QttError& ex) {
+        status[l] = ex.code;
+        errs[l] = ex.what();
+      } catch (const std::exception& ex) {
+        status[l] = QTT_EINVAL;
+        errs[l] = ex.what();
+      }
+    }
+  };
+  if (nl > 1) {
+    std::vector<std::thread> th;
+    for (int l = 0; l < nl; ++l) th.emplace_back(worker, l);
+    for (auto& t : th) t.join();
+    for (int l = 0; l < nl; ++l) {
+      cudaStreamSynchronize(lanes[l].stream);
+      cudaStreamDestroy(lanes[l].stream);
+      cudaFreeHost(lanes[l].pinned);
+      ctx->arena.release(blocks[l]);
+    }
+  } else {
+    worker(0);
+  }
   int worst = QTT_OK;
   for (int l = 0; l < nloads; ++l) {
-    const int k = loads[l];
-    QREQ(k >= 0 && k < 6, "ls_solve_ceff: load index out of range");
-    double Ev[6] = {0, 0, 0, 0, 0, 0};
-    Ev[k] = 1.0;
-    double sig[12];
-    const int st = ls_solve(ctx, dC, Ev, p, sig, info ? info + l : nullptr);
-    if (st < 0) return st;
-    worst = std::max(worst, st);
-    for (int i = 0; i < 6; ++i) Ceff[k * 6 + i] = sig[2 * i];
+    if (status[l] < 0) {
+      ctx->err = errs[l];
+      return status[l];
+    }
+    worst = std::max(worst, status[l]);
+    for (int i = 0; i < 6; ++i) Ceff[loads[l] * 6 + i] = sig[l][2 * i];
+    if (info) info[l] = inf[l];
   }
   return worst;
   API_END
+}
+
+int qtt_ctx_set_jacobi(qtt_ctx_t ctx, double tol_scale, int max_sweeps_fp32) {
+  if (!ctx || !(tol_scale > 0) || max_sweeps_fp32 < 1 || max_sweeps_fp32 > 200) return QTT_EINVAL;
+  ctx->jacobi_tol_scale = tol_scale;
+  ctx->jacobi_max_sweeps32 = max_sweeps_fp32;
+  return QTT_OK;
+}
+
+int qtt_ctx_set_concurrency(qtt_ctx_t ctx, int concurrent_loads) {
+  if (!ctx || concurrent_loads < 1 || concurrent_loads > 6) return QTT_EINVAL;
+  ctx->concurrent_loads = concurrent_loads;
+  return QTT_OK;
 }
 
 }  // extern "C"

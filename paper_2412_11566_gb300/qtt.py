@@ -89,6 +89,8 @@ _sig("qtt_op_mean_apply", _i, [_p, _p, _p, _dp])
 _sig("ls_solve_ops", _i, [_p, _p, _p, _p, _p, _dp, _dp, C.POINTER(SolveParams), _dp,
                           C.POINTER(SolveInfo)])
 _sig("ls_solve", _i, [_p, _p, _dp, C.POINTER(SolveParams), _dp, C.POINTER(SolveInfo)])
+_sig("qtt_ctx_set_concurrency", _i, [_p, _i])
+_sig("qtt_ctx_set_jacobi", _i, [_p, _d, _i])
 _sig("ls_solve_ceff", _i, [_p, _p, C.POINTER(SolveParams), _ip, _i, _dp, C.POINTER(SolveInfo)])
 
 
@@ -162,15 +164,23 @@ class Context:
     def launches(self):
         return lib.qtt_ctx_launches(self.h)
 
+    def set_concurrency(self, loads: int):
+        self.check(lib.qtt_ctx_set_concurrency(self.h, int(loads)))
+
+    def set_jacobi(self, tol_scale: float = 1.0, max_sweeps_fp32: int = 40):
+        self.check(lib.qtt_ctx_set_jacobi(self.h, float(tol_scale), int(max_sweeps_fp32)))
+
     def set_profiling(self, on: bool):
         self.check(lib.qtt_ctx_set_profiling(self.h, int(on)))
 
     def profile(self, reset: bool = False):
         """{class: (launches, total_ms, algorithmic_flops)} for gemm, qr, svd."""
-        out = np.zeros(9)
+        out = np.zeros(10)
         self.check(lib.qtt_ctx_profile(self.h, int(reset), out.ctypes.data_as(_dp)))
-        return {name: (int(out[3 * i]), float(out[3 * i + 1]), float(out[3 * i + 2]))
-                for i, name in enumerate(("gemm", "qr", "svd"))}
+        d = {name: (int(out[3 * i]), float(out[3 * i + 1]), float(out[3 * i + 2]))
+             for i, name in enumerate(("gemm", "qr", "svd"))}
+        self.last_sweeps = float(out[9])
+        return d
 
     # ------------------------------------------------------------ handles
     def tt(self, cores):
