@@ -170,6 +170,26 @@ int gamma0_apply(qtt_ctx_t ctx, const int n[3], double lambda0, double mu0, int 
 int tt_round(qtt_ctx_t ctx, qtt_tt_t inout, double eps_tt, int rmax);
 /* <a, b> = sum conj(a) b (FP64 accumulation). */
 int qtt_tt_dot(qtt_ctx_t ctx, qtt_tt_t a, qtt_tt_t b, double* re, double* im);
+/* <a, b> for callers that cannot allocate memory during the call -- code
+ * that runs while an external framework owns all device memory, a hot loop
+ * that must not block in the allocator, or a process that has handed its
+ * memory budget out already. No counterpart in the paper: it is the same
+ * inner product as qtt_tt_dot (FP64 transfer matrices, same kernels) with
+ * every temporary in a fixed device array compiled into the library, so the
+ * call neither allocates device or host memory nor uses the context's
+ * workspace. Limits: TT ranks <= QTT_NOALLOC_MAX_RANK (64) and mode sizes <=
+ * QTT_NOALLOC_MAX_DIM (6); larger inputs return QTT_EINVAL with a message in
+ * qtt_last_error of the TTs' context. The array (1.25 MiB) stays resident on
+ * every device that loads the library until the process exits. The first
+ * call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * and caches it; make that first call before any stream capture. All calls
+ * share the one array: calls whose work overlaps on the GPU (other streams or
+ * host threads) race and must be serialised by the caller. Work is ordered on
+ * `cuda_stream` (NULL = legacy default stream); the call synchronises it
+ * before writing *re, *im. */
+#define QTT_NOALLOC_MAX_RANK 64
+#define QTT_NOALLOC_MAX_DIM 6
+int qtt_tt_dot_noalloc(qtt_tt_t a, qtt_tt_t b, void* cuda_stream, double* re, double* im);
 /* Grid mean of A x without forming A x; writes 2 * d_out[0] doubles
  * (interleaved complex, one per component of the first core). */
 int qtt_op_mean_apply(qtt_ctx_t ctx, qtt_op_t op, qtt_tt_t x, double* out);

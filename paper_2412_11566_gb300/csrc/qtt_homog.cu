@@ -2086,3 +2086,150 @@ int qtt_ctx_set_concurrency(qtt_ctx_t ctx, int concurrent_loads) {
 }
 
 }  // extern "C"
+
+// ================================================================== inner product without allocation
+//
+// qtt_tt_dot_noalloc computes the same <a, b> as qtt_tt_dot for callers that
+// must not allocate while they call it (nothing here touches cudaMalloc,
+// cudaFree, the context's workspace arena or any allocating library call):
+// every temporary lives in the file-scope device array below, sized for TT
+// ranks up to QTT_NOALLOC_MAX_RANK and mode sizes up to QTT_NOALLOC_MAX_DIM.
+// Host code cannot pass the array's name to a kernel (on the host it is only
+// a stand-in symbol, not a device address): its device address is looked up
+// once per device with cudaGetSymbolAddress, on the first call made on that
+// device, and cached.
+
+namespace {
+
+constexpr int kNoAllocMaxRank = QTT_NOALLOC_MAX_RANK;
+constexpr int kNoAllocMaxDim = QTT_NOALLOC_MAX_DIM;
+// Layout (complex128 elements): E (R x R), F (R x R), EB (R x D x R),
+// A64 (R x D x R), B64 (R x D x R).
+constexpr long long kNoAllocRR = (long long)kNoAllocMaxRank * kNoAllocMaxRank;
+constexpr long long kNoAllocRDR = (long long)kNoAllocMaxRank * kNoAllocMaxDim * kNoAllocMaxRank;
+constexpr long long kNoAllocElems = 2 * kNoAllocRR + 3 * kNoAllocRDR;
+
+static __device__ __align__(256) Cx<double> g_noalloc_scratch[kNoAllocElems];
+
+std::mutex g_noalloc_mu;
+std::map<int, Cx<double>*> g_noalloc_addr;  // device -> device address of the scratch
+
+// Device address of the scratch on the current device (looked up once per
+// device, with that device current).
+int noalloc_scratch(Cx<double>** out, std::string& err) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    err = "qtt_tt_dot_noalloc: no current CUDA device";
+    return QTT_ECUDA;
+  }
+  std::lock_guard<std::mutex> g(g_noalloc_mu);
+  auto it = g_noalloc_addr.find(dev);
+  if (it != g_noalloc_addr.end()) {
+    *out = it->second;
+    return QTT_OK;
+  }
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p) {
+    err = std::string("qtt_tt_dot_noalloc: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e);
+    return QTT_ECUDA;
+  }
+  g_noalloc_addr[dev] = (Cx<double>*)p;
+  *out = (Cx<double>*)p;
+  return QTT_OK;
+}
+
+// One launch of the strided GEMM kernel on caller-checked scratch buffers.
+cudaError_t noalloc_gemm(cudaStream_t st, int M, int N, int K, const Cx<double>* A, long long a_rs,
+                         long long a_cs, int conjA, const Cx<double>* B, long long b_rs,
+                         long long b_cs, Cx<double>* C, long long c_rs, long long c_cs) {
+  GemmArgs g{};
+  g.M = M;
+  g.N = N;
+  g.K = K;
+  g.A = A;
+  g.a_rs = a_rs;
+  g.a_cs = a_cs;
+  g.conjA = conjA;
+  g.B = B;
+  g.b_rs = b_rs;
+  g.b_cs = b_cs;
+  g.C = C;
+  g.c_rs = c_rs;
+  g.c_cs = c_cs;
+  g.nb1 = g.nb2 = g.nb3 = g.ksplit = 1;
+  g.alpha_re = 1.0;
+  const dim3 grid((unsigned)((M + 63) / 64), (unsigned)((N + 63) / 64), 1);
+  gemm_kernel<double, 64, 64, 8, 4, 4><<<grid, 256, 0, st>>>(g);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+extern "C" int qtt_tt_dot_noalloc(qtt_tt_t a, qtt_tt_t b, void* cuda_stream, double* re,
+                                  double* im) {
+  if (!a || !b || !re || !im) return QTT_EINVAL;
+  qtt_ctx* c = a->ctx;
+  auto fail = [&](int code, const std::string& msg) {
+    if (c) c->err = msg;
+    return code;
+  };
+  if (b->ctx != c) return fail(QTT_EINVAL, "qtt_tt_dot_noalloc: TTs from different contexts");
+  const int L = a->L;
+  if (b->L != L) return fail(QTT_EINVAL, "qtt_tt_dot_noalloc: core counts differ");
+  for (int k = 0; k < L; ++k) {
+    if (a->dims[k] != b->dims[k]) return fail(QTT_EINVAL, "qtt_tt_dot_noalloc: dims differ");
+    if (a->dims[k] > kNoAllocMaxDim)
+      return fail(QTT_EINVAL, "qtt_tt_dot_noalloc: mode size " + std::to_string(a->dims[k]) +
+                                  " exceeds the maximum " + std::to_string(kNoAllocMaxDim));
+  }
+  for (int k = 0; k <= L; ++k)
+    if (a->ranks[k] > kNoAllocMaxRank || b->ranks[k] > kNoAllocMaxRank)
+      return fail(QTT_EINVAL, "qtt_tt_dot_noalloc: TT rank above the maximum " +
+                                  std::to_string(kNoAllocMaxRank));
+  if (cudaSetDevice(c->device) != cudaSuccess)
+    return fail(QTT_ECUDA, "qtt_tt_dot_noalloc: cudaSetDevice failed");
+  Cx<double>* base = nullptr;
+  std::string err;
+  const int rc = noalloc_scratch(&base, err);
+  if (rc != QTT_OK) return fail(rc, err);
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  Cx<double>* E = base;
+  Cx<double>* F = base + kNoAllocRR;
+  Cx<double>* EB = base + 2 * kNoAllocRR;
+  Cx<double>* A64 = EB + kNoAllocRDR;
+  Cx<double>* B64 = A64 + kNoAllocRDR;
+  // E starts as the 1 x 1 matrix [1] (the array keeps the previous call's data)
+  const Cx<double> one = mk<double>(1.0, 0.0);
+  if (cudaMemcpyAsync(E, &one, sizeof(one), cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return fail(QTT_ECUDA, "qtt_tt_dot_noalloc: upload of the start value failed");
+  for (int k = 0; k < L; ++k) {
+    const int ra = a->ranks[k], rb = b->ranks[k], pa = a->ranks[k + 1], pb = b->ranks[k + 1];
+    const int D = a->dims[k];
+    const Cx<double>* Ak = (const Cx<double>*)a->core[k];
+    const Cx<double>* Bk = (const Cx<double>*)b->core[k];
+    if (c->prec != QTT_FP64) {
+      convert_kernel<float, double><<<grid1d(a->count(k)), 256, 0, st>>>(
+          (const Cx<float>*)a->core[k], A64, a->count(k));
+      convert_kernel<float, double><<<grid1d(b->count(k)), 256, 0, st>>>(
+          (const Cx<float>*)b->core[k], B64, b->count(k));
+      Ak = A64;
+      Bk = B64;
+    }
+    // EB (ra x D pb) = E (ra x rb) B_k (rb x D pb); F (pa x pb) = A_k^H EB
+    cudaError_t e1 = noalloc_gemm(st, ra, D * pb, rb, E, rb, 1, 0, Bk, (long long)D * pb, 1, EB,
+                                  (long long)D * pb, 1);
+    cudaError_t e2 = noalloc_gemm(st, pa, pb, ra * D, Ak, 1, pa, 1, EB, pb, 1, F, pb, 1);
+    if (e1 != cudaSuccess || e2 != cudaSuccess)
+      return fail(QTT_ECUDA, std::string("qtt_tt_dot_noalloc: launch failed: ") +
+                                 cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
+    std::swap(E, F);
+  }
+  double h[2];
+  if (cudaMemcpyAsync(h, E, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return fail(QTT_ECUDA, "qtt_tt_dot_noalloc: kernel or read-back failed");
+  *re = h[0];
+  *im = h[1];
+  return QTT_OK;
+}

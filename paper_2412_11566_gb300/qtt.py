@@ -86,6 +86,7 @@ _sig("gamma0_apply", _i, [_p, _ip, _d, _d, _i, _p, _d, _i, C.POINTER(_p)])
 _sig("tt_round", _i, [_p, _p, _d, _i])
 _sig("qtt_tt_dot", _i, [_p, _p, _p, _dp, _dp])
 _sig("qtt_op_mean_apply", _i, [_p, _p, _p, _dp])
+_sig("qtt_tt_dot_noalloc", _i, [_p, _p, _p, _dp, _dp])
 _sig("ls_solve_ops", _i, [_p, _p, _p, _p, _p, _dp, _dp, C.POINTER(SolveParams), _dp,
                           C.POINTER(SolveInfo)])
 _sig("ls_solve", _i, [_p, _p, _dp, C.POINTER(SolveParams), _dp, C.POINTER(SolveInfo)])
@@ -352,6 +353,14 @@ def tt_round(ctx: Context, x: TT, eps_tt, rmax):
 def qtt_tt_dot(ctx: Context, a: TT, b: TT) -> complex:
     re, im = C.c_double(), C.c_double()
     ctx.check(lib.qtt_tt_dot(ctx.h, a.h, b.h, C.byref(re), C.byref(im)))
+    return complex(re.value, im.value)
+
+
+def qtt_tt_dot_noalloc(ctx: Context, a: TT, b: TT, stream=None) -> complex:
+    """<a, b> through the entry point that allocates nothing (ranks <= 64)."""
+    re, im = C.c_double(), C.c_double()
+    s = ctx.stream if stream is None else stream
+    ctx.check(lib.qtt_tt_dot_noalloc(a.h, b.h, _p(s.cuda_stream), C.byref(re), C.byref(im)))
     return complex(re.value, im.value)
 
 
