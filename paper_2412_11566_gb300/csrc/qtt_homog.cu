@@ -1054,7 +1054,8 @@ void op_mean(Eng<R>& e, const qtt_op* A, const qtt_tt* x, std::vector<double>& o
 // lambda = sigma^2 decide the rank by the tail rule, core j = V[:, :k]^H and
 // the carry is M V[:, :k]. T is consumed (overwritten).
 std::vector<Cx<double>*> tt_svd_device(Eng<double>& e, Cx<double>* T, const std::vector<int>& dims,
-                                       double eps, int rmax, std::vector<int>& ranks) {
+                                       double eps, int rmax, std::vector<int>& ranks,
+                                       bool consume_T = false) {
   const int L = (int)dims.size();
   std::vector<Cx<double>*> cores(L, nullptr);
   ranks.assign(L + 1, 1);
@@ -1112,7 +1113,7 @@ std::vector<Cx<double>*> tt_svd_device(Eng<double>& e, Cx<double>* T, const std:
       e.ln->arena->release(sg);
       cores[j] = core;
       ranks[j] = kk;
-      if (own_M) e.release(M);
+      if (own_M || consume_T) e.release(M);  // T itself once consumed, if allowed
       M = Mn;
       own_M = true;
       continue;
@@ -1197,7 +1198,7 @@ std::vector<Cx<double>*> tt_svd_device(Eng<double>& e, Cx<double>* T, const std:
     }
     e.ln->arena->release(didx);
     e.release(MV);
-    if (own_M) e.release(M);
+    if (own_M || consume_T) e.release(M);  // T itself once consumed, if allowed
     M = Mn;
     own_M = true;
   }
@@ -1205,6 +1206,7 @@ std::vector<Cx<double>*> tt_svd_device(Eng<double>& e, Cx<double>* T, const std:
     Cx<double>* c0 = e.alloc((long long)dims[0] * ranks[1]);
     QCHECK(cudaMemcpyAsync(c0, M, 16 * (size_t)dims[0] * ranks[1], cudaMemcpyDeviceToDevice,
                            e.st()));
+    if (consume_T) e.release(M);
     M = c0;
   }
   cores[0] = M;
@@ -1313,8 +1315,7 @@ qtt_op* build_sfft(qtt_ctx* c, int n, int adjoint, double eps) {
   sfft_tensor_kernel<<<grid1d(N * N), 256, 0, e.st()>>>((double*)T, n);
   e.post("sfft_tensor_kernel", __LINE__);
   std::vector<int> dims(n, 4), ranks;
-  std::vector<Cx<double>*> ax = tt_svd_device(e, T, dims, eps, 1 << 30, ranks);
-  e.release(T);
+  std::vector<Cx<double>*> ax = tt_svd_device(e, T, dims, eps, 1 << 30, ranks, true);
   // assemble: Voigt identity core, then the axis MPO three times
   const int L = 3 * n + 1;
   std::vector<Cx<double>*> cores(L);
@@ -1363,7 +1364,7 @@ qtt_op* raised_from_field(qtt_ctx* c, Cx<double>* F, int n, const int bcast[3], 
   for (int a = 0; a < 3; ++a) bits += bcast[a] ? 0 : n;
   std::vector<int> dims(1 + bits, 2), ranks;
   dims[0] = 36;
-  std::vector<Cx<double>*> tc = tt_svd_device(e, F, dims, eps, rmax, ranks);
+  std::vector<Cx<double>*> tc = tt_svd_device(e, F, dims, eps, rmax, ranks, true);
   const int L = 3 * n + 1;
   std::vector<Cx<double>*> cores(L);
   std::vector<int> R(L + 1, 1), dout(L, 2), din(L, 2), diag(L, 1);
@@ -1408,8 +1409,7 @@ qtt_op* build_gamma(qtt_ctx* c, int n, double lam0, double mu0, int scheme, doub
   gamma_field_kernel<<<grid1d(N3), 256, 0, e.st()>>>(F, n, lam0, mu0);
   e.post("gamma_field_kernel", __LINE__);
   const int bc[3] = {0, 0, 0};
-  qtt_op* o = raised_from_field(c, F, n, bc, eps, rmax);
-  e.release(F);
+  qtt_op* o = raised_from_field(c, F, n, bc, eps, rmax);  // consumes F
   o->n = n;
   o->has_c0 = 1;
   o->lame0[0] = lam0;
@@ -1661,8 +1661,7 @@ int qtt_tt_from_dense(qtt_ctx_t ctx, int L, const int* dims, const double* dense
   Cx<double>* T = e.alloc(tot);
   QCHECK(cudaMemcpyAsync(T, dense, (size_t)tot * 16, cudaMemcpyHostToDevice, ctx->stream));
   std::vector<int> dv(dims, dims + L), ranks;
-  std::vector<Cx<double>*> cores = tt_svd_device(e, T, dv, eps, rmax, ranks);
-  e.release(T);
+  std::vector<Cx<double>*> cores = tt_svd_device(e, T, dv, eps, rmax, ranks, true);
   qtt_tt* t = new_tt(ctx, &ctx->arena, L, dims);
   for (int k = 0; k <= L; ++k) t->ranks[k] = ranks[k];
   if (ctx->prec == QTT_FP64) {
@@ -1851,8 +1850,7 @@ int qtt_from_phase_field(qtt_ctx_t ctx, const uint8_t* phase, const int shape[3]
   QCHECK(cudaStreamSynchronize(ctx->stream));
   ctx->arena.release(dph);
   ctx->arena.release(ddc);
-  qtt_op* o = raised_from_field(ctx, F, n, bc, eps_tt, rmax);
-  e.release(F);
+  qtt_op* o = raised_from_field(ctx, F, n, bc, eps_tt, rmax);  // consumes F
   o->n = n;
   o->has_c0 = 1;
   o->lame0[0] = lam0;
