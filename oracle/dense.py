@@ -13,9 +13,13 @@ Conventions (readings of the paper, each stated once here):
     operator as the SFFT scheme's exp(+2 pi i k x / N) transform with the
     paper's representatives {-N/2+1, ..., N/2} (App. A) and the conjugated
     momentum-space operator (Sec. 4.3).
-  * Nyquist symmetrisation (App. A) is read literally: Gamma is real and even in
-    q, so the averaging leaves it unchanged. Iterates are therefore complex;
-    C_eff takes the real part and the imaginary part is reported.
+  * Nyquist symmetrisation (App. A): the step's stated purpose is the symmetry
+    Gamma(q)* = Gamma(-q) that keeps the strain real. For an even N the
+    partner of a Nyquist mode is its alias -q mod N, i.e. q with its Nyquist
+    components negated, so at those modes Gamma is replaced by the average of
+    Gamma(xi) and Gamma(xi with its Nyquist components negated). This makes
+    the discrete operator real-preserving and self-adjoint (iterates stay
+    real; C_eff is the energy form).
   * Stop test (Alg. 1): ||eps_{m+1} - eps_m||_F / ||E field||_F < tol, with the
     unweighted Euclidean norm over voxels and Voigt components.
 """
@@ -90,6 +94,16 @@ def green_voigt_direct(xi: np.ndarray, lam0: float, mu0: float) -> np.ndarray:
     return out
 
 
+def green_voigt_symmetrised(xi: np.ndarray, lam0: float, mu0: float, N: int) -> np.ndarray:
+    """Gamma_V with the Nyquist symmetrisation of App. A for an even grid of N
+    points per axis: at modes with a component |xi_a| = N/2 the value is the
+    average of Gamma_V(xi) and Gamma_V at xi with those components negated (its
+    aliased partner -xi mod N, Gamma being even); elsewhere Gamma_V(xi)."""
+    xi = np.asarray(xi, dtype=np.float64)
+    flip = np.where(np.abs(xi) == N / 2, -xi, xi)
+    return 0.5 * (green_voigt_direct(xi, lam0, mu0) + green_voigt_direct(flip, lam0, mu0))
+
+
 def frequencies(N: int) -> np.ndarray:
     """Integer frequencies xi of numpy's FFT bins (Nyquist at -N/2); q = 2 pi xi / N."""
     return np.fft.fftfreq(N, d=1.0 / N)
@@ -114,7 +128,7 @@ def _apply_green(tau_hat, lam0, mu0):
     x2, x3 = np.meshgrid(f2, f3, indexing="ij")
     for a in range(N1):
         xi = np.stack([np.full_like(x2, f1[a]), x2, x3], axis=-1)
-        G = green_voigt_direct(xi, lam0, mu0)               # (N2, N3, 6, 6)
+        G = green_voigt_symmetrised(xi, lam0, mu0, N1)      # (N2, N3, 6, 6), cubic grid
         out[:, a] = np.einsum("yzIJ,Jyz->Iyz", G, tau_hat[:, a])
     return out
 
@@ -169,3 +183,40 @@ def ceff(phase, E, nu, tol=1e-6, max_iter=5000, lame0=None, loads=range(6)):
         imag = max(imag, float(np.abs(r["sigma_bar"].imag).max()))
         iters.append(r["iters"])
     return C, imag, iters
+
+
+def stiffness_voigt_derivative(E: float, nu: float, wrt: str) -> np.ndarray:
+    """d C_V / d E or d C_V / d nu of an isotropic phase (chain rule through
+    lam(E, nu), mu(E, nu))."""
+    d = 1.0 - 2.0 * nu
+    if wrt == "E":
+        dlam = nu / ((1.0 + nu) * d)
+        dmu = 1.0 / (2.0 * (1.0 + nu))
+    elif wrt == "nu":
+        dlam = E * (1.0 + 2.0 * nu * nu) / ((1.0 + nu) ** 2 * d ** 2)
+        dmu = -E / (2.0 * (1.0 + nu) ** 2)
+    else:
+        raise ValueError(wrt)
+    return stiffness_voigt(dlam, dmu)
+
+
+def ceff_gradient_energy(phase, E, nu, eps_fields, params):
+    """dC_eff / dp from converged strain fields (one per unit load, Sec. 2):
+    at the fixed point of the LS equation the strains minimise the energy over
+    E + compatible fields, so  dC_eff[l][k]/dp = < eps_l^T (dC/dp) eps_k >  with
+    dC/dp non-zero only in the phase p refers to. params: list of
+    (phase index, 'E' or 'nu'). eps_fields: dict k -> (6, N1, N2, N3).
+    Returns {param: 6x6 array}."""
+    out = {}
+    loads = sorted(eps_fields)
+    for (p, wrt) in params:
+        D = stiffness_voigt_derivative(E[p], nu[p], wrt)
+        mask = (np.asarray(phase) == p)
+        G = np.zeros((6, 6))
+        for k in loads:
+            De = np.zeros_like(eps_fields[k])
+            De[:, mask] = D @ eps_fields[k][:, mask]
+            for l in loads:
+                G[l, k] = np.mean(np.sum(eps_fields[l] * De, axis=0)).real
+        out[(p, wrt)] = G
+    return out

@@ -383,14 +383,16 @@ def axis_frequencies_bitrev(n: int) -> np.ndarray:
 
 def gamma_field_sfft(n: int, lam0: float, mu0: float) -> np.ndarray:
     """Dense Voigt Green field in the SFFT momentum convention (Sec. 4.3):
-    G[I, J, k'1, k'2, k'3] = conj(Gamma_V[I, J](xi(rev k'1), xi(rev k'2), xi(rev k'3)))."""
+    G[I, J, k'1, k'2, k'3] = conj(Gamma_V[I, J](xi(rev k'1), xi(rev k'2), xi(rev k'3))),
+    Nyquist-symmetrised as in App. A (see oracle.dense)."""
     f = axis_frequencies_bitrev(n)
     N = 1 << n
     out = np.empty((6, 6, N, N, N))
     X2, X3 = np.meshgrid(f, f, indexing="ij")
     for a in range(N):
         xi = np.stack([np.full_like(X2, f[a]), X2, X3], axis=-1)
-        out[:, :, a] = np.moveaxis(dense.green_voigt_direct(xi, lam0, mu0), (-2, -1), (0, 1))
+        out[:, :, a] = np.moveaxis(dense.green_voigt_symmetrised(xi, lam0, mu0, N), (-2, -1),
+                                   (0, 1))
     return out   # real: conj is the identity for the Direct scheme
 
 
@@ -481,3 +483,25 @@ def ls_solve(dC, G, S, Sh, E_voigt, n: int, tol: float, eps: float, rmax: int,
     if lame0 is not None:
         sig = sig + dense.stiffness_voigt(*lame0) @ np.asarray(E_voigt, dtype=np.float64)
     return dict(eps=x, sigma_bar=sig, iters=it, history=hist, max_rank=maxr, cap_hit=cap)
+
+
+def phase_matrices_qtt(phase: np.ndarray, n: int, mats, eps: float, rmax: int = 1 << 30):
+    """Raised TTO of the Voigt-matrix field sum_p mats[p] [phase == p]."""
+    N = 1 << n
+    ph = np.broadcast_to(phase, (N, N, N))
+    F = np.zeros((6, 6, N, N, N))
+    for p, M in enumerate(mats):
+        F += np.asarray(M)[:, :, None, None, None] * (ph == p)[None, None]
+    return controlled_field_to_tto(F, n, eps, rmax)
+
+
+def tto_sandwich_bilinear_mean(op, y, x):
+    """mean over the grid of sum_{I,J} y_I(x) A[I, J](x) x_J(x) (bilinear, no
+    conjugation), by a transfer sweep over the cores with the binary cores
+    averaged by (1/2, 1/2)."""
+    W0, X0, Y0 = op[0], x[0], y[0]
+    # V[s, a, t] = sum_{I, J} Y0[0, I, s] W0[0, I, J, a] X0[0, J, t]
+    V = np.einsum("Is,IJa,Jt->sat", Y0[0], W0[0], X0[0])
+    for W, X, Y in zip(op[1:], x[1:], y[1:]):
+        V = 0.5 * np.einsum("sat,sib,aijc,tjd->bcd", V, Y, W, X)
+    return complex(V[0, 0, 0])

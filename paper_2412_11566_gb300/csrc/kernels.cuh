@@ -734,42 +734,56 @@ __device__ __forceinline__ int bitrev(int k, int n) { return (int)(__brev((unsig
 // xi_a = xi(rev k_a), xi(k) = k for k <= N/2 else k - N, and
 // Gamma_ijkl = (d_ik n_j n_l + d_il n_j n_k + d_jk n_i n_l + d_jl n_i n_k) / (4 mu0)
 //              - (lam0 + mu0) / (mu0 (lam0 + 2 mu0)) n_i n_j n_k n_l,
-// Gamma_V[I, J] = w_I w_J Gamma_{i_I j_I k_J l_J}, Gamma(0) = 0. Real-valued, so
-// the conjugation of the convention is the identity.
+// Gamma_V[I, J] = w_I w_J Gamma_{i_I j_I k_J l_J}, Gamma(0) = 0; at modes with
+// a Nyquist component (|xi_a| = N/2) the value is averaged with the one at xi
+// with those components negated (Nyquist symmetrisation, the aliased partner
+// -xi mod N). Real-valued, so the conjugation of the convention is the identity.
+__device__ void gamma_voigt_at(const double xi[3], double lam0, double mu0, double* g36) {
+  const double beta0 = (lam0 + mu0) / (mu0 * (lam0 + 2.0 * mu0));
+  const double r2 = xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2];
+  double nn[3] = {0, 0, 0};
+  if (r2 > 0) {
+    const double r = sqrt(r2);
+    for (int a = 0; a < 3; ++a) nn[a] = xi[a] / r;
+  }
+  for (int I = 0; I < 6; ++I) {
+    int i, j;
+    voigt_ij(I, i, j);
+    for (int J = 0; J < 6; ++J) {
+      int k, l;
+      voigt_ij(J, k, l);
+      double g = 0;
+      if (r2 > 0) {
+        const double t1 = (i == k) * nn[j] * nn[l] + (i == l) * nn[j] * nn[k] +
+                          (j == k) * nn[i] * nn[l] + (j == l) * nn[i] * nn[k];
+        g = t1 / (4.0 * mu0) - beta0 * nn[i] * nn[j] * nn[k] * nn[l];
+      }
+      g36[I * 6 + J] = (I < 3 ? 1.0 : 2.0) * (J < 3 ? 1.0 : 2.0) * g;
+    }
+  }
+}
+
 __global__ void gamma_field_kernel(Cx<double>* out, int n, double lam0, double mu0) {
   const long long N = 1ll << n, N3 = N * N * N;
-  const double beta0 = (lam0 + mu0) / (mu0 * (lam0 + 2.0 * mu0));
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N3;
        e += (long long)gridDim.x * blockDim.x) {
-    const int k1 = (int)(e / (N * N)), k2 = (int)((e / N) % N), k3 = (int)(e % N);
-    double xi[3];
-    const int ks[3] = {k1, k2, k3};
+    const int ks[3] = {(int)(e / (N * N)), (int)((e / N) % N), (int)(e % N)};
+    double xi[3], xf[3];
+    bool nyq = false;
     for (int a = 0; a < 3; ++a) {
       const int k = n > 0 ? bitrev(ks[a], n) : 0;
       xi[a] = (k <= N / 2) ? (double)k : (double)(k - N);
+      const bool isn = (2 * (long long)fabs(xi[a]) == N);
+      nyq |= isn;
+      xf[a] = isn ? -xi[a] : xi[a];
     }
-    const double r2 = xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2];
-    double nn[3] = {0, 0, 0};
-    if (r2 > 0) {
-      const double r = sqrt(r2);
-      for (int a = 0; a < 3; ++a) nn[a] = xi[a] / r;
+    double g[36], gf[36];
+    gamma_voigt_at(xi, lam0, mu0, g);
+    if (nyq) {
+      gamma_voigt_at(xf, lam0, mu0, gf);
+      for (int P = 0; P < 36; ++P) g[P] = 0.5 * (g[P] + gf[P]);
     }
-    for (int I = 0; I < 6; ++I) {
-      int i, j;
-      voigt_ij(I, i, j);
-      for (int J = 0; J < 6; ++J) {
-        int k, l;
-        voigt_ij(J, k, l);
-        double g = 0;
-        if (r2 > 0) {
-          const double t1 = (i == k) * nn[j] * nn[l] + (i == l) * nn[j] * nn[k] +
-                            (j == k) * nn[i] * nn[l] + (j == l) * nn[i] * nn[k];
-          g = t1 / (4.0 * mu0) - beta0 * nn[i] * nn[j] * nn[k] * nn[l];
-        }
-        const double w = (I < 3 ? 1.0 : 2.0) * (J < 3 ? 1.0 : 2.0);
-        out[((long long)(I * 6 + J)) * N3 + e] = mk<double>(w * g, 0.0);
-      }
-    }
+    for (int P = 0; P < 36; ++P) out[(long long)P * N3 + e] = mk<double>(g[P], 0.0);
   }
 }
 

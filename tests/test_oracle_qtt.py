@@ -127,7 +127,7 @@ def test_momentum_convention_matches_dense_pipeline(n):
     tau = rng.standard_normal((6, N, N, N)) + 1j * rng.standard_normal((6, N, N, N))
     f = dense.frequencies(N)
     XI = np.stack(np.meshgrid(f, f, f, indexing="ij"), -1)
-    d = np.fft.ifftn(np.einsum("abcIJ,Jabc->Iabc", dense.green_voigt_direct(XI, lam0, mu0),
+    d = np.fft.ifftn(np.einsum("abcIJ,Jabc->Iabc", dense.green_voigt_symmetrised(XI, lam0, mu0, N),
                                np.fft.fftn(tau, axes=(1, 2, 3))), axes=(1, 2, 3))
     S = oq.tto_full(oq.sfft_operator(n))
     Sh = oq.tto_full(oq.sfft_operator(n, adjoint=True))
