@@ -135,6 +135,13 @@ int qtt_from_phase_field(qtt_ctx_t ctx, const uint8_t* phase, const int shape[3]
                          int nphase, const double* E, const double* nu,
                          const double* lame0, double eps_tt, int rmax, qtt_op_t* dC);
 
+/* Raised TTO of the Voigt-matrix field sum_p mats[p] [phase == p]: the same
+ * construction as qtt_from_phase_field with arbitrary per-phase 6x6 matrices
+ * (mats: nphase row-major 6x6 blocks), e.g. dC/dp for a material parameter. */
+int qtt_from_phase_matrices(qtt_ctx_t ctx, const uint8_t* phase, const int shape[3], int n,
+                            int nphase, const double* mats, double eps_tt, int rmax,
+                            qtt_op_t* out);
+
 /* The SFFT (Sec. 4.1-4.2): S = P_rev F+ per axis, F+[k, x] =
  * N^-1/2 exp(+2 pi i k x / N), P_rev reversing the n output bits, as a TTO
  * with an identity Voigt core; adjoint = 1 gives S^H = S^-1. Built on the
@@ -190,6 +197,11 @@ int qtt_tt_dot(qtt_ctx_t ctx, qtt_tt_t a, qtt_tt_t b, double* re, double* im);
 #define QTT_NOALLOC_MAX_RANK 64
 #define QTT_NOALLOC_MAX_DIM 6
 int qtt_tt_dot_noalloc(qtt_tt_t a, qtt_tt_t b, void* cuda_stream, double* re, double* im);
+/* Bilinear grid mean of y^T A x = mean_x sum_{I,J} y_I(x) A[I,J](x) x_J(x)
+ * (no conjugation), by an FP64 transfer sweep; A's first core full, binary
+ * cores raised. */
+int qtt_op_sandwich_mean(qtt_ctx_t ctx, qtt_op_t op, qtt_tt_t y, qtt_tt_t x, double* re,
+                         double* im);
 /* Grid mean of A x without forming A x; writes 2 * d_out[0] doubles
  * (interleaved complex, one per component of the first core). */
 int qtt_op_mean_apply(qtt_ctx_t ctx, qtt_op_t op, qtt_tt_t x, double* out);
@@ -197,7 +209,12 @@ int qtt_op_mean_apply(qtt_ctx_t ctx, qtt_op_t op, qtt_tt_t x, double* out);
 /* ---------------------------------------------------------------- solver */
 
 typedef struct {
-  double tol;      /* stop when ||eps_{m+1} - eps_m||_F / ||E||_F < tol */
+  double tol;      /* stop when ||eps_{m+1} - eps_m||_F / ||E||_F < tol; the
+                      residual comes from FP64 inner products and is never
+                      reported below their cancellation floor
+                      sqrt(64 eps (||eps_{m+1}||^2 + ||eps_m||^2)) / ||E||_F
+                      (about 2e-7 relative to ||eps||), so a smaller tol runs
+                      to max_iter */
   int max_iter;    /* iteration cap (QTT_WNOCONV when reached) */
   double eps_tt;   /* rounding accuracy of every step */
   int rmax;        /* rank cap of every rounding */
@@ -236,6 +253,19 @@ int ls_solve_ceff(qtt_ctx_t ctx, qtt_op_t dC, const qtt_solve_params* p, const i
  * precision; default tol_scale 1); max_sweeps_fp32 caps the sweeps in FP32
  * mode (default 40; FP64 mode uses 60). */
 int qtt_ctx_set_jacobi(qtt_ctx_t ctx, double tol_scale, int max_sweeps_fp32);
+/* C_eff and its derivatives with respect to phase parameters (E or nu of a
+ * phase). The Direct-scheme LS operator (with the Nyquist symmetrisation of
+ * App. A) is self-adjoint, so the adjoint solution of load l equals its
+ * forward strain and dC_eff[l][k]/dp = mean(eps_l^T (dC/dp) eps_k): the six
+ * forward solves are kept and contracted with the raised TTO of dC/dp
+ * (qtt_from_phase_matrices of the derivative of the phase stiffness). phase,
+ * shape, nphase, E, nu: the inputs dC was built from. param_phase[q],
+ * param_kind[q] (0 = E, 1 = nu) for q < nparams. Ceff as in ls_solve_ceff;
+ * dCeff: nparams blocks of 36 doubles, same column-major layout; info: 6. */
+int ls_solve_ceff_grad(qtt_ctx_t ctx, qtt_op_t dC, const uint8_t* phase, const int shape[3],
+                       int nphase, const double* E, const double* nu, int nparams,
+                       const int* param_phase, const int* param_kind, const qtt_solve_params* p,
+                       double* Ceff, double* dCeff, qtt_solve_info* info);
 /* Number of load cases ls_solve_ceff solves concurrently (1..6, default 1). */
 int qtt_ctx_set_concurrency(qtt_ctx_t ctx, int concurrent_loads);
 

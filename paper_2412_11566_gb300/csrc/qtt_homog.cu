@@ -1046,6 +1046,79 @@ void op_mean(Eng<R>& e, const qtt_op* A, const qtt_tt* x, std::vector<double>& o
   out = h;
 }
 
+// Bilinear grid mean of y^T A x (no conjugation) by an FP64 transfer sweep:
+// first core full (1, Do, Di, a1), binary cores raised.
+template <typename R>
+void op_sandwich(Eng<R>& e, const qtt_op* A, const qtt_tt* y, const qtt_tt* x, double* out2) {
+  Eng<double> d(e.c, e.ln);
+  const int L = x->L;
+  QREQ(A->L == L && y->L == L, "sandwich: core counts differ");
+  QREQ(!A->diag[0], "sandwich: first operator core must be full");
+  for (int k = 1; k < L; ++k) QREQ(A->diag[k], "sandwich: binary operator cores must be raised");
+  for (int k = 0; k < L; ++k)
+    QREQ(x->dims[k] == A->din[k] && y->dims[k] == A->dout[k], "sandwich: dims differ");
+  auto to64 = [&](const void* p, long long cnt) -> Cx<double>* {
+    Cx<double>* t = d.alloc(cnt);
+    if (sizeof(R) == 8) {
+      QCHECK(cudaMemcpyAsync(t, p, cnt * 16, cudaMemcpyDeviceToDevice, e.st()));
+    } else {
+      convert_kernel<R, double><<<grid1d(cnt), 256, 0, e.st()>>>((const Cx<R>*)p, t, cnt);
+      e.post("convert_kernel", __LINE__);
+    }
+    return t;
+  };
+  const int Do = A->dout[0], Di = A->din[0], A1 = A->ranks[1], T1 = x->ranks[1], S1 = y->ranks[1];
+  Cx<double>* W0 = to64(A->core[0], A->count(0));
+  Cx<double>* X0 = to64(x->core[0], x->count(0));
+  Cx<double>* Y0 = to64(y->core[0], y->count(0));
+  // XW[I][a][t] = sum_J W0[I, J, a] X0[J, t]
+  Cx<double>* XW = d.alloc((long long)Do * A1 * T1);
+  d.gemm(A1, T1, Di, mref(W0, 1, A1, (long long)Di * A1), mref(X0, T1, 1), XW, T1, 1,
+         (long long)A1 * T1, 0, 0, Do, 1, 1);
+  // V[s][(a t)] = sum_I Y0[I, s] XW[I][(a t)]
+  Cx<double>* V = d.alloc((long long)S1 * A1 * T1);
+  d.gemm(S1, A1 * T1, Do, mref(Y0, 1, S1), mref(XW, (long long)A1 * T1, 1), V,
+         (long long)A1 * T1, 1, 0, 0, 0, 1, 1, 1);
+  d.release(W0);
+  d.release(X0);
+  d.release(Y0);
+  d.release(XW);
+  int S = S1, Ar = A1, T = T1;
+  for (int k = 1; k < L; ++k) {
+    const int D = x->dims[k], Sp = y->ranks[k + 1], B = A->ranks[k + 1], Tp = x->ranks[k + 1];
+    Cx<double>* Wk = to64(A->core[k], A->count(k));
+    Cx<double>* Xk = to64(x->core[k], x->count(k));
+    Cx<double>* Yk = to64(y->core[k], y->count(k));
+    // VX[(s a)][(i t')] = V[(s a)][t] X[t][(i t')]
+    Cx<double>* VX = d.alloc((long long)S * Ar * D * Tp);
+    d.gemm(S * Ar, D * Tp, T, mref(V, T, 1), mref(Xk, (long long)D * Tp, 1), VX, (long long)D * Tp,
+           1, 0, 0, 0, 1, 1, 1);
+    // VXW[s][i][b][t'] = sum_a w[a, i, b] VX[s][a][i][t']   (batch s, i)
+    Cx<double>* VXW = d.alloc((long long)S * D * B * Tp);
+    d.gemm(B, Tp, Ar, mref(Wk, 1, (long long)D * B, 0, B),
+           mref(VX, (long long)D * Tp, 1, (long long)Ar * D * Tp, Tp), VXW, Tp, 1,
+           (long long)D * B * Tp, (long long)B * Tp, 0, S, D, 1);
+    // V'[s'][(b t')] = 1/2 sum_{(s i)} Y[(s i), s'] VXW[(s i)][(b t')]
+    Cx<double>* Vn = d.alloc((long long)Sp * B * Tp);
+    d.gemm(Sp, B * Tp, S * D, mref(Yk, 1, Sp), mref(VXW, (long long)B * Tp, 1), Vn,
+           (long long)B * Tp, 1, 0, 0, 0, 1, 1, 1, Cplx{0.5, 0});
+    d.release(VX);
+    d.release(VXW);
+    d.release(V);
+    d.release(Wk);
+    d.release(Xk);
+    d.release(Yk);
+    V = Vn;
+    S = Sp;
+    Ar = B;
+    T = Tp;
+  }
+  QCHECK(cudaMemcpyAsync(e.ln->pinned, V, 16, cudaMemcpyDeviceToHost, e.st()));
+  QCHECK(cudaStreamSynchronize(e.st()));
+  memcpy(out2, e.ln->pinned, 16);
+  d.release(V);
+}
+
 // ------------------------------------------------------------------ TT-SVD (preprocessing, FP64)
 
 // TT-SVD of a dense complex tensor T (dims[0..L-1], row-major) right to left:
@@ -1468,7 +1541,8 @@ int max_rank(const qtt_tt* t) {
 template <typename R>
 int solve_impl(qtt_ctx* c, const qtt_op* dC, const qtt_op* S, const qtt_op* Sh, const qtt_op* G,
                const double* C0, const double* Ev, const qtt_solve_params* p, double* sig,
-               qtt_solve_info* info, int apply_base, Lane* lane = nullptr) {
+               qtt_solve_info* info, int apply_base, Lane* lane = nullptr,
+               qtt_tt** keep = nullptr) {
   Eng<R> e(c, lane);
   const auto t0 = std::chrono::steady_clock::now();
   const int L = dC->L;
@@ -1500,7 +1574,11 @@ int solve_impl(qtt_ctx* c, const qtt_op* dC, const qtt_op* S, const qtt_op* Sh, 
     tt_dot<R>(e, xn, xn, &a2r, &a2i);
     tt_dot<R>(e, x, x, &b2r, &b2i);
     tt_dot<R>(e, xn, x, &abr, &abi);
-    const double d2 = std::max(0.0, a2r + b2r - 2.0 * abr);
+    // ||xn - x||^2 cancels: below ~64 eps (||xn||^2 + ||x||^2) the difference
+    // is rounding noise (it can even come out <= 0), so the residual is never
+    // reported below that floor and the stop test cannot fire on noise.
+    const double floor2 = 64.0 * 2.220446049250313e-16 * (a2r + b2r);
+    const double d2 = std::max(floor2, a2r + b2r - 2.0 * abr);
     rel = std::sqrt(d2) / normE;
     free_tt(tau);
     free_tt(tauh);
@@ -1528,6 +1606,18 @@ int solve_impl(qtt_ctx* c, const qtt_op* dC, const qtt_op* S, const qtt_op* Sh, 
     sig[2 * i] = c0e + m[2 * i];
     sig[2 * i + 1] = m[2 * i + 1];
     leak = std::max(leak, std::fabs(m[2 * i + 1]));
+  }
+  if (keep) {
+    // copy of the final strain in the context's own arena (outlives the lane)
+    qtt_tt* k = new_tt(c, &c->arena, x->L, x->dims);
+    for (int b = 0; b <= x->L; ++b) k->ranks[b] = x->ranks[b];
+    for (int b = 0; b < x->L; ++b) {
+      k->core[b] = c->arena.alloc((size_t)x->count(b) * sizeof(Cx<R>));
+      QCHECK(cudaMemcpyAsync(k->core[b], x->core[b], x->count(b) * sizeof(Cx<R>),
+                             cudaMemcpyDeviceToDevice, e.st()));
+    }
+    QCHECK(cudaStreamSynchronize(e.st()));
+    *keep = k;
   }
   free_tt(x);
   free_tt(Ett);
@@ -1978,9 +2068,12 @@ int ls_solve(qtt_ctx_t ctx, qtt_op_t dC, const double E_voigt[6], const qtt_solv
   API_END
 }
 
-int ls_solve_ceff(qtt_ctx_t ctx, qtt_op_t dC, const qtt_solve_params* p, const int* loads,
-                  int nloads, double* Ceff, qtt_solve_info* info) {
-  API_BEGIN(ctx)
+}  // extern "C"
+
+namespace {
+int solve_loads(qtt_ctx_t ctx, qtt_op_t dC, const qtt_solve_params* p, const int* loads,
+                       int nloads, double* Ceff, qtt_solve_info* info,
+                       std::vector<qtt_tt*>* keep) {
   QREQ(ctx && dC && p && Ceff, "ls_solve_ceff: null argument");
   QREQ(dC->has_c0, "ls_solve_ceff: dC must come from qtt_from_phase_field");
   int all[6] = {0, 1, 2, 3, 4, 5};
@@ -2025,6 +2118,7 @@ int ls_solve_ceff(qtt_ctx_t ctx, qtt_op_t dC, const qtt_solve_params* p, const i
   std::vector<std::string> errs(nloads);
   std::vector<std::vector<double>> sig(nloads, std::vector<double>(12, 0.0));
   std::vector<qtt_solve_info> inf(nloads);
+  if (keep) keep->assign(nloads, nullptr);
   std::atomic<int> next{0};
   auto worker = [&](int lane_id) {
     cudaSetDevice(ctx->device);
@@ -2033,7 +2127,7 @@ int ls_solve_ceff(qtt_ctx_t ctx, qtt_op_t dC, const qtt_solve_params* p, const i
       Ev[loads[l]] = 1.0;
       try {
         status[l] = DISPATCH(ctx, solve_impl, ctx, dC, S, Sh, G, dC->C0, Ev, p, sig[l].data(),
-                             &inf[l], 0, &lanes[lane_id]);
+                             &inf[l], 0, &lanes[lane_id], keep ? &(*keep)[l] : nullptr);
       } catch (const QttError& ex) {
         status[l] = ex.code;
         errs[l] = ex.what();
@@ -2059,14 +2153,138 @@ int ls_solve_ceff(qtt_ctx_t ctx, qtt_op_t dC, const qtt_solve_params* p, const i
   int worst = QTT_OK;
   for (int l = 0; l < nloads; ++l) {
     if (status[l] < 0) {
-      ctx->err = errs[l];
-      return status[l];
+      if (keep)
+        for (auto* t : *keep) free_tt(t);
+      throw QttError(status[l], errs[l]);
     }
     worst = std::max(worst, status[l]);
     for (int i = 0; i < 6; ++i) Ceff[loads[l] * 6 + i] = sig[l][2 * i];
     if (info) info[l] = inf[l];
   }
   return worst;
+}
+
+
+}  // namespace
+
+extern "C" {
+
+int ls_solve_ceff(qtt_ctx_t ctx, qtt_op_t dC, const qtt_solve_params* p, const int* loads,
+                  int nloads, double* Ceff, qtt_solve_info* info) {
+  API_BEGIN(ctx)
+  return solve_loads(ctx, dC, p, loads, nloads, Ceff, info, nullptr);
+  API_END
+}
+
+int qtt_from_phase_matrices(qtt_ctx_t ctx, const uint8_t* phase, const int shape[3], int n,
+                            int nphase, const double* mats, double eps_tt, int rmax,
+                            qtt_op_t* out) {
+  API_BEGIN(ctx)
+  QREQ(ctx && phase && shape && mats && out, "qtt_from_phase_matrices: null argument");
+  QREQ(n >= 1 && 3 * n + 1 <= QTT_MAX_CORES, "qtt_from_phase_matrices: n out of range");
+  QREQ(nphase >= 1 && nphase <= 255, "qtt_from_phase_matrices: nphase out of range");
+  const long long N = 1ll << n;
+  int bc[3];
+  long long cells = 1;
+  for (int a = 0; a < 3; ++a) {
+    QREQ(shape[a] == 1 || shape[a] == N, "qtt_from_phase_matrices: extents must be 1 or 2^n");
+    bc[a] = shape[a] == 1;
+    cells *= shape[a];
+  }
+  Eng<double> e(ctx);
+  uint8_t* dph = (uint8_t*)ctx->arena.alloc(cells);
+  double* dm = (double*)ctx->arena.alloc(sizeof(double) * 36 * nphase);
+  QCHECK(cudaMemcpyAsync(dph, phase, cells, cudaMemcpyHostToDevice, ctx->stream));
+  QCHECK(cudaMemcpyAsync(dm, mats, sizeof(double) * 36 * nphase, cudaMemcpyHostToDevice,
+                         ctx->stream));
+  Cx<double>* F = e.alloc(36 * cells);
+  stiffness_field_kernel<<<grid1d(cells), 256, 0, ctx->stream>>>(dph, cells, dm, nphase, F);
+  e.post("stiffness_field_kernel", __LINE__);
+  QCHECK(cudaStreamSynchronize(ctx->stream));
+  ctx->arena.release(dph);
+  ctx->arena.release(dm);
+  qtt_op* o = raised_from_field(ctx, F, n, bc, eps_tt, rmax);  // consumes F
+  o->n = n;
+  *out = o;
+  return QTT_OK;
+  API_END
+}
+
+int qtt_op_sandwich_mean(qtt_ctx_t ctx, qtt_op_t op, qtt_tt_t y, qtt_tt_t x, double* re,
+                         double* im) {
+  API_BEGIN(ctx)
+  QREQ(ctx && op && y && x && re && im, "qtt_op_sandwich_mean: null argument");
+  double v[2];
+  if (ctx->prec == QTT_FP64) {
+    Eng<double> e(ctx);
+    op_sandwich<double>(e, op, y, x, v);
+  } else {
+    Eng<float> e(ctx);
+    op_sandwich<float>(e, op, y, x, v);
+  }
+  *re = v[0];
+  *im = v[1];
+  return QTT_OK;
+  API_END
+}
+
+int ls_solve_ceff_grad(qtt_ctx_t ctx, qtt_op_t dC, const uint8_t* phase, const int shape[3],
+                       int nphase, const double* E, const double* nu, int nparams,
+                       const int* param_phase, const int* param_kind, const qtt_solve_params* p,
+                       double* Ceff, double* dCeff, qtt_solve_info* info) {
+  API_BEGIN(ctx)
+  QREQ(ctx && dC && phase && shape && E && nu && p && Ceff && (nparams == 0 || dCeff),
+       "ls_solve_ceff_grad: null argument");
+  QREQ(nparams >= 0 && nparams <= 64 && (nparams == 0 || (param_phase && param_kind)),
+       "ls_solve_ceff_grad: bad parameter list");
+  for (int q = 0; q < nparams; ++q)
+    QREQ(param_phase[q] >= 0 && param_phase[q] < nphase &&
+             (param_kind[q] == 0 || param_kind[q] == 1),
+         "ls_solve_ceff_grad: bad parameter");
+  std::vector<qtt_tt*> eps;
+  const int st = solve_loads(ctx, dC, p, nullptr, 6, Ceff, info, &eps);
+  struct Guard {
+    std::vector<qtt_tt*>& v;
+    ~Guard() {
+      for (auto* t : v) free_tt(t);
+    }
+  } guard{eps};
+  for (int q = 0; q < nparams; ++q) {
+    // dC/dp: derivative of the phase's isotropic stiffness through
+    // lambda(E, nu), mu(E, nu); zero in the other phases
+    const double e0 = E[param_phase[q]], n0 = nu[param_phase[q]];
+    double dlam, dmu;
+    if (param_kind[q] == 0) {
+      dlam = n0 / ((1.0 + n0) * (1.0 - 2.0 * n0));
+      dmu = 1.0 / (2.0 * (1.0 + n0));
+    } else {
+      const double dd = 1.0 - 2.0 * n0;
+      dlam = e0 * (1.0 + 2.0 * n0 * n0) / ((1.0 + n0) * (1.0 + n0) * dd * dd);
+      dmu = -e0 / (2.0 * (1.0 + n0) * (1.0 + n0));
+    }
+    std::vector<double> mats(36 * nphase, 0.0);
+    voigt_stiffness(dlam, dmu, &mats[36 * param_phase[q]]);
+    qtt_op_t D = nullptr;
+    const int rc = qtt_from_phase_matrices(ctx, phase, shape, dC->n, nphase, mats.data(), p->eps_tt,
+                                           1 << 30, &D);
+    if (rc < 0) return rc;
+    for (int k = 0; k < 6; ++k)
+      for (int l = k; l < 6; ++l) {
+        double v[2];
+        if (ctx->prec == QTT_FP64) {
+          Eng<double> e(ctx);
+          op_sandwich<double>(e, D, eps[l], eps[k], v);
+        } else {
+          Eng<float> e(ctx);
+          op_sandwich<float>(e, D, eps[l], eps[k], v);
+        }
+        // column-major like Ceff: dCeff[q*36 + k*6 + l] = dC_eff[l][k] / dp
+        dCeff[q * 36 + k * 6 + l] = v[0];
+        dCeff[q * 36 + l * 6 + k] = v[0];
+      }
+    free_op(D);
+  }
+  return st;
   API_END
 }
 

@@ -87,6 +87,11 @@ _sig("tt_round", _i, [_p, _p, _d, _i])
 _sig("qtt_tt_dot", _i, [_p, _p, _p, _dp, _dp])
 _sig("qtt_op_mean_apply", _i, [_p, _p, _p, _dp])
 _sig("qtt_tt_dot_noalloc", _i, [_p, _p, _p, _dp, _dp])
+_sig("qtt_from_phase_matrices", _i, [_p, C.POINTER(C.c_uint8), _ip, _i, _i, _dp, _d, _i,
+                                      C.POINTER(_p)])
+_sig("qtt_op_sandwich_mean", _i, [_p, _p, _p, _p, _dp, _dp])
+_sig("ls_solve_ceff_grad", _i, [_p, _p, C.POINTER(C.c_uint8), _ip, _i, _dp, _dp, _i, _ip, _ip,
+                                 C.POINTER(SolveParams), _dp, _dp, C.POINTER(SolveInfo)])
 _sig("ls_solve_ops", _i, [_p, _p, _p, _p, _p, _dp, _dp, C.POINTER(SolveParams), _dp,
                           C.POINTER(SolveInfo)])
 _sig("ls_solve", _i, [_p, _p, _dp, C.POINTER(SolveParams), _dp, C.POINTER(SolveInfo)])
@@ -296,9 +301,10 @@ class Op:
 def qtt_from_phase_field(ctx: Context, phase, n, E, nu, lame0=None, eps_tt=1e-6, rmax=1 << 30):
     ph = np.ascontiguousarray(phase, dtype=np.uint8)
     shape = list(ph.shape)
-    Ea = np.asarray(E, dtype=np.float64)
-    nua = np.asarray(nu, dtype=np.float64)
-    l0 = None if lame0 is None else np.asarray(lame0, dtype=np.float64)
+    # contiguous copies: a strided view's .ctypes pointer would skip entries
+    Ea = np.ascontiguousarray(E, dtype=np.float64)
+    nua = np.ascontiguousarray(nu, dtype=np.float64)
+    l0 = None if lame0 is None else np.ascontiguousarray(lame0, dtype=np.float64)
     h = _p()
     ctx.check(lib.qtt_from_phase_field(ctx.h, ph.ctypes.data_as(C.POINTER(C.c_uint8)),
                                        _ints(shape), n, len(Ea), Ea.ctypes.data_as(_dp),
@@ -402,3 +408,68 @@ def ls_solve_ceff(ctx: Context, dC: Op, params: SolveParams, loads=None):
     rc = ctx.check(lib.ls_solve_ceff(ctx.h, dC.h, C.byref(params), _ints(loads), len(loads),
                                      Ceff.ctypes.data_as(_dp), infos))
     return Ceff.reshape(6, 6).T.copy(), [i.as_dict() for i in infos], rc
+
+
+def qtt_from_phase_matrices(ctx: Context, phase, n, mats, eps_tt=1e-6, rmax=1 << 30):
+    ph = np.ascontiguousarray(phase, dtype=np.uint8)
+    M = np.ascontiguousarray(np.asarray(mats, dtype=np.float64).reshape(-1, 36))
+    h = _p()
+    ctx.check(lib.qtt_from_phase_matrices(ctx.h, ph.ctypes.data_as(C.POINTER(C.c_uint8)),
+                                          _ints(list(ph.shape)), n, M.shape[0],
+                                          M.ctypes.data_as(_dp), eps_tt, rmax, C.byref(h)))
+    return Op(ctx, h)
+
+
+def qtt_op_sandwich_mean(ctx: Context, op: Op, y: TT, x: TT) -> complex:
+    re, im = C.c_double(), C.c_double()
+    ctx.check(lib.qtt_op_sandwich_mean(ctx.h, op.h, y.h, x.h, C.byref(re), C.byref(im)))
+    return complex(re.value, im.value)
+
+
+PARAM_E, PARAM_NU = 0, 1
+
+
+def ls_solve_ceff_grad(ctx: Context, dC: Op, phase, E, nu, params: SolveParams, wrt):
+    """C_eff (6x6) and dC_eff/dp for p in wrt = [(phase index, 'E' | 'nu'), ...]."""
+    ph = np.ascontiguousarray(phase, dtype=np.uint8)
+    Ea = np.ascontiguousarray(E, dtype=np.float64)
+    nua = np.ascontiguousarray(nu, dtype=np.float64)
+    pp = [int(p) for p, _ in wrt]
+    pk = [PARAM_E if k == "E" else PARAM_NU for _, k in wrt]
+    Ceff = np.zeros(36)
+    dC_ = np.zeros(36 * max(1, len(wrt)))
+    infos = (SolveInfo * 6)()
+    rc = ctx.check(lib.ls_solve_ceff_grad(ctx.h, dC.h, ph.ctypes.data_as(C.POINTER(C.c_uint8)),
+                                          _ints(list(ph.shape)), len(Ea), Ea.ctypes.data_as(_dp),
+                                          nua.ctypes.data_as(_dp), len(wrt), _ints(pp), _ints(pk),
+                                          C.byref(params), Ceff.ctypes.data_as(_dp),
+                                          dC_.ctypes.data_as(_dp), infos))
+    grads = [dC_[36 * q:36 * (q + 1)].reshape(6, 6).T.copy() for q in range(len(wrt))]
+    return Ceff.reshape(6, 6).T.copy(), grads, [i.as_dict() for i in infos], rc
+
+
+def make_ceff_function(ctx: Context, phase, n, params: SolveParams, eps_op=1e-6, rmax_op=1 << 30):
+    """torch.autograd.Function computing C_eff (6x6 float64 tensor) from the
+    phase parameters (E_0, nu_0, E_1, nu_1, ...) of a fixed microstructure;
+    backward contracts the kept forward strains with dC/dp on the device."""
+    import torch
+
+    class CeffFunction(torch.autograd.Function):
+        @staticmethod
+        def forward(fctx, theta):
+            th = theta.detach().cpu().double().numpy()
+            E, nu = th[0::2].tolist(), th[1::2].tolist()
+            dC = qtt_from_phase_field(ctx, phase, n, E, nu, None, eps_op, rmax_op)
+            wrt = [(p, k) for p in range(len(E)) for k in ("E", "nu")]
+            C, grads, _, _ = ls_solve_ceff_grad(ctx, dC, phase, E, nu, params, wrt)
+            dC.free()
+            fctx.save_for_backward(torch.from_numpy(np.stack(grads)))
+            return torch.from_numpy(C).to(theta.device)
+
+        @staticmethod
+        def backward(fctx, grad_out):
+            (G,) = fctx.saved_tensors
+            g = grad_out.detach().cpu().double()
+            return (G * g.unsqueeze(0)).sum(dim=(1, 2)).to(grad_out.device)
+
+    return CeffFunction

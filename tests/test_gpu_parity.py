@@ -213,3 +213,21 @@ def test_fp32_mode_vs_dense_oracle(Q):
     for k in (0, 3):
         assert np.abs(C[:, k] - Cd[:, k]).max() < 2e-4 * np.abs(Cd).max()
     ctx.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_concurrent_loads_match_sequential(Q, precision):
+    """Six load cases on six streams/lanes give the same C_eff as one after
+    the other (same sketches, same operators)."""
+    prec = Q.QTT_FP64 if precision == "fp64" else Q.QTT_FP32
+    ctx = Q.Context(0, prec, 1 << 31, seed=SEED)
+    n = 3
+    ph = synth.centred_sphere(n, 0.3)
+    dC = Q.qtt_from_phase_field(ctx, ph, n, (1.0, 10.0), (0.3, 0.25), None, 1e-10)
+    p = Q.solve_params(1e-30, 6, 1e-10, 32)
+    C1, i1, _ = Q.ls_solve_ceff(ctx, dC, p)
+    ctx.set_concurrency(6)
+    C6, i6, _ = Q.ls_solve_ceff(ctx, dC, p)
+    tol = 1e-12 if precision == "fp64" else 1e-5
+    assert np.abs(C6 - C1).max() <= tol * np.abs(C1).max()
+    ctx.close()
