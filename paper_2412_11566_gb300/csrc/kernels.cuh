@@ -204,7 +204,14 @@ __global__ void qr_kernel(int m, int n, const Cx<R>* __restrict__ A, long long r
   __shared__ Cx<R> s_v0;
   __shared__ R s_h;
   const int tid = threadIdx.x, nt = blockDim.x;
-  const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
+  // lanes per column in the trailing updates: with the matrix in shared
+  // memory, the largest power of two <= 32 that gives every column its own
+  // group (at least 4 lanes); from global memory, whole warps (more loads in
+  // flight per column beat more columns in flight)
+  int G = 32;
+  if (use_smem)
+    while (G > 4 && (nt / G) < n) G >>= 1;
+  const int gid = tid / G, gl = tid % G, ngroups = nt / G;
   for (long long e = tid; e < (long long)m * n; e += nt) {
     const int i = (int)(e % m), j = (int)(e / m);
     Cx<R> v = A[(long long)i * rs + (long long)j * cs];
@@ -242,15 +249,25 @@ __global__ void qr_kernel(int m, int n, const Cx<R>* __restrict__ A, long long r
     const R h = s_h;
     const Cx<R> v0 = s_v0;
     if (h != (R)0) {
-      for (int c = j + 1 + warp; c < n; c += nw) {
-        Cx<R>* a = W + (long long)c * m;
+      // one group of G lanes per trailing column (uniform loop: every lane
+      // takes part in the shuffles)
+      for (int c0 = j + 1; c0 < n; c0 += ngroups) {
+        const int c = c0 + gid;
+        const bool valid = c < n;
+        Cx<R>* a = W + (long long)(valid ? c : j) * m;
         Cx<R> w = mk<R>(0, 0);
-        if (lane == 0) w = cmulc(v0, a[j]);
-        for (int i = j + 1 + lane; i < m; i += 32) w = cadd(w, cmulc(col[i], a[i]));
-        w = warp_sum(w);
+        if (valid) {
+          if (gl == 0) w = cmulc(v0, a[j]);
+          for (int i = j + 1 + gl; i < m; i += G) w = cadd(w, cmulc(col[i], a[i]));
+        }
+        for (int o = G >> 1; o > 0; o >>= 1) {
+          w.x += __shfl_xor_sync(0xffffffffu, w.x, o);
+          w.y += __shfl_xor_sync(0xffffffffu, w.y, o);
+        }
+        if (!valid) continue;
         const Cx<R> hw = cscale(w, h);
-        if (lane == 0) a[j] = csub(a[j], cmul(hw, v0));
-        for (int i = j + 1 + lane; i < m; i += 32) a[i] = csub(a[i], cmul(hw, col[i]));
+        if (gl == 0) a[j] = csub(a[j], cmul(hw, v0));
+        for (int i = j + 1 + gl; i < m; i += G) a[i] = csub(a[i], cmul(hw, col[i]));
       }
     }
     __syncthreads();
@@ -271,15 +288,23 @@ __global__ void qr_kernel(int m, int n, const Cx<R>* __restrict__ A, long long r
     if (h == (R)0) continue;
     const Cx<R> v0 = vhead[j];
     const Cx<R>* col = W + (long long)j * m;
-    for (int c = j + warp; c < k; c += nw) {
-      Cx<R>* q = Q + (long long)c * m;
+    for (int c0 = j; c0 < k; c0 += ngroups) {
+      const int c = c0 + gid;
+      const bool valid = c < k;
+      Cx<R>* q = Q + (long long)(valid ? c : j) * m;
       Cx<R> w = mk<R>(0, 0);
-      if (lane == 0) w = cmulc(v0, q[j]);
-      for (int i = j + 1 + lane; i < m; i += 32) w = cadd(w, cmulc(col[i], q[i]));
-      w = warp_sum(w);
+      if (valid) {
+        if (gl == 0) w = cmulc(v0, q[j]);
+        for (int i = j + 1 + gl; i < m; i += G) w = cadd(w, cmulc(col[i], q[i]));
+      }
+      for (int o = G >> 1; o > 0; o >>= 1) {
+        w.x += __shfl_xor_sync(0xffffffffu, w.x, o);
+        w.y += __shfl_xor_sync(0xffffffffu, w.y, o);
+      }
+      if (!valid) continue;
       const Cx<R> hw = cscale(w, h);
-      if (lane == 0) q[j] = csub(q[j], cmul(hw, v0));
-      for (int i = j + 1 + lane; i < m; i += 32) q[i] = csub(q[i], cmul(hw, col[i]));
+      if (gl == 0) q[j] = csub(q[j], cmul(hw, v0));
+      for (int i = j + 1 + gl; i < m; i += G) q[i] = csub(q[i], cmul(hw, col[i]));
     }
     __syncthreads();
   }
@@ -330,6 +355,11 @@ __global__ void jacobi_svd_kernel(int m, int n, Cx<R>* A, Cx<R>* V, double* sigm
   const R negl = eps_r * eps_r * f2;
   const int np = (n + 1) & ~1;  // players (even)
   const int mp = np - 1;
+  // lanes per pair: the largest power of two <= 32 that still gives every
+  // pair of a round its own group (at least 4 lanes)
+  int G = 32;
+  while (G > 4 && (nt / G) < np / 2) G >>= 1;
+  const int gid = tid / G, gl = tid % G, ngroups = nt / G;
   int sweep = 0;
   if (tid == 0) s_rot = 1;
   __syncthreads();
@@ -340,30 +370,40 @@ __global__ void jacobi_svd_kernel(int m, int n, Cx<R>* A, Cx<R>* V, double* sigm
     if (tid == 0) s_rot = 0;
     __syncthreads();
     for (int r = 0; r < mp; ++r) {
-      for (int pi = warp; pi < np / 2; pi += nw) {
-        int p, q;
-        if (pi == 0) {
-          p = 0;
-          q = (r % mp) + 1;
-        } else {
-          p = ((r + pi) % mp) + 1;
-          q = ((r + mp - pi) % mp) + 1;
+      // G lanes per column pair (aligned sub-warp groups): all pairs of a
+      // round in one wave, short shuffle trees, m/G elements per lane.
+      for (int pi0 = 0; pi0 < np / 2; pi0 += ngroups) {  // uniform across the block
+        const int pi = pi0 + gid;
+        int p = 0, q = 0;
+        bool valid = pi < np / 2;
+        if (valid) {
+          if (pi == 0) {
+            p = 0;
+            q = (r % mp) + 1;
+          } else {
+            p = ((r + pi) % mp) + 1;
+            q = ((r + mp - pi) % mp) + 1;
+          }
+          valid = p < n && q < n;
         }
-        if (p >= n || q >= n) continue;
         Cx<R>* ap = A + (long long)p * m;
         Cx<R>* aq = A + (long long)q * m;
         R app = 0, aqq = 0;
         Cx<R> apq = mk<R>(0, 0);
-        for (int i = lane; i < m; i += 32) {
-          const Cx<R> x = ap[i], y = aq[i];
-          app += cabs2(x);
-          aqq += cabs2(y);
-          apq = cadd(apq, cmulc(x, y));
+        if (valid)
+          for (int i = gl; i < m; i += G) {
+            const Cx<R> x = ap[i], y = aq[i];
+            app += cabs2(x);
+            aqq += cabs2(y);
+            apq = cadd(apq, cmulc(x, y));
+          }
+        for (int o = G >> 1; o > 0; o >>= 1) {  // executed by every lane of the warp
+          app += __shfl_xor_sync(0xffffffffu, app, o);
+          aqq += __shfl_xor_sync(0xffffffffu, aqq, o);
+          apq.x += __shfl_xor_sync(0xffffffffu, apq.x, o);
+          apq.y += __shfl_xor_sync(0xffffffffu, apq.y, o);
         }
-        app = warp_sum(app);
-        aqq = warp_sum(aqq);
-        apq = warp_sum(apq);
-        if (app <= negl || aqq <= negl) continue;
+        if (!valid || app <= negl || aqq <= negl) continue;
         const R g = hypot(apq.x, apq.y);
         if (!(g > tol * sqrt(app) * sqrt(aqq))) continue;
         // reduce to a real symmetric 2x2 problem with phase e^{i phi} = apq/|apq|
@@ -374,7 +414,7 @@ __global__ void jacobi_svd_kernel(int m, int n, Cx<R>* A, Cx<R>* V, double* sigm
         const R s = c * t;
         // a_p' = c a_p - s conj(e) a_q ; a_q' = s a_p + c conj(e) a_q
         const Cx<R> ec = cconj(e);
-        for (int i = lane; i < m; i += 32) {
+        for (int i = gl; i < m; i += G) {
           const Cx<R> x = ap[i], y = cmul(ec, aq[i]);
           ap[i] = mk<R>(c * x.x - s * y.x, c * x.y - s * y.y);
           aq[i] = mk<R>(s * x.x + c * y.x, s * x.y + c * y.y);
@@ -382,13 +422,13 @@ __global__ void jacobi_svd_kernel(int m, int n, Cx<R>* A, Cx<R>* V, double* sigm
         if (want_v) {
           Cx<R>* vp = V + (long long)p * n;
           Cx<R>* vq = V + (long long)q * n;
-          for (int i = lane; i < n; i += 32) {
+          for (int i = gl; i < n; i += G) {
             const Cx<R> x = vp[i], y = cmul(ec, vq[i]);
             vp[i] = mk<R>(c * x.x - s * y.x, c * x.y - s * y.y);
             vq[i] = mk<R>(s * x.x + c * y.x, s * x.y + c * y.y);
           }
         }
-        if (lane == 0) s_rot = 1;
+        if (gl == 0) s_rot = 1;
       }
       __syncthreads();
     }
