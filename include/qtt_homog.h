@@ -253,6 +253,13 @@ int ls_solve_ceff(qtt_ctx_t ctx, qtt_op_t dC, const qtt_solve_params* p, const i
  * precision; default tol_scale 1); max_sweeps_fp32 caps the sweeps in FP32
  * mode (default 40; FP64 mode uses 60). */
 int qtt_ctx_set_jacobi(qtt_ctx_t ctx, double tol_scale, int max_sweeps_fp32);
+/* TT-SVD of a dense field (Alg. 1, used to build the stiffness and Green
+ * operators): a P x c unfolding with 8 P c min(P, c) above gram_threshold
+ * (default 2e9) takes its right factor from the eigenvectors of the Gram
+ * matrix M^H M, with the ranks decided by the column norms of M V; smaller
+ * ones take an SVD of M itself (QR + one-sided Jacobi). 0 sends every
+ * unfolding through the Gram path. Returns QTT_EINVAL for a negative value. */
+int qtt_ctx_set_tt_svd(qtt_ctx_t ctx, double gram_threshold);
 /* C_eff and its derivatives with respect to phase parameters (E or nu of a
  * phase). The Direct-scheme LS operator (with the Nyquist symmetrisation of
  * App. A) is self-adjoint, so the adjoint solution of load l equals its

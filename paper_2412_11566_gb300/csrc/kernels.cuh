@@ -71,6 +71,10 @@ struct GemmArgs {
   int nb1, nb2, nb3, ksplit;
   int conjA, conjB;
   double alpha_re, alpha_im, beta_re, beta_im;
+  // split-K without atomics: with ksplit > 1 and part != nullptr each split
+  // writes alpha * (its partial product) to part[((ks * nbatch + b) * M + m) * N
+  // + n] and splitk_reduce_kernel sums the splits in a fixed order.
+  void* part;
 };
 
 template <typename R, int BM, int BN, int BK, int TM, int TN>
@@ -157,7 +161,11 @@ gemm_kernel(GemmArgs g) {
       if (gn >= g.N) continue;
       Cx<R>* p = C + (long long)gm * g.c_rs + (long long)gn * g.c_cs;
       Cx<R> v = cmul(alpha, acc[i][j]);
-      if (g.ksplit > 1) {
+      if (g.part) {
+        const long long nbat = (long long)g.nb1 * g.nb2 * g.nb3;
+        const long long bidx = ((long long)b1 * g.nb2 + b2) * g.nb3 + b3;
+        ((Cx<R>*)g.part)[(((long long)ks * nbat + bidx) * g.M + gm) * g.N + gn] = v;
+      } else if (g.ksplit > 1) {
         atomicAdd(&p->x, v.x);
         atomicAdd(&p->y, v.y);
       } else {
@@ -165,6 +173,30 @@ gemm_kernel(GemmArgs g) {
         *p = v;
       }
     }
+  }
+}
+
+// C = sum over the ks splits of part (fixed order) + beta C, for the batch
+// and strides of the GEMM that wrote part (layout in GemmArgs::part).
+template <typename R>
+__global__ void splitk_reduce_kernel(const Cx<R>* __restrict__ part, int ks, long long nbat, int M,
+                                     int N, int nb2, int nb3, Cx<R>* C, long long c_rs,
+                                     long long c_cs, long long c_b1, long long c_b2,
+                                     long long c_b3, double beta_re, double beta_im) {
+  const long long per = (long long)M * N, tot = nbat * per;
+  const Cx<R> beta = mk<R>((R)beta_re, (R)beta_im);
+  const bool use_beta = (beta_re != 0.0 || beta_im != 0.0);
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    Cx<R> s = part[e];
+    for (int k = 1; k < ks; ++k) s = cadd(s, part[e + k * tot]);
+    const long long bidx = e / per, r = e - bidx * per;
+    const long long gm = r / N, gn = r - gm * N;
+    const long long b3 = bidx % nb3, t = bidx / nb3;
+    const long long b2 = t % nb2, b1 = t / nb2;
+    Cx<R>* p = C + b1 * c_b1 + b2 * c_b2 + b3 * c_b3 + gm * c_rs + gn * c_cs;
+    if (use_beta) s = cadd(s, cmul(beta, *p));
+    *p = s;
   }
 }
 
@@ -873,6 +905,128 @@ __global__ void gather_cols_kernel(const Cx<R>* __restrict__ src, long long P, i
       continue;
     }
     dst[e] = src[r * c + j];
+  }
+}
+
+// Tall-skinny Gram matrix G += M^H M (G column-major c x c, zeroed by the
+// caller) of a row-major P x c matrix M with c <= kGramMaxCols. A 64 x 64 GEMM
+// tile would do (64/c)^2 times the useful work here, and FP64 is slow enough
+// on this part for that to dominate the TT-SVD of a dense field. Each CTA
+// stages a contiguous slab of rows through shared memory; each thread owns
+// entries (a <= b) of the upper triangle and, when there are fewer than 256 of
+// them, one of S interleaved row slices. Per-CTA partial sums are reduced over
+// the slices in shared memory and added to both triangles of G atomically.
+constexpr int kGramMaxCols = 64;
+constexpr int kGramChunk = 2048;  // complex elements staged per chunk
+
+template <typename R>
+__global__ void __launch_bounds__(256)
+gram_skinny_kernel(const Cx<R>* __restrict__ M, long long P, int c, long long rows_per_cta,
+                   Cx<R>* G) {
+  constexpr int kMaxOwn = (kGramMaxCols * (kGramMaxCols + 1) / 2 + 255) / 256;
+  __shared__ Cx<R> sm[kGramChunk];
+  __shared__ Cx<R> red[256];
+  const int Q = c * (c + 1) / 2;
+  const int S = Q >= 256 ? 1 : 256 / Q;
+  const int t = threadIdx.x;
+  const bool active = S > 1 ? t < S * Q : true;
+  const int s = S > 1 ? t / Q : 0;
+  int pa[kMaxOwn], pb[kMaxOwn];
+  int np = 0;
+  if (active) {
+    const int step = S > 1 ? Q : 256;
+#pragma unroll
+    for (int k = 0; k < kMaxOwn; ++k) {
+      const int q = (S > 1 ? t % Q : t) + k * step;
+      pa[k] = 0;
+      pb[k] = 0;
+      if (q < Q && (S == 1 || k == 0)) {
+        int b = 0;
+        while ((b + 1) * (b + 2) / 2 <= q) ++b;
+        pa[k] = q - b * (b + 1) / 2;
+        pb[k] = b;
+        np = k + 1;
+      }
+    }
+  }
+  Cx<R> acc[kMaxOwn];
+#pragma unroll
+  for (int k = 0; k < kMaxOwn; ++k) acc[k] = mk<R>(0, 0);
+  const long long r0 = (long long)blockIdx.x * rows_per_cta;
+  const long long r1 = r0 + rows_per_cta < P ? r0 + rows_per_cta : P;
+  const int ch = kGramChunk / c;
+  for (long long rb = r0; rb < r1; rb += ch) {
+    const int nr = (int)(r1 - rb < ch ? r1 - rb : ch);
+    const Cx<R>* src = M + rb * c;
+    __syncthreads();
+    for (int i = t; i < nr * c; i += 256) sm[i] = src[i];
+    __syncthreads();
+    for (int r = s; r < nr; r += S) {
+      const Cx<R>* row = sm + r * c;
+#pragma unroll
+      for (int k = 0; k < kMaxOwn; ++k)
+        if (k < np) acc[k] = cadd(acc[k], cmulc(row[pa[k]], row[pb[k]]));
+    }
+  }
+  if (S > 1) {
+    __syncthreads();
+    red[t] = active ? acc[0] : mk<R>(0, 0);
+    __syncthreads();
+    if (t < Q) {
+      Cx<R> v = red[t];
+      for (int j = 1; j < S; ++j) v = cadd(v, red[t + j * Q]);
+      acc[0] = v;
+      np = 1;
+    } else {
+      np = 0;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kMaxOwn; ++k)
+    if (k < np) {
+      const int a = pa[k], b = pb[k];
+      atomicAdd(&G[a + (long long)b * c].x, acc[k].x);
+      atomicAdd(&G[a + (long long)b * c].y, acc[k].y);
+      if (a != b) {
+        atomicAdd(&G[b + (long long)a * c].x, acc[k].x);
+        atomicAdd(&G[b + (long long)a * c].y, -acc[k].y);
+      }
+    }
+}
+
+// out = M V for a row-major P x c matrix M and a column-major c x c matrix V,
+// c <= kSkinnyMaxCols, written row-major P x c; V sits in shared memory and
+// one thread computes one output entry (the threads of a row share its loads).
+constexpr int kSkinnyMaxCols = 32;
+
+template <typename R>
+__global__ void matmul_skinny_kernel(const Cx<R>* __restrict__ M, long long P, int c,
+                                     const Cx<R>* __restrict__ V, Cx<R>* __restrict__ out) {
+  __shared__ Cx<R> vs[kSkinnyMaxCols * kSkinnyMaxCols];
+  for (int i = threadIdx.x; i < c * c; i += blockDim.x) vs[i] = V[i];
+  __syncthreads();
+  const long long tot = P * c;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long p = e / c;
+    const int j = (int)(e - p * c);
+    const Cx<R>* row = M + p * c;
+    Cx<R> acc = mk<R>(0, 0);
+    for (int a = 0; a < c; ++a) acc = cadd(acc, cmul(row[a], vs[a + j * c]));
+    out[e] = acc;
+  }
+}
+
+// out[a * cells + x] = table[phase(x) + a * nphase] for a < k: a field whose
+// rows are k complex coefficient vectors indexed by the phase of each cell.
+__global__ void phase_table_field_kernel(const uint8_t* __restrict__ phase, long long cells,
+                                         const Cx<double>* __restrict__ table, int nphase, int k,
+                                         Cx<double>* __restrict__ out) {
+  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < cells;
+       x += (long long)gridDim.x * blockDim.x) {
+    int p = phase[x];
+    if (p >= nphase) p = nphase - 1;
+    for (int a = 0; a < k; ++a) out[(long long)a * cells + x] = table[p + a * nphase];
   }
 }
 

@@ -145,6 +145,7 @@ struct qtt_ctx {
   std::atomic<uint64_t> launches{0};
   std::mutex prof_mu;
   int concurrent_loads = 1;  // load cases of ls_solve_ceff run side by side
+  double gram_threshold = 2e9;     // TT-SVD: 8 P c min(P, c) above this takes the Gram path
   double jacobi_tol_scale = 1.0;   // Jacobi stop: |a_p^H a_q| <= scale sqrt(m) eps |a_p||a_q|
   int jacobi_max_sweeps32 = 40;    // sweep cap in FP32 mode
   void* pinned = nullptr;  // small host readback buffer
@@ -248,6 +249,8 @@ inline MatRef mref(const void* p, long long rs, long long cs, long long b1 = 0, 
                    long long b3 = 0, int conj = 0) {
   return MatRef{p, rs, cs, b1, b2, b3, conj};
 }
+
+constexpr long long kSMs = 152;  // streaming multiprocessors of a GB300
 
 int grid1d(long long n, int threads = 256) {
   long long b = (n + threads - 1) / threads;
@@ -365,6 +368,37 @@ struct Eng {
     check_span(B.p, span(K, B.rs, N, B.cs, nb1, B.b1, nb2, B.b2, nb3, B.b3), "gemm B");
     check_span(C, span(M, c_rs, N, c_cs, nb1, c_b1, nb2, c_b2, nb3, c_b3), "gemm C");
     constexpr int BM = 64, BN = 64, BK = sizeof(R) == 8 ? 8 : 16;
+    {
+      // Few output tiles and a long K (the sketched carry T Psi: M = 2 r,
+      // N = r + oversampling, K = r x operator rank): split K over enough
+      // CTAs to cover the SMs, partial products summed by a second kernel in
+      // a fixed order (deterministic, unlike atomics).
+      const long long tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN) * (long long)nb1 * nb2 * nb3;
+      if (g.ksplit == 1 && tiles < kSMs && K >= 256) {
+        long long ks = std::min<long long>((2 * kSMs + tiles - 1) / tiles, K / 128);
+        ks = std::min<long long>(ks, 32);
+        const long long nbat = (long long)nb1 * nb2 * nb3;
+        if (ks >= 2 && ks * nbat <= 65535 && ks * nbat * M * N <= (16ll << 20)) {
+          Cx<R>* part = alloc(ks * nbat * M * N);
+          g.ksplit = (int)ks;
+          g.nb1 = nb1;
+          g.part = part;
+          const dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)((N + BN - 1) / BN),
+                          (unsigned)(nbat * ks));
+          {
+            ProfScope ps(c, st(), 0, 8.0 * M * N * (double)K * nbat);
+            gemm_kernel<R, BM, BN, BK, 4, 4><<<grid, dim3(256), 0, st()>>>(g);
+            post("gemm_kernel", __LINE__);
+            splitk_reduce_kernel<R><<<grid1d(nbat * M * N), 256, 0, st()>>>(
+                part, (int)ks, nbat, M, N, nb2, nb3, (Cx<R>*)C, c_rs, c_cs, c_b1, c_b2, c_b3,
+                beta.re, beta.im);
+            post("splitk_reduce_kernel", __LINE__);
+          }
+          release(part);
+          return;
+        }
+      }
+    }
     const long long per_b1 = (long long)nb2 * nb3 * g.ksplit;
     QREQ(per_b1 <= 65535, "gemm batch too large");
     const int chunk = (int)std::max<long long>(1, 65535 / per_b1);
@@ -1144,7 +1178,7 @@ std::vector<Cx<double>*> tt_svd_device(Eng<double>& e, Cx<double>* T, const std:
     const int c = dims[j] * ranks[j + 1];
     const long long P = prod_dims(dims.data(), 0, j);
     QREQ(P < (1ll << 31), "TT-SVD unfolding too large");
-    if (8.0 * (double)P * c * std::min<double>(P, c) < 2e9) {
+    if (8.0 * (double)P * c * std::min<double>(P, c) < e.c->gram_threshold) {
       // Small unfolding: accurate SVD of M itself (QR + one-sided Jacobi; no
       // squared condition number). M = U S V^H, core j = V[:, :kk]^H, carry
       // = U[:, :kk] S (row-major P x kk for the next reshape).
@@ -1199,10 +1233,20 @@ std::vector<Cx<double>*> tt_svd_device(Eng<double>& e, Cx<double>* T, const std:
     // eigenvectors V of the Gram matrix G = M^H M (column-major for the
     // Jacobi kernel)
     Cx<double>* G = e.alloc((long long)c * c);
-    const int ks = (int)std::min<long long>(std::max<long long>(1, P / 8192),
-                                            4096 / std::max(1, (c / 64 + 1) * (c / 64 + 1)));
-    e.gemm(c, c, (int)P, mref(M, 1, c, 0, 0, 0, 1), mref(M, c, 1), G, 1, c, 0, 0, 0, 1, 1, 1,
-           Cplx{1, 0}, Cplx{0, 0}, std::max(1, ks));
+    if (c <= kGramMaxCols) {
+      // tall-skinny: a dedicated kernel (a 64 x 64 GEMM tile wastes (64/c)^2)
+      e.zero(G, (long long)c * c);
+      const int ch = kGramChunk / c;
+      long long rows = std::max<long long>(ch, (P + 152 * 6 - 1) / (152 * 6));
+      const long long nb = (P + rows - 1) / rows;
+      gram_skinny_kernel<double><<<(unsigned)nb, 256, 0, e.st()>>>(M, P, c, rows, G);
+      e.post("gram_skinny_kernel", __LINE__);
+    } else {
+      const int ks = (int)std::min<long long>(std::max<long long>(1, P / 8192),
+                                              4096 / std::max(1, (c / 64 + 1) * (c / 64 + 1)));
+      e.gemm(c, c, (int)P, mref(M, 1, c, 0, 0, 0, 1), mref(M, c, 1), G, 1, c, 0, 0, 0, 1, 1, 1,
+             Cplx{1, 0}, Cplx{0, 0}, std::max(1, ks));
+    }
     Cx<double>* U = e.alloc((long long)c * c);
     Cx<double>* V = e.alloc((long long)c * c);
     double* sig = (double*)e.ln->arena->alloc(sizeof(double) * c);
@@ -1215,7 +1259,12 @@ std::vector<Cx<double>*> tt_svd_device(Eng<double>& e, Cx<double>* T, const std:
     // accuracy (the Gram eigenvalues carry noise ~ c eps lambda_max, which
     // would swamp the tail threshold for wide bonds); they decide the rank.
     Cx<double>* MV = e.alloc(P * c);
-    e.gemm((int)P, c, c, mref(M, c, 1), mref(V, 1, c), MV, c, 1, 0, 0, 0, 1, 1, 1);
+    if (c <= kSkinnyMaxCols) {
+      matmul_skinny_kernel<double><<<grid1d(P * c), 256, 0, e.st()>>>(M, P, c, V, MV);
+      e.post("matmul_skinny_kernel", __LINE__);
+    } else {
+      e.gemm((int)P, c, c, mref(M, c, 1), mref(V, 1, c), MV, c, 1, 0, 0, 0, 1, 1, 1);
+    }
     double* cn = (double*)e.ln->arena->alloc(sizeof(double) * c);
     QCHECK(cudaMemsetAsync(cn, 0, sizeof(double) * c, e.st()));
     colnorm2_kernel<double><<<grid1d(P * c), 256, sizeof(double) * c, e.st()>>>(MV, P, c, cn);
@@ -1429,15 +1478,24 @@ qtt_op* build_sfft(qtt_ctx* c, int n, int adjoint, double eps) {
 
 // Raised operator from a dense (36, 2^bits) FP64 complex field with
 // broadcast axes (axis a contributes nbits[a] cores from the field or n
-// identity cores when broadcast).
+// identity cores when broadcast). With `Uleft` (column-major 36 x rows, and
+// F holding `rows` rows) the field is Uleft F and Uleft multiplies the first
+// core after the TT-SVD.
 qtt_op* raised_from_field(qtt_ctx* c, Cx<double>* F, int n, const int bcast[3], double eps,
-                          int rmax) {
+                          int rmax, int rows = 36, const Cx<double>* Uleft = nullptr) {
   Eng<double> e(c);
   int bits = 0;
   for (int a = 0; a < 3; ++a) bits += bcast[a] ? 0 : n;
   std::vector<int> dims(1 + bits, 2), ranks;
-  dims[0] = 36;
+  dims[0] = rows;
   std::vector<Cx<double>*> tc = tt_svd_device(e, F, dims, eps, rmax, ranks, true);
+  if (Uleft) {
+    Cx<double>* c0 = e.alloc(36ll * ranks[1]);
+    e.gemm(36, ranks[1], rows, mref(Uleft, 1, 36), mref(tc[0], ranks[1], 1), c0, ranks[1], 1, 0,
+           0, 0, 1, 1, 1);
+    e.release(tc[0]);
+    tc[0] = c0;
+  }
   const int L = 3 * n + 1;
   std::vector<Cx<double>*> cores(L);
   std::vector<int> R(L + 1, 1), dout(L, 2), din(L, 2), diag(L, 1);
@@ -1470,6 +1528,69 @@ qtt_op* raised_from_field(qtt_ctx* c, Cx<double>* F, int n, const int bcast[3], 
     }
   return c->prec == QTT_FP64 ? op_from_fp64<double>(c, cores, R, dout, din, diag)
                              : op_from_fp64<float>(c, cores, R, dout, din, diag);
+}
+
+// Raised operator of a phase field whose cells carry one of nphase Voigt
+// matrices, D[:, p] = Dh[36 p .. 36 p + 36). The field's 36 Voigt rows lie in
+// the column space of D: with the thin SVD D = U S V^H the field is U Y,
+// Y[a, x] = s_a conj(V[phase(x), a]). U has orthonormal columns, so it leaves
+// the singular values of every unfolding unchanged: the TT-SVD of the k-row
+// field Y, with U applied to its first core, is that of the 36-row field up to
+// rounding, on k/36 of the data (k <= 2 for isotropic phases).
+qtt_op* raised_from_phases(qtt_ctx* ctx, const uint8_t* phase, long long cells, const double* Dh,
+                           int nphase, int n, const int bc[3], double eps, int rmax) {
+  Eng<double> e(ctx);
+  uint8_t* dph = (uint8_t*)ctx->arena.alloc(cells);
+  QCHECK(cudaMemcpyAsync(dph, phase, cells, cudaMemcpyHostToDevice, ctx->stream));
+  if (nphase > 36) {  // no reduction possible: the 36-row field itself
+    double* ddc = (double*)ctx->arena.alloc(sizeof(double) * 36 * nphase);
+    QCHECK(cudaMemcpyAsync(ddc, Dh, sizeof(double) * 36 * nphase, cudaMemcpyHostToDevice,
+                           ctx->stream));
+    Cx<double>* F = e.alloc(36 * cells);
+    stiffness_field_kernel<<<grid1d(cells), 256, 0, ctx->stream>>>(dph, cells, ddc, nphase, F);
+    e.post("stiffness_field_kernel", __LINE__);
+    QCHECK(cudaStreamSynchronize(ctx->stream));
+    ctx->arena.release(dph);
+    ctx->arena.release(ddc);
+    return raised_from_field(ctx, F, n, bc, eps, rmax);  // consumes F
+  }
+  // D as a complex column-major 36 x nphase matrix (same linear order)
+  std::vector<double> hD(2 * 36 * nphase, 0.0);
+  double nD2 = 0;
+  for (int i = 0; i < 36 * nphase; ++i) {
+    hD[2 * i] = Dh[i];
+    nD2 += Dh[i] * Dh[i];
+  }
+  Cx<double>* A = e.alloc(36ll * nphase);
+  QCHECK(cudaMemcpyAsync(A, hD.data(), hD.size() * sizeof(double), cudaMemcpyHostToDevice,
+                         ctx->stream));
+  Cx<double>* U = e.alloc(36ll * nphase);
+  Cx<double>* V = e.alloc((long long)nphase * nphase);
+  double* sg = (double*)ctx->arena.alloc(sizeof(double) * nphase);
+  int cap = 0;
+  // directions below 1e-14 of ||D|| are rounding noise of the differences
+  const int k = e.svd(36, nphase, A, U, sg, V, 1e-28 * nD2, nphase, &cap);
+  // table[p + a nphase] = s_a conj(V[p, a])
+  Cx<double>* table = e.alloc((long long)nphase * k);
+  {
+    const long long sz[1] = {(long long)nphase * k}, st1[1] = {1};
+    e.copy(V, table, 1, sz, st1, st1, 1);
+  }
+  scale_cols_kernel<double><<<grid1d((long long)nphase * k), 256, 0, e.st()>>>(table, nphase, k,
+                                                                               sg);
+  e.post("scale_cols_kernel", __LINE__);
+  Cx<double>* Y = e.alloc((long long)k * cells);
+  phase_table_field_kernel<<<grid1d(cells), 256, 0, e.st()>>>(dph, cells, table, nphase, k, Y);
+  e.post("phase_table_field_kernel", __LINE__);
+  QCHECK(cudaStreamSynchronize(ctx->stream));
+  e.release(A);
+  e.release(V);
+  e.release(table);
+  ctx->arena.release(sg);
+  ctx->arena.release(dph);
+  qtt_op* o = raised_from_field(ctx, Y, n, bc, eps, rmax, k, U);  // consumes Y
+  e.release(U);
+  return o;
 }
 
 qtt_op* build_gamma(qtt_ctx* c, int n, double lam0, double mu0, int scheme, double eps, int rmax) {
@@ -1928,19 +2049,7 @@ int qtt_from_phase_field(qtt_ctx_t ctx, const uint8_t* phase, const int shape[3]
     voigt_stiffness(l, m, Cp);
     for (int i = 0; i < 36; ++i) dCh[p * 36 + i] = Cp[i] - C0[i];
   }
-  Eng<double> e(ctx);
-  uint8_t* dph = (uint8_t*)ctx->arena.alloc(cells);
-  double* ddc = (double*)ctx->arena.alloc(sizeof(double) * 36 * nphase);
-  QCHECK(cudaMemcpyAsync(dph, phase, cells, cudaMemcpyHostToDevice, ctx->stream));
-  QCHECK(cudaMemcpyAsync(ddc, dCh.data(), sizeof(double) * 36 * nphase, cudaMemcpyHostToDevice,
-                         ctx->stream));
-  Cx<double>* F = e.alloc(36 * cells);
-  stiffness_field_kernel<<<grid1d(cells), 256, 0, ctx->stream>>>(dph, cells, ddc, nphase, F);
-  e.post("stiffness_field_kernel", __LINE__);
-  QCHECK(cudaStreamSynchronize(ctx->stream));
-  ctx->arena.release(dph);
-  ctx->arena.release(ddc);
-  qtt_op* o = raised_from_field(ctx, F, n, bc, eps_tt, rmax);  // consumes F
+  qtt_op* o = raised_from_phases(ctx, phase, cells, dCh.data(), nphase, n, bc, eps_tt, rmax);
   o->n = n;
   o->has_c0 = 1;
   o->lame0[0] = lam0;
@@ -2191,19 +2300,7 @@ int qtt_from_phase_matrices(qtt_ctx_t ctx, const uint8_t* phase, const int shape
     bc[a] = shape[a] == 1;
     cells *= shape[a];
   }
-  Eng<double> e(ctx);
-  uint8_t* dph = (uint8_t*)ctx->arena.alloc(cells);
-  double* dm = (double*)ctx->arena.alloc(sizeof(double) * 36 * nphase);
-  QCHECK(cudaMemcpyAsync(dph, phase, cells, cudaMemcpyHostToDevice, ctx->stream));
-  QCHECK(cudaMemcpyAsync(dm, mats, sizeof(double) * 36 * nphase, cudaMemcpyHostToDevice,
-                         ctx->stream));
-  Cx<double>* F = e.alloc(36 * cells);
-  stiffness_field_kernel<<<grid1d(cells), 256, 0, ctx->stream>>>(dph, cells, dm, nphase, F);
-  e.post("stiffness_field_kernel", __LINE__);
-  QCHECK(cudaStreamSynchronize(ctx->stream));
-  ctx->arena.release(dph);
-  ctx->arena.release(dm);
-  qtt_op* o = raised_from_field(ctx, F, n, bc, eps_tt, rmax);  // consumes F
+  qtt_op* o = raised_from_phases(ctx, phase, cells, mats, nphase, n, bc, eps_tt, rmax);
   o->n = n;
   *out = o;
   return QTT_OK;
@@ -2292,6 +2389,12 @@ int qtt_ctx_set_jacobi(qtt_ctx_t ctx, double tol_scale, int max_sweeps_fp32) {
   if (!ctx || !(tol_scale > 0) || max_sweeps_fp32 < 1 || max_sweeps_fp32 > 200) return QTT_EINVAL;
   ctx->jacobi_tol_scale = tol_scale;
   ctx->jacobi_max_sweeps32 = max_sweeps_fp32;
+  return QTT_OK;
+}
+
+int qtt_ctx_set_tt_svd(qtt_ctx_t ctx, double gram_threshold) {
+  if (!ctx || !(gram_threshold >= 0)) return QTT_EINVAL;
+  ctx->gram_threshold = gram_threshold;
   return QTT_OK;
 }
 

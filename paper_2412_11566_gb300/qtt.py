@@ -97,6 +97,7 @@ _sig("ls_solve_ops", _i, [_p, _p, _p, _p, _p, _dp, _dp, C.POINTER(SolveParams), 
 _sig("ls_solve", _i, [_p, _p, _dp, C.POINTER(SolveParams), _dp, C.POINTER(SolveInfo)])
 _sig("qtt_ctx_set_concurrency", _i, [_p, _i])
 _sig("qtt_ctx_set_jacobi", _i, [_p, _d, _i])
+_sig("qtt_ctx_set_tt_svd", _i, [_p, _d])
 _sig("ls_solve_ceff", _i, [_p, _p, C.POINTER(SolveParams), _ip, _i, _dp, C.POINTER(SolveInfo)])
 
 
@@ -175,6 +176,9 @@ class Context:
 
     def set_jacobi(self, tol_scale: float = 1.0, max_sweeps_fp32: int = 40):
         self.check(lib.qtt_ctx_set_jacobi(self.h, float(tol_scale), int(max_sweeps_fp32)))
+
+    def set_tt_svd(self, gram_threshold: float = 2e9):
+        self.check(lib.qtt_ctx_set_tt_svd(self.h, float(gram_threshold)))
 
     def set_profiling(self, on: bool):
         self.check(lib.qtt_ctx_set_profiling(self.h, int(on)))

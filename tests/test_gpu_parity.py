@@ -139,6 +139,46 @@ def test_stiffness_operator_broadcast_axis(Q, ctx64):
     assert rel(got, ref) < 1e-10
 
 
+@pytest.mark.parametrize("nphase", [3, 40])
+def test_phase_matrices_operator_vs_oracle(Q, ctx64, nphase):
+    """Arbitrary (non-isotropic) phase matrices: 3 phases take the reduced
+    path (field = U Y with the 36-row Voigt range of the 3 matrices), 40
+    phases exceed 36 and take the full 36-row field."""
+    n = 2
+    rng = np.random.default_rng(SEED + nphase)
+    ph = rng.integers(0, nphase, size=(4, 4, 4)).astype(np.uint8)
+    mats = rng.standard_normal((nphase, 6, 6))
+    op = Q.qtt_from_phase_matrices(ctx64, ph, n, mats, 1e-12)
+    got = oq.tto_full(from_lib_op(op.cores(), op.shape()[3]))
+    ref = oq.tto_full(oq.phase_matrices_qtt(ph, n, mats, 1e-12))
+    assert rel(got, ref) < 1e-10
+
+
+def test_operators_through_gram_path(Q):
+    """Every dense-field TT-SVD unfolding through the Gram path (threshold
+    0): the tall-skinny Gram and M V kernels for narrow bonds, the tiled
+    GEMM for wide ones."""
+    ctx = Q.Context(0, Q.QTT_FP64, 1 << 30, seed=SEED)
+    try:
+        ctx.set_tt_svd(0.0)
+        n = 3
+        ph = synth.centred_sphere(n, 0.3)
+        E, nu = (1.0, 10.0), (0.3, 0.25)
+        lam0 = dense.reference_lame(E, nu)
+        op = Q.qtt_from_phase_field(ctx, ph, n, E, nu, None, 1e-10)
+        got = oq.tto_full(from_lib_op(op.cores(), op.shape()[3]))
+        ref = oq.tto_full(oq.stiffness_qtt(ph, n, E, nu, lam0, 1e-12))
+        assert rel(got, ref) < 1e-9
+        g = Q.qtt_gamma_operator(ctx, n, 3.5, 1.25, 0, 1e-10)
+        got = oq.tto_full(from_lib_op(g.cores(), g.shape()[3]))
+        ref = oq.tto_full(oq.gamma_qtt(n, 3.5, 1.25, 1e-12))
+        assert rel(got, ref) < 1e-9
+        with pytest.raises(Q.QttError):
+            ctx.set_tt_svd(-1.0)
+    finally:
+        ctx.close()
+
+
 def test_mean_vs_dense(Q, ctx64):
     n = 2
     rng = np.random.default_rng(3)
