@@ -19,7 +19,11 @@ Steps follow the paper's order. Readings where the paper is garbled or silent:
   * Matrix-vector product: the paper uses an AMEn-adapted product (App. B); this
     oracle provides the exact contraction (Table 2, "contract") and a
     randomized sketch-and-orthogonalise product (successive randomized
-    compression), followed by rounding. Zip-up (SVD truncation on the fly without
+    compression), followed by rounding. Each right-to-left sketch environment
+    is replaced by an orthonormal basis of its range before it enters the next
+    one (orthonormal_range): the unnormalised environments are products of
+    random cores whose condition number grows ~10x per core (6e6 after six
+    cores at 16^3), which single precision cannot carry. Zip-up (SVD truncation on the fly without
     the right environment) was measured to lose 15-30 % of the product on the
     Green operator already at n = 3 and is not used.
   * SFFT: S = P_rev F+ per axis, F+[k, x] = N^-1/2 exp(+2 pi i k x / N), P_rev
@@ -269,6 +273,39 @@ def sketch_core(seed: int, apply_id: int, core: int, shape):
     return (_u32_to_unit(re) + 1j * _u32_to_unit(im)).reshape(shape)
 
 
+SKETCH_DROP_TAU = 1e-11  # relative Cholesky pivot below which a sketch column is dropped
+
+
+def orthonormal_range(P: np.ndarray, tau: float = SKETCH_DROP_TAU):
+    """Q = P M with orthonormal (or zero) columns spanning range(P): M is the
+    inverse of the upper Cholesky factor R of the Gram matrix P^H P (R^H R =
+    P^H P, real positive diagonal, i.e. the R of P's thin QR). A pivot of the
+    factorisation at or below tau * max_i (P^H P)_ii marks column j as linearly
+    dependent on the previous ones: row j of R and column j of M are zero, so Q
+    gets a zero column there. Returns (Q, M)."""
+    G = P.conj().T @ P
+    L = G.shape[0]
+    A = G.astype(np.complex128, copy=True)
+    R = np.zeros_like(A)
+    ref = float(np.max(np.real(np.diag(G)))) if L else 0.0
+    kept = np.zeros(L, dtype=bool)
+    for j in range(L):
+        d = float(np.real(A[j, j]))
+        if not d > tau * ref:
+            continue
+        kept[j] = True
+        R[j, j] = math.sqrt(d)
+        R[j, j + 1:] = A[j, j + 1:] / math.sqrt(d)
+        A[j + 1:, j + 1:] -= np.outer(R[j, j + 1:].conj(), R[j, j + 1:])
+    M = np.zeros_like(A)
+    for j in range(L):
+        if kept[j]:
+            e = np.zeros(L, dtype=np.complex128)
+            e[j] = 1.0
+            M[:, j] = (e - M[:, :j] @ R[:j, j]) / R[j, j]
+    return P @ M, M
+
+
 def sketch_ranks(op, x, ell: int):
     """Sketch bond sizes: min(ell, exact product rank, left and right grid dims)."""
     L = len(op)
@@ -285,7 +322,8 @@ def tto_apply_sketched(op, x, ell: int, seed: int, apply_id: int):
     """Compressed matrix-vector product by successive randomized compression:
       1. right-to-left: sketch the exact product's right parts with a random TT
          Omega of ranks ell_k,  Psi_k[a, s, p] = sum W_k[a, o, i, b] X_k[s, i, t]
-         Psi_{k+1}[b, t, q] Omega_k[p, o, q];
+         Psi_{k+1}[b, t, q] Omega_k[p, o, q], each Psi_k then replaced by an
+         orthonormal basis of its range (orthonormal_range);
       2. left-to-right: with carry C[r, a, s], form T[r, o, b, t] = sum C W_k X_k,
          Z = T Psi_{k+1} ((r o) x ell_k), Q = orth(Z) by Householder QR, keep Q as
          output core k and carry Q^H T.
@@ -302,7 +340,9 @@ def tto_apply_sketched(op, x, ell: int, seed: int, apply_id: int):
         XP = np.einsum("sit,btq->sibq", X, psi[k + 1])
         # U[s, i, b, p] = sum_q XP[s, i, b, q] Om[p, o, q]  (o kept)  -> [s, i, b, o, p]
         U = np.einsum("sibq,poq->sibop", XP, Om)
-        psi[k] = np.einsum("aoib,sibop->asp", W, U)
+        P = np.einsum("aoib,sibop->asp", W, U)
+        Q, _ = orthonormal_range(P.reshape(-1, P.shape[2]))
+        psi[k] = Q.reshape(P.shape)
     C = np.ones((1, 1, 1), dtype=np.complex128)
     out = []
     for k in range(L):
@@ -314,7 +354,10 @@ def tto_apply_sketched(op, x, ell: int, seed: int, apply_id: int):
             out.append(T.reshape(r, do, a1 * s1))
             break
         Z = np.einsum("robt,btp->rop", T, psi[k + 1]).reshape(r * do, -1)
-        Q, _ = np.linalg.qr(Z)
+        Q, Rz = np.linalg.qr(Z)
+        # a dropped sketch direction is an exactly zero column of Z; the QR's
+        # direction for it is arbitrary and is removed
+        Q[:, np.abs(np.diag(Rz)) == 0] = 0
         out.append(Q.reshape(r, do, Q.shape[1]))
         C = np.einsum("mr,rbt->mbt", Q.conj().T, T.reshape(r * do, a1, s1))
     return out

@@ -908,6 +908,98 @@ __global__ void gather_cols_kernel(const Cx<R>* __restrict__ src, long long P, i
   }
 }
 
+// Orthonormalising factor of a sketch environment. G (row-major L x L) is
+// the Gram matrix P^H P of a matrix P with L columns. One CTA computes the
+// upper Cholesky factor R (R^H R = G, real positive diagonal) in A (row-major,
+// overwritten) and M = R^{-1} (row-major, upper), so that P M has orthonormal
+// columns. A pivot at or below tau * max_i G_ii marks a column as dependent on
+// the previous ones: row j of R and column j of M are set to zero (P M then has
+// a zero column there). A non-finite diagonal sets *err and leaves M zero.
+template <typename R>
+__global__ void __launch_bounds__(1024)
+chol_drop_inv_kernel(int L, const Cx<R>* __restrict__ G, Cx<R>* A, Cx<R>* M, double tau,
+                     int* err) {
+  __shared__ R red[32];
+  __shared__ int s_bad;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const long long LL = (long long)L * L;
+  for (long long e = tid; e < LL; e += nt) {
+    A[e] = G[e];
+    M[e] = mk<R>(0, 0);
+  }
+  if (tid == 0) s_bad = 0;
+  __syncthreads();
+  R mx = 0;
+  for (int i = tid; i < L; i += nt) {
+    const R v = G[(long long)i * L + i].x;
+    if (!isfinite(v)) s_bad = 1;
+    mx = v > mx ? v : mx;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const R w = __shfl_xor_sync(0xffffffffu, mx, o);
+    mx = w > mx ? w : mx;
+  }
+  if ((tid & 31) == 0) red[tid >> 5] = mx;
+  __syncthreads();
+  if (s_bad) {
+    if (tid == 0) atomicExch(err, 1);
+    return;
+  }
+  R ref = 0;
+  for (int w = 0; w < (nt + 31) / 32; ++w) ref = red[w] > ref ? red[w] : ref;
+  const R thr = (R)tau * ref;
+  for (int j = 0; j < L; ++j) {
+    __syncthreads();
+    const R d = A[(long long)j * L + j].x;
+    __syncthreads();  // every thread has read the pivot before row j changes
+    Cx<R>* rowj = A + (long long)j * L;
+    if (!(d > thr)) {
+      for (int c = j + tid; c < L; c += nt) rowj[c] = mk<R>(0, 0);
+      continue;
+    }
+    const R sd = sqrt(d);
+    const R inv = (R)1 / sd;
+    for (int c = j + 1 + tid; c < L; c += nt) rowj[c] = cscale(rowj[c], inv);
+    if (tid == 0) rowj[j] = mk<R>(sd, 0);
+    __syncthreads();
+    const int t = L - j - 1;
+    for (long long e = tid; e < (long long)t * t; e += nt) {
+      const int r = j + 1 + (int)(e / t), c = j + 1 + (int)(e % t);
+      if (c < r) continue;
+      Cx<R>* p = A + (long long)r * L + c;
+      *p = csub(*p, cmulc(rowj[r], rowj[c]));
+    }
+  }
+  __syncthreads();
+  // M = R^{-1} column by column: M[i][j] = (d_ij - sum_{i<=l<j} M[i][l] R[l][j]) / R[j][j]
+  for (int j = 0; j < L; ++j) {
+    const R rjj = A[(long long)j * L + j].x;
+    if (rjj == (R)0) continue;  // dropped (uniform: every thread reads the same value)
+    const R inv = (R)1 / rjj;
+    for (int i = tid; i <= j; i += nt) {
+      Cx<R> acc = i == j ? mk<R>(1, 0) : mk<R>(0, 0);
+      for (int l = i; l < j; ++l)
+        acc = csub(acc, cmul(M[(long long)i * L + l], A[(long long)l * L + j]));
+      M[(long long)i * L + j] = cscale(acc, inv);
+    }
+    __syncthreads();
+  }
+}
+
+// Q[:, j] = 0 for every j < k with R[j][j] exactly zero (Q column-major m x k,
+// R column-major with leading dimension ldr): a zero column of the factored
+// matrix spans nothing, so the reflector's arbitrary direction is removed.
+template <typename R>
+__global__ void zero_dead_cols_kernel(Cx<R>* Q, int m, int k, const Cx<R>* Rm, int ldr) {
+  const long long tot = (long long)m * k;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(e / m);
+    const Cx<R> d = Rm[j + (long long)j * ldr];
+    if (d.x == (R)0 && d.y == (R)0) Q[e] = mk<R>(0, 0);
+  }
+}
+
 // Tall-skinny Gram matrix G += M^H M (G column-major c x c, zeroed by the
 // caller) of a row-major P x c matrix M with c <= kGramMaxCols. A 64 x 64 GEMM
 // tile would do (64/c)^2 times the useful work here, and FP64 is slow enough

@@ -509,6 +509,26 @@ struct Eng {
     release(v0);
   }
 
+  // M (row-major L x L, upper) with P M orthonormal-or-zero columns for the
+  // row-major m x L matrix P: Gram matrix by GEMM, then one CTA factors it
+  // (Cholesky with dependent columns dropped) and inverts the factor.
+  Cx<R>* orth_factor(const Cx<R>* P, long long m, int L, double tau, int* err) {
+    Cx<R>* G = alloc((long long)L * L);
+    QREQ(m < (1ll << 31), "orth_factor: too many rows");
+    gemm(L, L, (int)m, mref(P, 1, L, 0, 0, 0, 1), mref(P, L, 1), G, L, 1, 0, 0, 0, 1, 1, 1);
+    Cx<R>* A = alloc((long long)L * L);
+    Cx<R>* M = alloc((long long)L * L);
+    {
+      const double l3 = (double)L * L * L;
+      ProfScope ps(c, st(), 1, 8.0 * l3 / 3.0 * 2.0);
+      chol_drop_inv_kernel<R><<<1, 1024, 0, st()>>>(L, G, A, M, tau, err);
+      post("chol_drop_inv_kernel", __LINE__);
+    }
+    release(G);
+    release(A);
+    return M;
+  }
+
   // One-sided Jacobi SVD of the column-major m x n (m >= n) matrix in A
   // (destroyed): U (m x n), sigma (n, descending), V (n x n), all
   // column-major; returns the truncation rank for (delta2, rmax).
@@ -798,6 +818,15 @@ qtt_tt* apply_sketched(Eng<R>& e, const qtt_op* A, const qtt_tt* x, int ell, int
   }
   // ---- right-to-left sketches: Psi[b] has layout (s, a, l) = (x->ranks[b], A->ranks[b], lr[b])
   std::vector<Cx<R>*> psi(L + 1, nullptr);
+  // Mk[k]: Psi_k Mk[k] is an orthonormal basis (zero columns for dependent
+  // directions) of range(Psi_k). The next sketch is taken of that basis (Mk
+  // folded into the next random core) so that the environments' condition
+  // number does not compound over the cores (a product of random cores loses
+  // ~10x per core, more than single precision can hold after a few cores).
+  std::vector<Cx<R>*> Mk(L + 1, nullptr);
+  const double drop_tau = sizeof(R) == 8 ? 1e-11 : 1e-6;
+  int* oerr = (int*)e.ln->arena->alloc(sizeof(int));
+  QCHECK(cudaMemsetAsync(oerr, 0, sizeof(int), e.st()));
   psi[L] = e.alloc(1);
   {
     Cx<R> one = mk<R>(1, 0);
@@ -811,6 +840,14 @@ qtt_tt* apply_sketched(Eng<R>& e, const qtt_op* A, const qtt_tt* x, int ell, int
     sketch_kernel<R><<<grid1d((long long)L0 * Dout * L1), 256, 0, e.st()>>>(
         Om, (long long)L0 * Dout * L1, e.c->seed, k, apply_id);
     e.post("sketch_kernel", __LINE__);
+    if (Mk[k + 1]) {
+      // sketch of Psi_{k+1} M_{k+1}: Om'[(l0 o), j] = sum_l1 Om[(l0 o), l1] M[j, l1]
+      Cx<R>* Om2 = e.alloc((long long)L0 * Dout * L1);
+      e.gemm(L0 * Dout, L1, L1, mref(Om, L1, 1), mref(Mk[k + 1], 1, L1), Om2, L1, 1, 0, 0, 0, 1,
+             1, 1);
+      e.release(Om);
+      Om = Om2;
+    }
     // S1: XP[i][s0][a1 l1] = sum_s1 X[s0, i, s1] Psi[s1, (a1 l1)]
     Cx<R>* XP = e.alloc((long long)Din * S0 * A1 * L1);
     e.gemm(S0, A1 * L1, S1, mref(x->core[k], (long long)Din * S1, 1, S1), mref(psi[k + 1], (long long)A1 * L1, 1),
@@ -854,6 +891,7 @@ qtt_tt* apply_sketched(Eng<R>& e, const qtt_op* A, const qtt_tt* x, int ell, int
       e.ln->arena->release(nrm);
     }
     psi[k] = Pk;
+    Mk[k] = e.orth_factor(Pk, (long long)S0 * A0, L0, drop_tau, oerr);
   }
   // ---- left-to-right compression
   qtt_tt* y = new_tt(e.c, e.ln->arena, L, A->dout);
@@ -903,15 +941,25 @@ qtt_tt* apply_sketched(Eng<R>& e, const qtt_op* A, const qtt_tt* x, int ell, int
     }
     const int L1 = lr[k + 1];
     const int mz = Dout * Rr;
-    Cx<R>* Z = e.alloc((long long)mz * L1);
-    e.gemm(mz, L1, S1 * A1, mref(T, (long long)S1 * A1, 1), mref(psi[k + 1], L1, 1), Z, L1, 1, 0,
+    Cx<R>* Z0 = e.alloc((long long)mz * L1);
+    e.gemm(mz, L1, S1 * A1, mref(T, (long long)S1 * A1, 1), mref(psi[k + 1], L1, 1), Z0, L1, 1, 0,
            0, 0, 1, 1, 1);
     e.release(psi[k + 1]);
     psi[k + 1] = nullptr;
+    // Z = T Psi_{k+1} M_{k+1}: the sketch of T by the orthonormal basis
+    Cx<R>* Z = e.alloc((long long)mz * L1);
+    e.gemm(mz, L1, L1, mref(Z0, L1, 1), mref(Mk[k + 1], L1, 1), Z, L1, 1, 0, 0, 0, 1, 1, 1);
+    e.release(Z0);
+    e.release(Mk[k + 1]);
+    Mk[k + 1] = nullptr;
     const int kq = std::min(mz, L1);
     Cx<R>* Q = e.alloc((long long)mz * kq);
     Cx<R>* Rm = e.alloc((long long)kq * L1);
     e.qr(mz, L1, Z, L1, 1, 0, Q, Rm);
+    // a dropped sketch direction gives an exactly zero column of Z: its
+    // reflector direction is arbitrary, so it is removed from the output
+    zero_dead_cols_kernel<R><<<grid1d((long long)mz * kq), 256, 0, e.st()>>>(Q, mz, kq, Rm, kq);
+    e.post("zero_dead_cols_kernel", __LINE__);
     e.release(Z);
     e.release(Rm);
     // carry' (kq, S1, A1) = Q^H T
@@ -932,8 +980,19 @@ qtt_tt* apply_sketched(Eng<R>& e, const qtt_op* A, const qtt_tt* x, int ell, int
   }
   y->ranks[0] = 1;
   y->ranks[L] = 1;
-  for (int b = 0; b <= L; ++b)
+  for (int b = 0; b <= L; ++b) {
     if (psi[b]) e.release(psi[b]);
+    if (Mk[b]) e.release(Mk[b]);
+  }
+  int herr = 0;
+  QCHECK(cudaMemcpyAsync(e.ln->pinned, oerr, sizeof(int), cudaMemcpyDeviceToHost, e.st()));
+  QCHECK(cudaStreamSynchronize(e.st()));
+  memcpy(&herr, e.ln->pinned, sizeof(int));
+  e.ln->arena->release(oerr);
+  if (herr) {
+    free_tt(y);
+    throw QttError(QTT_ENAN, "sketched product: non-finite sketch environment");
+  }
   return y;
 }
 

@@ -181,10 +181,54 @@ def test_sketched_product_exact_with_full_sketch():
     ref = oq.tto_full(G) @ oq.tt_full(x).reshape(-1)
     y = oq.tto_apply_sketched(G, x, 10 ** 4, 1, 0)
     assert rel(oq.tt_full(y).reshape(-1), ref) < 1e-11
-    # output cores 0..L-2 left-orthonormal
+    # output cores 0..L-2 left-orthonormal, up to exactly zero columns where a
+    # sketch direction was dependent on the others
     for c in y[:-1]:
         M = c.reshape(-1, c.shape[2])
-        assert np.allclose(M.conj().T @ M, np.eye(M.shape[1]), atol=1e-11)
+        G = M.conj().T @ M
+        live = np.linalg.norm(M, axis=0) > 0
+        assert np.allclose(G, np.diag(live.astype(float)), atol=1e-11)
+
+
+def test_orthonormal_range_is_positive_diagonal_qr():
+    # full column rank: Q is the thin-QR factor whose R has a real positive
+    # diagonal (numpy's QR with its column phases moved into R)
+    rng = np.random.default_rng(31)
+    P = rng.standard_normal((40, 10)) + 1j * rng.standard_normal((40, 10))
+    Q, M = oq.orthonormal_range(P)
+    assert np.allclose(Q.conj().T @ Q, np.eye(10), atol=1e-12)
+    assert np.allclose(np.tril(M, -1), 0)
+    Rinv = np.linalg.inv(M)
+    assert np.allclose(Q @ Rinv, P, atol=1e-12)
+    Qn, Rn = np.linalg.qr(P)
+    ph = np.diag(Rn) / np.abs(np.diag(Rn))
+    assert np.allclose(Q, Qn * ph[None, :], atol=1e-12)
+    assert np.allclose(np.diag(Rinv).imag, 0) and np.all(np.diag(Rinv).real > 0)
+
+
+def test_orthonormal_range_drops_dependent_columns():
+    rng = np.random.default_rng(32)
+    P = rng.standard_normal((30, 9)) + 1j * rng.standard_normal((30, 9))
+    P[:, 3] = 2 * P[:, 0] - (1 - 1j) * P[:, 1]
+    P[:, 7] = 0
+    Q, M = oq.orthonormal_range(P)
+    assert np.all(Q[:, 3] == 0) and np.all(Q[:, 7] == 0)
+    assert np.all(M[:, 3] == 0) and np.all(M[:, 7] == 0)
+    live = [j for j in range(9) if j not in (3, 7)]
+    assert np.allclose(Q[:, live].conj().T @ Q[:, live], np.eye(7), atol=1e-12)
+    # same range: P is reproduced by its projection onto Q
+    assert np.allclose(Q @ (Q.conj().T @ P), P, atol=1e-11)
+
+
+def test_orthonormal_range_ill_conditioned():
+    # singular values 1 .. 1e-4: Gram condition 1e8, orthogonality to ~eps 1e8
+    rng = np.random.default_rng(33)
+    U, _ = np.linalg.qr(rng.standard_normal((50, 12)) + 1j * rng.standard_normal((50, 12)))
+    V, _ = np.linalg.qr(rng.standard_normal((12, 12)) + 1j * rng.standard_normal((12, 12)))
+    P = U @ np.diag(np.logspace(0, -4, 12)) @ V
+    Q, _ = oq.orthonormal_range(P)
+    assert np.allclose(Q.conj().T @ Q, np.eye(12), atol=1e-6)
+    assert np.allclose(Q @ (Q.conj().T @ P), P, atol=1e-12)
 
 
 def test_e_tt_and_mean():
