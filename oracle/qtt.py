@@ -277,32 +277,40 @@ SKETCH_DROP_TAU = 1e-11  # relative Cholesky pivot below which a sketch column i
 
 
 def orthonormal_range(P: np.ndarray, tau: float = SKETCH_DROP_TAU):
-    """Q = P M with orthonormal (or zero) columns spanning range(P): M is the
-    inverse of the upper Cholesky factor R of the Gram matrix P^H P (R^H R =
-    P^H P, real positive diagonal, i.e. the R of P's thin QR). A pivot of the
-    factorisation at or below tau * max_i (P^H P)_ii marks column j as linearly
-    dependent on the previous ones: row j of R and column j of M are zero, so Q
-    gets a zero column there. Returns (Q, M)."""
+    """Q = P M with orthonormal columns spanning range(P), followed by zero
+    columns: Cholesky factorisation R^H R = Pi^T (P^H P) Pi with diagonal
+    pivoting (step j takes the largest remaining diagonal entry, the first one
+    on ties), stopped when that entry is at or below tau * max_i (P^H P)_ii;
+    the k steps taken give Q[:, :k] = (P Pi)[:, :k] R^{-1} and Q[:, k:] = 0.
+    Pivoting keeps R^{-1} bounded where columns of P are nearly dependent.
+    Returns (Q, M)."""
     G = P.conj().T @ P
     L = G.shape[0]
     A = G.astype(np.complex128, copy=True)
-    R = np.zeros_like(A)
+    perm = np.arange(L)
     ref = float(np.max(np.real(np.diag(G)))) if L else 0.0
-    kept = np.zeros(L, dtype=bool)
+    k = 0
     for j in range(L):
+        dia = np.real(np.diag(A))[j:]
+        p = j + int(np.argmax(dia))
+        if not dia[p - j] > tau * ref:
+            break
+        A[[j, p], :] = A[[p, j], :]
+        A[:, [j, p]] = A[:, [p, j]]
+        perm[[j, p]] = perm[[p, j]]
         d = float(np.real(A[j, j]))
-        if not d > tau * ref:
-            continue
-        kept[j] = True
-        R[j, j] = math.sqrt(d)
-        R[j, j + 1:] = A[j, j + 1:] / math.sqrt(d)
-        A[j + 1:, j + 1:] -= np.outer(R[j, j + 1:].conj(), R[j, j + 1:])
-    M = np.zeros_like(A)
-    for j in range(L):
-        if kept[j]:
-            e = np.zeros(L, dtype=np.complex128)
-            e[j] = 1.0
-            M[:, j] = (e - M[:, :j] @ R[:j, j]) / R[j, j]
+        A[j, j] = math.sqrt(d)
+        A[j, j + 1:] = A[j, j + 1:] / math.sqrt(d)
+        A[j + 1:, j + 1:] -= np.outer(A[j, j + 1:].conj(), A[j, j + 1:])
+        k = j + 1
+    R = np.triu(A[:k, :k])
+    Rinv = np.zeros((k, k), dtype=np.complex128)
+    for j in range(k):
+        e = np.zeros(k, dtype=np.complex128)
+        e[j] = 1.0
+        Rinv[:, j] = (e - Rinv[:, :j] @ R[:j, j]) / R[j, j]
+    M = np.zeros((L, L), dtype=np.complex128)
+    M[perm[:k], :k] = Rinv
     return P @ M, M
 
 

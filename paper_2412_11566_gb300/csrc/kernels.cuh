@@ -909,24 +909,31 @@ __global__ void gather_cols_kernel(const Cx<R>* __restrict__ src, long long P, i
 }
 
 // Orthonormalising factor of a sketch environment. G (row-major L x L) is
-// the Gram matrix P^H P of a matrix P with L columns. One CTA computes the
-// upper Cholesky factor R (R^H R = G, real positive diagonal) in A (row-major,
-// overwritten) and M = R^{-1} (row-major, upper), so that P M has orthonormal
-// columns. A pivot at or below tau * max_i G_ii marks a column as dependent on
-// the previous ones: row j of R and column j of M are set to zero (P M then has
-// a zero column there). A non-finite diagonal sets *err and leaves M zero.
+// the Gram matrix P^H P of a matrix P with L columns. One CTA runs a Cholesky
+// factorisation with diagonal pivoting (step j takes the largest remaining
+// diagonal entry, the first on ties), R^H R = Pi^T G Pi, in A (row-major,
+// overwritten), and stops at the first step whose pivot is at or below
+// tau * max_i G_ii; with k steps taken, M (row-major L x L) gets
+// M[perm[i]][j] = (R^{-1})[i][j] for i <= j < k and zeros elsewhere, so that
+// P M has k orthonormal columns followed by zero ones. Pivoting keeps R^{-1}
+// bounded where columns of P are nearly dependent. perm is int scratch of L.
+// A non-finite diagonal of G sets *err and leaves M zero.
 template <typename R>
 __global__ void __launch_bounds__(1024)
-chol_drop_inv_kernel(int L, const Cx<R>* __restrict__ G, Cx<R>* A, Cx<R>* M, double tau,
-                     int* err) {
-  __shared__ R red[32];
-  __shared__ int s_bad;
-  const int tid = threadIdx.x, nt = blockDim.x;
+chol_piv_inv_kernel(int L, const Cx<R>* __restrict__ G, Cx<R>* A, Cx<R>* M, int* perm,
+                    double tau, int* err) {
+  __shared__ R red_v[32];
+  __shared__ int red_i[32];
+  __shared__ int s_bad, s_p;
+  __shared__ R s_d;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  const int nw = (nt + 31) >> 5;
   const long long LL = (long long)L * L;
   for (long long e = tid; e < LL; e += nt) {
     A[e] = G[e];
     M[e] = mk<R>(0, 0);
   }
+  for (int i = tid; i < L; i += nt) perm[i] = i;
   if (tid == 0) s_bad = 0;
   __syncthreads();
   R mx = 0;
@@ -939,48 +946,103 @@ chol_drop_inv_kernel(int L, const Cx<R>* __restrict__ G, Cx<R>* A, Cx<R>* M, dou
     const R w = __shfl_xor_sync(0xffffffffu, mx, o);
     mx = w > mx ? w : mx;
   }
-  if ((tid & 31) == 0) red[tid >> 5] = mx;
+  if (lane == 0) red_v[warp] = mx;
   __syncthreads();
   if (s_bad) {
     if (tid == 0) atomicExch(err, 1);
     return;
   }
   R ref = 0;
-  for (int w = 0; w < (nt + 31) / 32; ++w) ref = red[w] > ref ? red[w] : ref;
+  for (int w = 0; w < nw; ++w) ref = red_v[w] > ref ? red_v[w] : ref;
   const R thr = (R)tau * ref;
+  __syncthreads();
+  int k = L;
   for (int j = 0; j < L; ++j) {
-    __syncthreads();
-    const R d = A[(long long)j * L + j].x;
-    __syncthreads();  // every thread has read the pivot before row j changes
-    Cx<R>* rowj = A + (long long)j * L;
-    if (!(d > thr)) {
-      for (int c = j + tid; c < L; c += nt) rowj[c] = mk<R>(0, 0);
-      continue;
+    // pivot: largest remaining diagonal entry, lowest index on ties
+    R bv = (R)-1;
+    int bi = L;
+    for (int i = j + tid; i < L; i += nt) {
+      const R v = A[(long long)i * L + i].x;
+      if (v > bv) {
+        bv = v;
+        bi = i;
+      }
     }
+    for (int o = 16; o > 0; o >>= 1) {
+      const R ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > bv || (ov == bv && oi < bi)) {
+        bv = ov;
+        bi = oi;
+      }
+    }
+    if (lane == 0) {
+      red_v[warp] = bv;
+      red_i[warp] = bi;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      R v = red_v[0];
+      int ix = red_i[0];
+      for (int w = 1; w < nw; ++w)
+        if (red_v[w] > v || (red_v[w] == v && red_i[w] < ix)) {
+          v = red_v[w];
+          ix = red_i[w];
+        }
+      s_d = v;
+      s_p = ix;
+    }
+    __syncthreads();
+    if (!(s_d > thr) || s_p >= L) {  // uniform: every thread reads the same values
+      k = j;
+      break;
+    }
+    const int p = s_p;
+    if (p != j) {
+      for (int c = tid; c < L; c += nt) {
+        const Cx<R> t = A[(long long)j * L + c];
+        A[(long long)j * L + c] = A[(long long)p * L + c];
+        A[(long long)p * L + c] = t;
+      }
+      __syncthreads();
+      for (int r = tid; r < L; r += nt) {
+        const Cx<R> t = A[(long long)r * L + j];
+        A[(long long)r * L + j] = A[(long long)r * L + p];
+        A[(long long)r * L + p] = t;
+      }
+      if (tid == 0) {
+        const int t = perm[j];
+        perm[j] = perm[p];
+        perm[p] = t;
+      }
+      __syncthreads();
+    }
+    Cx<R>* rowj = A + (long long)j * L;
+    const R d = rowj[j].x;
     const R sd = sqrt(d);
     const R inv = (R)1 / sd;
+    __syncthreads();  // every thread has read the pivot before row j changes
     for (int c = j + 1 + tid; c < L; c += nt) rowj[c] = cscale(rowj[c], inv);
     if (tid == 0) rowj[j] = mk<R>(sd, 0);
     __syncthreads();
     const int t = L - j - 1;
     for (long long e = tid; e < (long long)t * t; e += nt) {
       const int r = j + 1 + (int)(e / t), c = j + 1 + (int)(e % t);
-      if (c < r) continue;
-      Cx<R>* p = A + (long long)r * L + c;
-      *p = csub(*p, cmulc(rowj[r], rowj[c]));
+      Cx<R>* q = A + (long long)r * L + c;
+      *q = csub(*q, cmulc(rowj[r], rowj[c]));
     }
+    __syncthreads();
   }
   __syncthreads();
-  // M = R^{-1} column by column: M[i][j] = (d_ij - sum_{i<=l<j} M[i][l] R[l][j]) / R[j][j]
-  for (int j = 0; j < L; ++j) {
-    const R rjj = A[(long long)j * L + j].x;
-    if (rjj == (R)0) continue;  // dropped (uniform: every thread reads the same value)
-    const R inv = (R)1 / rjj;
+  // R^{-1} of the leading k x k block, column by column, into the rows perm[i] of M:
+  // Rinv[i][j] = (d_ij - sum_{i<=l<j} Rinv[i][l] R[l][j]) / R[j][j]
+  for (int j = 0; j < k; ++j) {
+    const R inv = (R)1 / A[(long long)j * L + j].x;
     for (int i = tid; i <= j; i += nt) {
+      const long long mrow = (long long)perm[i] * L;
       Cx<R> acc = i == j ? mk<R>(1, 0) : mk<R>(0, 0);
-      for (int l = i; l < j; ++l)
-        acc = csub(acc, cmul(M[(long long)i * L + l], A[(long long)l * L + j]));
-      M[(long long)i * L + j] = cscale(acc, inv);
+      for (int l = i; l < j; ++l) acc = csub(acc, cmul(M[mrow + l], A[(long long)l * L + j]));
+      M[mrow + j] = cscale(acc, inv);
     }
     __syncthreads();
   }

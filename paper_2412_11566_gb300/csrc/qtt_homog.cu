@@ -511,21 +511,23 @@ struct Eng {
 
   // M (row-major L x L, upper) with P M orthonormal-or-zero columns for the
   // row-major m x L matrix P: Gram matrix by GEMM, then one CTA factors it
-  // (Cholesky with dependent columns dropped) and inverts the factor.
+  // (pivoted Cholesky stopped at dependent columns) and inverts the factor.
   Cx<R>* orth_factor(const Cx<R>* P, long long m, int L, double tau, int* err) {
     Cx<R>* G = alloc((long long)L * L);
     QREQ(m < (1ll << 31), "orth_factor: too many rows");
     gemm(L, L, (int)m, mref(P, 1, L, 0, 0, 0, 1), mref(P, L, 1), G, L, 1, 0, 0, 0, 1, 1, 1);
     Cx<R>* A = alloc((long long)L * L);
     Cx<R>* M = alloc((long long)L * L);
+    int* perm = (int*)ln->arena->alloc(sizeof(int) * L);
     {
       const double l3 = (double)L * L * L;
       ProfScope ps(c, st(), 1, 8.0 * l3 / 3.0 * 2.0);
-      chol_drop_inv_kernel<R><<<1, 1024, 0, st()>>>(L, G, A, M, tau, err);
-      post("chol_drop_inv_kernel", __LINE__);
+      chol_piv_inv_kernel<R><<<1, 1024, 0, st()>>>(L, G, A, M, perm, tau, err);
+      post("chol_piv_inv_kernel", __LINE__);
     }
     release(G);
     release(A);
+    ln->arena->release(perm);
     return M;
   }
 
@@ -818,8 +820,8 @@ qtt_tt* apply_sketched(Eng<R>& e, const qtt_op* A, const qtt_tt* x, int ell, int
   }
   // ---- right-to-left sketches: Psi[b] has layout (s, a, l) = (x->ranks[b], A->ranks[b], lr[b])
   std::vector<Cx<R>*> psi(L + 1, nullptr);
-  // Mk[k]: Psi_k Mk[k] is an orthonormal basis (zero columns for dependent
-  // directions) of range(Psi_k). The next sketch is taken of that basis (Mk
+  // Mk[k]: Psi_k Mk[k] is an orthonormal basis of range(Psi_k) followed by
+  // zero columns (dependent directions). The next sketch is taken of that basis (Mk
   // folded into the next random core) so that the environments' condition
   // number does not compound over the cores (a product of random cores loses
   // ~10x per core, more than single precision can hold after a few cores).

@@ -190,20 +190,26 @@ def test_sketched_product_exact_with_full_sketch():
         assert np.allclose(G, np.diag(live.astype(float)), atol=1e-11)
 
 
-def test_orthonormal_range_is_positive_diagonal_qr():
-    # full column rank: Q is the thin-QR factor whose R has a real positive
-    # diagonal (numpy's QR with its column phases moved into R)
+def test_orthonormal_range_is_pivoted_qr():
+    # full column rank: Q is the thin-QR factor, with real positive diagonal
+    # in R, of P with its columns in the pivot order (numpy's QR of the
+    # permuted matrix, column phases moved into R)
     rng = np.random.default_rng(31)
-    P = rng.standard_normal((40, 10)) + 1j * rng.standard_normal((40, 10))
+    P = (rng.standard_normal((40, 10)) + 1j * rng.standard_normal((40, 10))) * np.arange(1, 11)
     Q, M = oq.orthonormal_range(P)
     assert np.allclose(Q.conj().T @ Q, np.eye(10), atol=1e-12)
-    assert np.allclose(np.tril(M, -1), 0)
-    Rinv = np.linalg.inv(M)
-    assert np.allclose(Q @ Rinv, P, atol=1e-12)
-    Qn, Rn = np.linalg.qr(P)
+    # recover the pivot order: column j of Q uses P's columns perm[0..j]
+    order = []
+    for j in range(10):
+        nz = set(np.flatnonzero(np.abs(M[:, j]) > 0).tolist())
+        new_cols = nz - set(order)
+        assert len(new_cols) == 1
+        order.append(new_cols.pop())
+    assert order[0] == 9          # largest column norm first
+    Qn, Rn = np.linalg.qr(P[:, order])
     ph = np.diag(Rn) / np.abs(np.diag(Rn))
     assert np.allclose(Q, Qn * ph[None, :], atol=1e-12)
-    assert np.allclose(np.diag(Rinv).imag, 0) and np.all(np.diag(Rinv).real > 0)
+    assert np.allclose(Q @ (Q.conj().T @ P), P, atol=1e-11)
 
 
 def test_orthonormal_range_drops_dependent_columns():
@@ -212,10 +218,9 @@ def test_orthonormal_range_drops_dependent_columns():
     P[:, 3] = 2 * P[:, 0] - (1 - 1j) * P[:, 1]
     P[:, 7] = 0
     Q, M = oq.orthonormal_range(P)
-    assert np.all(Q[:, 3] == 0) and np.all(Q[:, 7] == 0)
-    assert np.all(M[:, 3] == 0) and np.all(M[:, 7] == 0)
-    live = [j for j in range(9) if j not in (3, 7)]
-    assert np.allclose(Q[:, live].conj().T @ Q[:, live], np.eye(7), atol=1e-12)
+    # rank 7: seven orthonormal columns, then exactly zero ones
+    assert np.allclose(Q[:, :7].conj().T @ Q[:, :7], np.eye(7), atol=1e-12)
+    assert np.all(Q[:, 7:] == 0) and np.all(M[:, 7:] == 0)
     # same range: P is reproduced by its projection onto Q
     assert np.allclose(Q @ (Q.conj().T @ P), P, atol=1e-11)
 
@@ -226,9 +231,11 @@ def test_orthonormal_range_ill_conditioned():
     U, _ = np.linalg.qr(rng.standard_normal((50, 12)) + 1j * rng.standard_normal((50, 12)))
     V, _ = np.linalg.qr(rng.standard_normal((12, 12)) + 1j * rng.standard_normal((12, 12)))
     P = U @ np.diag(np.logspace(0, -4, 12)) @ V
-    Q, _ = oq.orthonormal_range(P)
+    Q, M = oq.orthonormal_range(P)
     assert np.allclose(Q.conj().T @ Q, np.eye(12), atol=1e-6)
     assert np.allclose(Q @ (Q.conj().T @ P), P, atol=1e-12)
+    # pivoting bounds the inverse factor: |M| stays within 1/sigma_min scale
+    assert np.abs(M).max() < 1e6
 
 
 def test_e_tt_and_mean():
