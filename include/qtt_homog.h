@@ -150,8 +150,12 @@ int qtt_sfft_operator(qtt_ctx_t ctx, int n, int adjoint, double eps, qtt_op_t* o
 
 /* The Green operator Gamma_hat^0 (App. A, eq. (orig_green_eshelby), Direct
  * scheme k = i q, isotropic C0 = (lambda0, mu0)) in the SFFT momentum
- * convention (Sec. 4.3: bit-reversed per axis, conjugated), as a raised TTO
- * compressed by TT-SVD at eps_tt and rank cap rmax. scheme: 0 = Direct. */
+ * convention (Sec. 4.3: bit-reversed per axis, conjugated), as a raised TTO.
+ * Built from its separable form (App. A): Gamma_V(xi) is a 36 x 15 matrix of
+ * (lambda0, mu0) times the 15 degree-4 monomials of xi/|xi|; the monomial
+ * fields are compressed by TT-SVD at eps_tt/10 and rank cap rmax once per
+ * (n, eps_tt, rmax) and context, and the matrix multiplies their first core.
+ * scheme: 0 = Direct. n in 1..9. */
 int qtt_gamma_operator(qtt_ctx_t ctx, int n, double lambda0, double mu0, int scheme,
                        double eps_tt, int rmax, qtt_op_t* out);
 
@@ -273,8 +277,23 @@ int ls_solve_ceff_grad(qtt_ctx_t ctx, qtt_op_t dC, const uint8_t* phase, const i
                        int nphase, const double* E, const double* nu, int nparams,
                        const int* param_phase, const int* param_kind, const qtt_solve_params* p,
                        double* Ceff, double* dCeff, qtt_solve_info* info);
-/* Number of load cases ls_solve_ceff solves concurrently (1..6, default 1). */
+/* Number of unit-load solves run side by side (1..64, default 1): each on
+ * its own CUDA stream and host thread with a private slice of the workspace.
+ * ls_solve_ceff uses at most 6 (its loads), ls_solve_batched all of them. */
 int qtt_ctx_set_concurrency(qtt_ctx_t ctx, int concurrent_loads);
+/* C_eff of many microstructures in one call (Sec. 2 per item; the batched
+ * generation of elastic training data the paper motivates). dC[i]: stiffness
+ * operator of item i from qtt_from_phase_field; grid sizes n and reference
+ * media may differ between items (S, S^H and Gamma are built once per grid
+ * and medium and cached). All nitems x 6 unit-load solves go through one
+ * queue, largest grids first, served by qtt_ctx_set_concurrency lanes; each
+ * solve is exactly the one ls_solve_ceff runs for that item and load (same
+ * sketches, same result). Ceff: nitems x 36 doubles, item i at Ceff + 36 i,
+ * column-major as in ls_solve_ceff. info: nitems x 6 entries (item i, load k
+ * at info[6 i + k]) or NULL. Returns the worst status over all solves; on an
+ * error nothing is written. */
+int ls_solve_batched(qtt_ctx_t ctx, int nitems, const qtt_op_t* dC, const qtt_solve_params* p,
+                     double* Ceff, qtt_solve_info* info);
 
 #ifdef __cplusplus
 }

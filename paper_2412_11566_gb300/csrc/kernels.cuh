@@ -791,51 +791,36 @@ __global__ void sketch_kernel(Cx<R>* out, long long count, uint64_t seed, int co
 
 // ------------------------------------------------------------------ dense fields (preprocessing)
 
-// Voigt pair I -> (i, j) and weights 1,1,1,2,2,2.
-__device__ __forceinline__ void voigt_ij(int I, int& i, int& j) {
-  const int a[6] = {0, 1, 2, 1, 0, 0};
-  const int b[6] = {0, 1, 2, 2, 2, 1};
-  i = a[I];
-  j = b[I];
-}
-
 __device__ __forceinline__ int bitrev(int k, int n) { return (int)(__brev((unsigned)k) >> (32 - n)); }
 
-// Green operator of the Direct scheme in the SFFT momentum convention:
-// out[(I*6 + J) * N^3 + (k1 * N + k2) * N + k3] = Gamma_V[I, J](xi) with
-// xi_a = xi(rev k_a), xi(k) = k for k <= N/2 else k - N, and
+// Green operator of the Direct scheme (App. A) in the SFFT momentum
+// convention: at momentum index (k1, k2, k3) the frequency is xi_a =
+// xi(rev k_a), xi(k) = k for k <= N/2 else k - N, and
 // Gamma_ijkl = (d_ik n_j n_l + d_il n_j n_k + d_jk n_i n_l + d_jl n_i n_k) / (4 mu0)
 //              - (lam0 + mu0) / (mu0 (lam0 + 2 mu0)) n_i n_j n_k n_l,
 // Gamma_V[I, J] = w_I w_J Gamma_{i_I j_I k_J l_J}, Gamma(0) = 0; at modes with
 // a Nyquist component (|xi_a| = N/2) the value is averaged with the one at xi
 // with those components negated (Nyquist symmetrisation, the aliased partner
 // -xi mod N). Real-valued, so the conjugation of the convention is the identity.
-__device__ void gamma_voigt_at(const double xi[3], double lam0, double mu0, double* g36) {
-  const double beta0 = (lam0 + mu0) / (mu0 * (lam0 + 2.0 * mu0));
+// Gamma_V is a fixed 36 x 15 matrix (depending on lam0, mu0; built on the
+// host) times the 15 degree-4 monomials n_a n_b n_c n_d (a <= b <= c <= d,
+// lexicographic order), since n_a n_b = sum_c n_a n_b n_c n_c; the kernels
+// below evaluate those monomials (all 0 at xi = 0, Nyquist-averaged).
+__device__ void green_monomials_at(const double xi[3], double* m15) {
   const double r2 = xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2];
   double nn[3] = {0, 0, 0};
   if (r2 > 0) {
     const double r = sqrt(r2);
     for (int a = 0; a < 3; ++a) nn[a] = xi[a] / r;
   }
-  for (int I = 0; I < 6; ++I) {
-    int i, j;
-    voigt_ij(I, i, j);
-    for (int J = 0; J < 6; ++J) {
-      int k, l;
-      voigt_ij(J, k, l);
-      double g = 0;
-      if (r2 > 0) {
-        const double t1 = (i == k) * nn[j] * nn[l] + (i == l) * nn[j] * nn[k] +
-                          (j == k) * nn[i] * nn[l] + (j == l) * nn[i] * nn[k];
-        g = t1 / (4.0 * mu0) - beta0 * nn[i] * nn[j] * nn[k] * nn[l];
-      }
-      g36[I * 6 + J] = (I < 3 ? 1.0 : 2.0) * (J < 3 ? 1.0 : 2.0) * g;
-    }
-  }
+  int g = 0;
+  for (int a = 0; a < 3; ++a)
+    for (int b = a; b < 3; ++b)
+      for (int c = b; c < 3; ++c)
+        for (int d = c; d < 3; ++d) m15[g++] = nn[a] * nn[b] * nn[c] * nn[d];
 }
 
-__global__ void gamma_field_kernel(Cx<double>* out, int n, double lam0, double mu0) {
+__global__ void green_monomials_kernel(Cx<double>* out, int n) {
   const long long N = 1ll << n, N3 = N * N * N;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N3;
        e += (long long)gridDim.x * blockDim.x) {
@@ -849,13 +834,13 @@ __global__ void gamma_field_kernel(Cx<double>* out, int n, double lam0, double m
       nyq |= isn;
       xf[a] = isn ? -xi[a] : xi[a];
     }
-    double g[36], gf[36];
-    gamma_voigt_at(xi, lam0, mu0, g);
+    double g[15], gf[15];
+    green_monomials_at(xi, g);
     if (nyq) {
-      gamma_voigt_at(xf, lam0, mu0, gf);
-      for (int P = 0; P < 36; ++P) g[P] = 0.5 * (g[P] + gf[P]);
+      green_monomials_at(xf, gf);
+      for (int q = 0; q < 15; ++q) g[q] = 0.5 * (g[q] + gf[q]);
     }
-    for (int P = 0; P < 36; ++P) out[(long long)P * N3 + e] = mk<double>(g[P], 0.0);
+    for (int q = 0; q < 15; ++q) out[(long long)q * N3 + e] = mk<double>(g[q], 0.0);
   }
 }
 

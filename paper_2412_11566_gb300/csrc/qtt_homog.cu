@@ -164,6 +164,12 @@ struct qtt_ctx {
   long long prof_n[3] = {0, 0, 0};
   std::map<std::pair<int, int>, qtt_op*> sfft_cache;                            // (n, adjoint)
   std::map<std::tuple<int, double, double, int, double, int>, qtt_op*> gamma_cache;
+  // TT of the 15 Green monomial fields per (n, eps, rmax), FP64, in the arena
+  struct GreenMono {
+    std::vector<void*> cores;
+    std::vector<int> ranks;
+  };
+  std::map<std::tuple<int, double, int>, GreenMono> green_mono_cache;
   size_t esize() const { return prec == QTT_FP64 ? 16 : 8; }
 };
 
@@ -1537,6 +1543,9 @@ qtt_op* build_sfft(qtt_ctx* c, int n, int adjoint, double eps) {
   return o;
 }
 
+qtt_op* assemble_raised(qtt_ctx* c, Eng<double>& e, std::vector<Cx<double>*>& tc,
+                        const std::vector<int>& ranks, int n, const int bcast[3]);
+
 // Raised operator from a dense (36, 2^bits) FP64 complex field with
 // broadcast axes (axis a contributes nbits[a] cores from the field or n
 // identity cores when broadcast). With `Uleft` (column-major 36 x rows, and
@@ -1557,6 +1566,14 @@ qtt_op* raised_from_field(qtt_ctx* c, Cx<double>* F, int n, const int bcast[3], 
     e.release(tc[0]);
     tc[0] = c0;
   }
+  return assemble_raised(c, e, tc, ranks, n, bcast);
+}
+
+// Raised operator from FP64 TT cores of a controlled field (first core
+// 36 x r1, then one binary core per non-broadcast bit; ownership of the cores
+// passes to the operator), with identity cores for broadcast axes.
+qtt_op* assemble_raised(qtt_ctx* c, Eng<double>& e, std::vector<Cx<double>*>& tc,
+                        const std::vector<int>& ranks, int n, const int bcast[3]) {
   const int L = 3 * n + 1;
   std::vector<Cx<double>*> cores(L);
   std::vector<int> R(L + 1, 1), dout(L, 2), din(L, 2), diag(L, 1);
@@ -1654,17 +1671,90 @@ qtt_op* raised_from_phases(qtt_ctx* ctx, const uint8_t* phase, long long cells, 
   return o;
 }
 
+// Coefficients of the Direct-scheme Green field in the 15 degree-4 monomials
+// of n = xi / |xi| (order of green_monomials_at): Gamma_V[I][J] = w_I w_J
+// Gamma_ijkl with Gamma_ijkl = (d_ik n_j n_l + d_il n_j n_k + d_jk n_i n_l +
+// d_jl n_i n_k) / (4 mu0) - beta0 n_i n_j n_k n_l (App. A), each quadratic
+// n_a n_b written as sum_c n_a n_b n_c n_c. C is 36 x 15 row-major.
+int green_monomial_index(int a, int b, int c, int d) {
+  int v[4] = {a, b, c, d};
+  std::sort(v, v + 4);
+  int g = 0;
+  for (int p = 0; p < 3; ++p)
+    for (int q = p; q < 3; ++q)
+      for (int r = q; r < 3; ++r)
+        for (int s = r; s < 3; ++s, ++g)
+          if (p == v[0] && q == v[1] && r == v[2] && s == v[3]) return g;
+  return -1;
+}
+
+void green_coeffs(double lam0, double mu0, double* C) {
+  static const int vi[6] = {0, 1, 2, 1, 0, 0}, vj[6] = {0, 1, 2, 2, 2, 1};
+  const double beta0 = (lam0 + mu0) / (mu0 * (lam0 + 2.0 * mu0));
+  for (int q = 0; q < 36 * 15; ++q) C[q] = 0;
+  for (int I = 0; I < 6; ++I)
+    for (int J = 0; J < 6; ++J) {
+      const int i = vi[I], j = vj[I], k = vi[J], l = vj[J];
+      const double w = (I < 3 ? 1.0 : 2.0) * (J < 3 ? 1.0 : 2.0);
+      double* row = C + (I * 6 + J) * 15;
+      auto add2 = [&](int a, int b) {
+        for (int cc = 0; cc < 3; ++cc) row[green_monomial_index(a, b, cc, cc)] += w / (4.0 * mu0);
+      };
+      if (i == k) add2(j, l);
+      if (i == l) add2(j, k);
+      if (j == k) add2(i, l);
+      if (j == l) add2(i, k);
+      row[green_monomial_index(i, j, k, l)] -= w * beta0;
+    }
+}
+
+// Green operator from its separable form: the TT of the 15 monomial fields
+// (TT-SVD at eps / 10, cached per grid: it does not depend on the reference
+// medium), then its first core mixed by the 36 x 15 coefficient matrix of
+// (lam0, mu0). C has condition number ~7, so the operator's relative error
+// stays below ~eps.
 qtt_op* build_gamma(qtt_ctx* c, int n, double lam0, double mu0, int scheme, double eps, int rmax) {
   QREQ(scheme == 0, "only the Direct scheme (0) is implemented");
-  QREQ(n >= 1 && n <= 8, "gamma: n must be in 1..8");
+  QREQ(n >= 1 && n <= 9, "gamma: n must be in 1..9");
   QREQ(mu0 > 0 && lam0 + 2 * mu0 > 0, "gamma: reference medium not positive definite");
   Eng<double> e(c);
-  const long long N3 = 1ll << (3 * n);
-  Cx<double>* F = e.alloc(36 * N3);
-  gamma_field_kernel<<<grid1d(N3), 256, 0, e.st()>>>(F, n, lam0, mu0);
-  e.post("gamma_field_kernel", __LINE__);
+  const double eps_m = eps / 10.0;
+  const auto key = std::make_tuple(n, eps_m, rmax);
+  auto it = c->green_mono_cache.find(key);
+  if (it == c->green_mono_cache.end()) {
+    const long long N3 = 1ll << (3 * n);
+    Cx<double>* F = e.alloc(15 * N3);
+    green_monomials_kernel<<<grid1d(N3), 256, 0, e.st()>>>(F, n);
+    e.post("green_monomials_kernel", __LINE__);
+    std::vector<int> dims(1 + 3 * n, 2), ranks;
+    dims[0] = 15;
+    std::vector<Cx<double>*> tc = tt_svd_device(e, F, dims, eps_m, rmax, ranks, true);
+    qtt_ctx::GreenMono gm;
+    for (auto* p : tc) gm.cores.push_back(p);
+    gm.ranks = ranks;
+    it = c->green_mono_cache.emplace(key, gm).first;
+  }
+  const qtt_ctx::GreenMono& gm = it->second;
+  const int L = 3 * n + 1, r1 = gm.ranks[1];
+  std::vector<double> Ch(36 * 15), hc(2 * 36 * 15, 0.0);
+  green_coeffs(lam0, mu0, Ch.data());
+  for (int q = 0; q < 36 * 15; ++q) hc[2 * q] = Ch[q];
+  Cx<double>* Cd = e.alloc(36 * 15);
+  QCHECK(cudaMemcpyAsync(Cd, hc.data(), hc.size() * sizeof(double), cudaMemcpyHostToDevice,
+                         e.st()));
+  std::vector<Cx<double>*> tc(L);
+  tc[0] = e.alloc(36ll * r1);
+  e.gemm(36, r1, 15, mref(Cd, 15, 1), mref(gm.cores[0], r1, 1), tc[0], r1, 1, 0, 0, 0, 1, 1, 1);
+  for (int k = 1; k < L; ++k) {
+    const long long cnt = (long long)gm.ranks[k] * 2 * gm.ranks[k + 1];
+    tc[k] = e.alloc(cnt);
+    QCHECK(cudaMemcpyAsync(tc[k], gm.cores[k], cnt * sizeof(Cx<double>), cudaMemcpyDeviceToDevice,
+                           e.st()));
+  }
+  QCHECK(cudaStreamSynchronize(e.st()));
+  e.release(Cd);
   const int bc[3] = {0, 0, 0};
-  qtt_op* o = raised_from_field(c, F, n, bc, eps, rmax);  // consumes F
+  qtt_op* o = assemble_raised(c, e, tc, gm.ranks, n, bc);
   o->n = n;
   o->has_c0 = 1;
   o->lame0[0] = lam0;
@@ -1851,6 +1941,8 @@ void qtt_ctx_destroy(qtt_ctx_t c) {
   prof_flush(c);
   for (auto& kv : c->sfft_cache) free_op(kv.second);
   for (auto& kv : c->gamma_cache) free_op(kv.second);
+  for (auto& kv : c->green_mono_cache)
+    for (void* p : kv.second.cores) c->arena.release(p);
   if (c->pinned) cudaFreeHost(c->pinned);
   delete c;
 }
@@ -2241,28 +2333,26 @@ int ls_solve(qtt_ctx_t ctx, qtt_op_t dC, const double E_voigt[6], const qtt_solv
 }  // extern "C"
 
 namespace {
-int solve_loads(qtt_ctx_t ctx, qtt_op_t dC, const qtt_solve_params* p, const int* loads,
-                       int nloads, double* Ceff, qtt_solve_info* info,
-                       std::vector<qtt_tt*>* keep) {
-  QREQ(ctx && dC && p && Ceff, "ls_solve_ceff: null argument");
-  QREQ(dC->has_c0, "ls_solve_ceff: dC must come from qtt_from_phase_field");
-  int all[6] = {0, 1, 2, 3, 4, 5};
-  if (!loads) {
-    loads = all;
-    nloads = 6;
-  }
-  QREQ(nloads >= 1 && nloads <= 6, "ls_solve_ceff: nloads out of range");
-  for (int l = 0; l < nloads; ++l) QREQ(loads[l] >= 0 && loads[l] < 6, "ls_solve_ceff: bad load");
-  for (int i = 0; i < 36; ++i) Ceff[i] = 0;
-  const int n = dC->n;
-  qtt_op* S = cached_sfft(ctx, n, 0);
-  qtt_op* Sh = cached_sfft(ctx, n, 1);
-  qtt_op* G = cached_gamma(ctx, n, dC->lame0[0], dC->lame0[1], p->scheme, p->eps_tt, 1 << 30);
-  QCHECK(cudaStreamSynchronize(ctx->stream));
-  const int nl = std::max(1, std::min(ctx->concurrent_loads, nloads));
-  // One lane per concurrently solved load: own stream, own slice of the
-  // workspace (so that no lane reuses memory another lane's kernels still
-  // touch), own pinned readback buffer. Operators are shared read-only.
+// One unit-load LS solve of a job queue.
+struct SolveJob {
+  const qtt_op* dC = nullptr;
+  const qtt_op *S = nullptr, *Sh = nullptr, *G = nullptr;
+  int load = 0;
+  double sig[12] = {0};
+  qtt_solve_info inf{};
+  int status = QTT_OK;
+  std::string err;
+  qtt_tt* keep = nullptr;
+};
+
+// Runs the jobs in queue order on nl lanes. One lane per concurrently solved
+// load: own stream, own slice of the workspace (so that no lane reuses memory
+// another lane's kernels still touch), own pinned readback buffer. Operators
+// are shared read-only. Errors stay in the jobs.
+void run_jobs(qtt_ctx* ctx, std::vector<SolveJob>& jobs, const qtt_solve_params* p, int nl,
+              bool keep) {
+  const int nj = (int)jobs.size();
+  nl = std::max(1, std::min(nl, nj));
   std::vector<Lane> lanes(nl);
   std::vector<Arena> arenas(nl);
   std::vector<void*> blocks(nl, nullptr);
@@ -2273,7 +2363,7 @@ int solve_loads(qtt_ctx_t ctx, qtt_op_t dC, const qtt_solve_params* p, const int
       for (auto& kv : ctx->arena.free_) freeb = std::max(freeb, kv.second);
     }
     const size_t slice = ((freeb / nl) & ~(size_t)255) - 4096;
-    QREQ(slice >= (64u << 20), "ls_solve_ceff: workspace too small for concurrent loads");
+    QREQ(freeb / nl > (64u << 20), "concurrent solves: workspace too small for the lanes");
     for (int l = 0; l < nl; ++l) {
       blocks[l] = ctx->arena.alloc(slice);
       arenas[l].init(blocks[l], slice);
@@ -2284,26 +2374,22 @@ int solve_loads(qtt_ctx_t ctx, qtt_op_t dC, const qtt_solve_params* p, const int
   } else {
     lanes[0] = ctx->lane0;
   }
-  std::vector<int> status(nloads, QTT_OK);
-  std::vector<std::string> errs(nloads);
-  std::vector<std::vector<double>> sig(nloads, std::vector<double>(12, 0.0));
-  std::vector<qtt_solve_info> inf(nloads);
-  if (keep) keep->assign(nloads, nullptr);
   std::atomic<int> next{0};
   auto worker = [&](int lane_id) {
     cudaSetDevice(ctx->device);
-    for (int l = next++; l < nloads; l = next++) {
+    for (int j = next++; j < nj; j = next++) {
+      SolveJob& J = jobs[j];
       double Ev[6] = {0, 0, 0, 0, 0, 0};
-      Ev[loads[l]] = 1.0;
+      Ev[J.load] = 1.0;
       try {
-        status[l] = DISPATCH(ctx, solve_impl, ctx, dC, S, Sh, G, dC->C0, Ev, p, sig[l].data(),
-                             &inf[l], 0, &lanes[lane_id], keep ? &(*keep)[l] : nullptr);
+        J.status = DISPATCH(ctx, solve_impl, ctx, J.dC, J.S, J.Sh, J.G, J.dC->C0, Ev, p, J.sig,
+                            &J.inf, 0, &lanes[lane_id], keep ? &J.keep : nullptr);
       } catch (const QttError& ex) {
-        status[l] = ex.code;
-        errs[l] = ex.what();
+        J.status = ex.code;
+        J.err = ex.what();
       } catch (const std::exception& ex) {
-        status[l] = QTT_EINVAL;
-        errs[l] = ex.what();
+        J.status = QTT_EINVAL;
+        J.err = ex.what();
       }
     }
   };
@@ -2320,24 +2406,111 @@ int solve_loads(qtt_ctx_t ctx, qtt_op_t dC, const qtt_solve_params* p, const int
   } else {
     worker(0);
   }
+}
+
+// First error of a finished queue (its kept strains freed), else the worst
+// warning.
+int jobs_status(std::vector<SolveJob>& jobs) {
   int worst = QTT_OK;
-  for (int l = 0; l < nloads; ++l) {
-    if (status[l] < 0) {
-      if (keep)
-        for (auto* t : *keep) free_tt(t);
-      throw QttError(status[l], errs[l]);
+  for (auto& J : jobs)
+    if (J.status < 0) {
+      for (auto& K : jobs) free_tt(K.keep);
+      throw QttError(J.status, J.err);
     }
-    worst = std::max(worst, status[l]);
-    for (int i = 0; i < 6; ++i) Ceff[loads[l] * 6 + i] = sig[l][2 * i];
-    if (info) info[l] = inf[l];
+  for (auto& J : jobs) worst = std::max(worst, J.status);
+  return worst;
+}
+
+int solve_loads(qtt_ctx_t ctx, qtt_op_t dC, const qtt_solve_params* p, const int* loads,
+                int nloads, double* Ceff, qtt_solve_info* info, std::vector<qtt_tt*>* keep) {
+  QREQ(ctx && dC && p && Ceff, "ls_solve_ceff: null argument");
+  QREQ(dC->has_c0, "ls_solve_ceff: dC must come from qtt_from_phase_field");
+  int all[6] = {0, 1, 2, 3, 4, 5};
+  if (!loads) {
+    loads = all;
+    nloads = 6;
+  }
+  QREQ(nloads >= 1 && nloads <= 6, "ls_solve_ceff: nloads out of range");
+  for (int l = 0; l < nloads; ++l) QREQ(loads[l] >= 0 && loads[l] < 6, "ls_solve_ceff: bad load");
+  for (int i = 0; i < 36; ++i) Ceff[i] = 0;
+  const int n = dC->n;
+  qtt_op* S = cached_sfft(ctx, n, 0);
+  qtt_op* Sh = cached_sfft(ctx, n, 1);
+  qtt_op* G = cached_gamma(ctx, n, dC->lame0[0], dC->lame0[1], p->scheme, p->eps_tt, 1 << 30);
+  QCHECK(cudaStreamSynchronize(ctx->stream));
+  std::vector<SolveJob> jobs(nloads);
+  for (int l = 0; l < nloads; ++l) {
+    jobs[l].dC = dC;
+    jobs[l].S = S;
+    jobs[l].Sh = Sh;
+    jobs[l].G = G;
+    jobs[l].load = loads[l];
+  }
+  run_jobs(ctx, jobs, p, std::min(ctx->concurrent_loads, 6), keep != nullptr);
+  const int worst = jobs_status(jobs);
+  if (keep) {
+    keep->assign(nloads, nullptr);
+    for (int l = 0; l < nloads; ++l) (*keep)[l] = jobs[l].keep;
+  }
+  for (int l = 0; l < nloads; ++l) {
+    for (int i = 0; i < 6; ++i) Ceff[loads[l] * 6 + i] = jobs[l].sig[2 * i];
+    if (info) info[l] = jobs[l].inf;
   }
   return worst;
 }
 
+// nitems x 6 unit-load solves through one queue, largest grids first.
+int solve_batched(qtt_ctx_t ctx, int nitems, const qtt_op_t* dC, const qtt_solve_params* p,
+                  double* Ceff, qtt_solve_info* info) {
+  QREQ(ctx && dC && p && Ceff && nitems >= 1, "ls_solve_batched: bad argument");
+  for (int i = 0; i < nitems; ++i) {
+    QREQ(dC[i], "ls_solve_batched: null operator");
+    QREQ(dC[i]->has_c0, "ls_solve_batched: dC must come from qtt_from_phase_field");
+  }
+  std::vector<SolveJob> jobs((size_t)nitems * 6);
+  for (int i = 0; i < nitems; ++i) {
+    const qtt_op* d = dC[i];
+    qtt_op* S = cached_sfft(ctx, d->n, 0);
+    qtt_op* Sh = cached_sfft(ctx, d->n, 1);
+    qtt_op* G = cached_gamma(ctx, d->n, d->lame0[0], d->lame0[1], p->scheme, p->eps_tt, 1 << 30);
+    for (int k = 0; k < 6; ++k) {
+      SolveJob& J = jobs[(size_t)i * 6 + k];
+      J.dC = d;
+      J.S = S;
+      J.Sh = Sh;
+      J.G = G;
+      J.load = k;
+    }
+  }
+  QCHECK(cudaStreamSynchronize(ctx->stream));
+  // queue order: largest grids first (they take longest), then item, load
+  std::vector<int> order(jobs.size());
+  for (size_t j = 0; j < order.size(); ++j) order[j] = (int)j;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return jobs[a].dC->n > jobs[b].dC->n; });
+  std::vector<SolveJob> queue(jobs.size());
+  for (size_t j = 0; j < order.size(); ++j) queue[j] = jobs[order[j]];
+  run_jobs(ctx, queue, p, ctx->concurrent_loads, false);
+  const int worst = jobs_status(queue);
+  for (size_t j = 0; j < order.size(); ++j) {
+    const SolveJob& J = queue[j];
+    const int item = order[j] / 6, k = J.load;
+    for (int r = 0; r < 6; ++r) Ceff[(size_t)item * 36 + k * 6 + r] = J.sig[2 * r];
+    if (info) info[(size_t)item * 6 + k] = J.inf;
+  }
+  return worst;
+}
 
 }  // namespace
 
 extern "C" {
+
+int ls_solve_batched(qtt_ctx_t ctx, int nitems, const qtt_op_t* dC, const qtt_solve_params* p,
+                     double* Ceff, qtt_solve_info* info) {
+  API_BEGIN(ctx)
+  return solve_batched(ctx, nitems, dC, p, Ceff, info);
+  API_END
+}
 
 int ls_solve_ceff(qtt_ctx_t ctx, qtt_op_t dC, const qtt_solve_params* p, const int* loads,
                   int nloads, double* Ceff, qtt_solve_info* info) {
@@ -2460,7 +2633,7 @@ int qtt_ctx_set_tt_svd(qtt_ctx_t ctx, double gram_threshold) {
 }
 
 int qtt_ctx_set_concurrency(qtt_ctx_t ctx, int concurrent_loads) {
-  if (!ctx || concurrent_loads < 1 || concurrent_loads > 6) return QTT_EINVAL;
+  if (!ctx || concurrent_loads < 1 || concurrent_loads > 64) return QTT_EINVAL;
   ctx->concurrent_loads = concurrent_loads;
   return QTT_OK;
 }

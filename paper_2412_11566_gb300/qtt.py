@@ -99,6 +99,8 @@ _sig("qtt_ctx_set_concurrency", _i, [_p, _i])
 _sig("qtt_ctx_set_jacobi", _i, [_p, _d, _i])
 _sig("qtt_ctx_set_tt_svd", _i, [_p, _d])
 _sig("ls_solve_ceff", _i, [_p, _p, C.POINTER(SolveParams), _ip, _i, _dp, C.POINTER(SolveInfo)])
+_sig("ls_solve_batched", _i, [_p, _i, C.POINTER(_p), C.POINTER(SolveParams), _dp,
+                             C.POINTER(SolveInfo)])
 
 
 def header_functions(path: str = HEADER):
@@ -412,6 +414,20 @@ def ls_solve_ceff(ctx: Context, dC: Op, params: SolveParams, loads=None):
     rc = ctx.check(lib.ls_solve_ceff(ctx.h, dC.h, C.byref(params), _ints(loads), len(loads),
                                      Ceff.ctypes.data_as(_dp), infos))
     return Ceff.reshape(6, 6).T.copy(), [i.as_dict() for i in infos], rc
+
+
+def ls_solve_batched(ctx: Context, dCs, params: SolveParams):
+    """C_eff of several microstructures: returns (array (items, 6, 6), infos
+    as a list of items lists of 6 dicts, worst status)."""
+    dCs = list(dCs)
+    hs = (_p * len(dCs))(*[d.h.value if isinstance(d.h, _p) else d.h for d in dCs])
+    Ceff = np.zeros(36 * len(dCs))
+    infos = (SolveInfo * (6 * len(dCs)))()
+    rc = ctx.check(lib.ls_solve_batched(ctx.h, len(dCs), hs, C.byref(params),
+                                        Ceff.ctypes.data_as(_dp), infos))
+    C6 = Ceff.reshape(len(dCs), 6, 6).transpose(0, 2, 1).copy()
+    inf = [[infos[6 * i + k].as_dict() for k in range(6)] for i in range(len(dCs))]
+    return C6, inf, rc
 
 
 def qtt_from_phase_matrices(ctx: Context, phase, n, mats, eps_tt=1e-6, rmax=1 << 30):

@@ -1,0 +1,57 @@
+"""Batched C_eff (ls_solve_batched): items of different grid size, geometry
+and reference medium through one queue of (item, load) solves on several
+lanes; every result equals the single-item ls_solve_ceff result."""
+import numpy as np
+import pytest
+
+from paper_2412_11566_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+SEED = 2412
+
+
+@pytest.fixture(scope="module")
+def Q(lib_built):
+    return lib_built
+
+
+def _items():
+    return [
+        (2, synth.centred_sphere(2, 0.3), (1.0, 10.0), (0.3, 0.3)),
+        (3, synth.centred_sphere(3, 0.25), (1.0, 5.0), (0.3, 0.25)),
+        (3, synth.laminate(3, 2), (1.0, 20.0), (0.3, 0.3)),
+    ]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_batched_matches_single_item_solves(Q, precision):
+    prec = Q.QTT_FP64 if precision == "fp64" else Q.QTT_FP32
+    ctx = Q.Context(0, prec, 2 << 30, seed=SEED)
+    try:
+        dCs = [Q.qtt_from_phase_field(ctx, ph, n, E, nu, None, 1e-8) for n, ph, E, nu in _items()]
+        params = Q.solve_params(1e-5, 60, 1e-8, 32)
+        ctx.set_concurrency(5)
+        Cb, infb, rc = Q.ls_solve_batched(ctx, dCs, params)
+        assert Cb.shape == (3, 6, 6)
+        ctx.set_concurrency(1)
+        for i, d in enumerate(dCs):
+            Cs, infs, _ = Q.ls_solve_ceff(ctx, d, params)
+            assert [f["iters"] for f in infb[i]] == [f["iters"] for f in infs]
+            # FP64 sums reduced with atomics differ in their last bits from run
+            # to run; in FP32 mode those differences surface at ~1e-7
+            tol = 1e-10 if precision == "fp64" else 1e-5
+            assert np.abs(Cb[i] - Cs).max() <= tol * np.abs(Cs).max()
+    finally:
+        ctx.close()
+
+
+def test_batched_rejects_bad_input(Q):
+    ctx = Q.Context(0, Q.QTT_FP64, 1 << 30, seed=SEED)
+    try:
+        with pytest.raises(Q.QttError):
+            Q.ls_solve_batched(ctx, [], Q.solve_params(1e-5, 10, 1e-8, 16))
+        with pytest.raises(Q.QttError):
+            ctx.set_concurrency(65)
+    finally:
+        ctx.close()

@@ -109,12 +109,14 @@ def test_sfft_operator_vs_oracle(Q, ctx64, n):
 
 @pytest.mark.parametrize("n", [2, 3])
 def test_gamma_operator_vs_oracle(Q, ctx64, n):
-    lam0, mu0 = 3.5, 1.25
-    op = Q.qtt_gamma_operator(ctx64, n, lam0, mu0, 0, 1e-12)
-    cores, diag = op.cores(), op.shape()[3]
-    G = oq.tto_full(from_lib_op(cores, diag))
-    ref = oq.tto_full(oq.gamma_qtt(n, lam0, mu0, 1e-12))
-    assert rel(G, ref) < 1e-9
+    # two reference media from the same cached monomial TT (the separable
+    # construction), each against the oracle's TT-SVD of its own Green field
+    for lam0, mu0 in [(3.5, 1.25), (0.7, 4.0)]:
+        op = Q.qtt_gamma_operator(ctx64, n, lam0, mu0, 0, 1e-12)
+        cores, diag = op.cores(), op.shape()[3]
+        G = oq.tto_full(from_lib_op(cores, diag))
+        ref = oq.tto_full(oq.gamma_qtt(n, lam0, mu0, 1e-12))
+        assert rel(G, ref) < 1e-9
 
 
 def test_stiffness_operator_vs_oracle(Q, ctx64):
@@ -238,11 +240,9 @@ def test_ls_solve_vs_dense_oracle(Q, ctx64):
 
 def test_fp32_mode_vs_dense_oracle(Q):
     """FP32 mode (complex64 cores, FP32 contractions and factorisations, FP64
-    norms and C_eff average) against the tightly converged dense oracle. The
-    measured FP32-mode floor on this contrast-10 case is 1.07e-4 relative (the
-    per-iteration FP32 factorisation error amplified by the fixed-point
-    iteration); the bound below is that floor with margin, not the 1e-4
-    target of the method's accuracy goal."""
+    norms and C_eff average) against the tightly converged dense oracle:
+    7.6e-6 relative measured on this contrast-10 case (the FP32 residual floor
+    keeps the iteration from reaching tol 1e-6, so it runs to the cap)."""
     ctx = Q.Context(0, Q.QTT_FP32, 1 << 30, seed=SEED)
     n = 3
     ph = synth.centred_sphere(n, 0.3)
@@ -251,8 +251,27 @@ def test_fp32_mode_vs_dense_oracle(Q):
     C, infos, rc = Q.ls_solve_ceff(ctx, dC, Q.solve_params(1e-6, 500, 1e-6, 64), loads=[0, 3])
     Cd, imag, its = dense.ceff(ph, E, nu, tol=1e-10, loads=[0, 3])
     for k in (0, 3):
-        assert np.abs(C[:, k] - Cd[:, k]).max() < 2e-4 * np.abs(Cd).max()
+        assert np.abs(C[:, k] - Cd[:, k]).max() < 5e-5 * np.abs(Cd).max()
     ctx.close()
+
+
+def test_fp32_mode_eight_spheres_16(Q):
+    """The benchmark's 8-sphere geometry (contrast 20) at 16^3, FP32 mode at
+    the workload's settings (tol 1e-4, eps_tt 1e-6, r_max 128, which is the
+    full rank at this size): converges like FP64 (29 iterations) and meets the
+    1e-4 C_eff goal against the dense oracle (4.8e-5 measured). Before the
+    sketch environments were orthonormalised FP32 stalled at a 1e-2 residual."""
+    w = synth.spheres256(n=4)
+    ctx = Q.Context(0, Q.QTT_FP32, 4 << 30, seed=SEED)
+    try:
+        dC = Q.qtt_from_phase_field(ctx, w.phase, w.n, w.E, w.nu, None, w.eps_tt, w.rmax)
+        C, infos, rc = Q.ls_solve_ceff(ctx, dC, Q.solve_params(w.tol, 80, w.eps_tt, w.rmax),
+                                       loads=[0])
+        Cd, imag, its = dense.ceff(w.phase, w.E, w.nu, tol=1e-8, loads=[0])
+        assert infos[0]["iters"] < 40 and infos[0]["residual"] < w.tol
+        assert np.abs(C[:, 0] - Cd[:, 0]).max() < 1e-4 * np.abs(Cd).max()
+    finally:
+        ctx.close()
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
