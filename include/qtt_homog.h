@@ -153,9 +153,10 @@ int qtt_sfft_operator(qtt_ctx_t ctx, int n, int adjoint, double eps, qtt_op_t* o
  * convention (Sec. 4.3: bit-reversed per axis, conjugated), as a raised TTO.
  * Built from its separable form (App. A): Gamma_V(xi) is a 36 x 15 matrix of
  * (lambda0, mu0) times the 15 degree-4 monomials of xi/|xi|; the monomial
- * fields are compressed by TT-SVD at eps_tt/10 and rank cap rmax once per
- * (n, eps_tt, rmax) and context, and the matrix multiplies their first core.
- * scheme: 0 = Direct. n in 1..9. */
+ * fields are compressed by TT-SVD at eps_tt and rank cap rmax once per
+ * (n, eps_tt, rmax) and context, and the matrix multiplies their first core
+ * (relative error at most cond(matrix) eps_tt, cond ~7). scheme: 0 = Direct.
+ * n in 1..9. */
 int qtt_gamma_operator(qtt_ctx_t ctx, int n, double lambda0, double mu0, int scheme,
                        double eps_tt, int rmax, qtt_op_t* out);
 

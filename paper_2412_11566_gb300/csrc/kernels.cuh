@@ -896,17 +896,22 @@ __global__ void gather_cols_kernel(const Cx<R>* __restrict__ src, long long P, i
 // Orthonormalising factor of a sketch environment. G (row-major L x L) is
 // the Gram matrix P^H P of a matrix P with L columns. One CTA runs a Cholesky
 // factorisation with diagonal pivoting (step j takes the largest remaining
-// diagonal entry, the first on ties), R^H R = Pi^T G Pi, in A (row-major,
-// overwritten), and stops at the first step whose pivot is at or below
-// tau * max_i G_ii; with k steps taken, M (row-major L x L) gets
-// M[perm[i]][j] = (R^{-1})[i][j] for i <= j < k and zeros elsewhere, so that
-// P M has k orthonormal columns followed by zero ones. Pivoting keeps R^{-1}
-// bounded where columns of P are nearly dependent. perm is int scratch of L.
-// A non-finite diagonal of G sets *err and leaves M zero.
+// diagonal entry, the first on ties), R^H R = Pi^T G Pi, and stops at the
+// first step whose pivot is at or below tau * max_i G_ii; with k steps taken,
+// M (row-major L x L) gets M[perm[i]][j] = (R^{-1})[i][j] for i <= j < k and
+// zeros elsewhere, so that P M has k orthonormal columns followed by zero
+// ones. Pivoting keeps R^{-1} bounded where columns of P are nearly dependent.
+// The working matrix (L x L, then R, then R^{-1} in place) and an L-vector
+// live in dynamic shared memory when use_smem, else in Wg (L * L + L
+// entries). perm: int scratch of L. A non-finite diagonal of G sets *err and
+// leaves M zero.
 template <typename R>
 __global__ void __launch_bounds__(1024)
-chol_piv_inv_kernel(int L, const Cx<R>* __restrict__ G, Cx<R>* A, Cx<R>* M, int* perm,
-                    double tau, int* err) {
+chol_piv_inv_kernel(int L, const Cx<R>* __restrict__ G, Cx<R>* Wg, Cx<R>* M, int* perm,
+                    double tau, int* err, int use_smem) {
+  extern __shared__ __align__(16) unsigned char chol_dyn[];
+  Cx<R>* const A = use_smem ? (Cx<R>*)chol_dyn : Wg;
+  Cx<R>* const tmp = A + (long long)L * L;
   __shared__ R red_v[32];
   __shared__ int red_i[32];
   __shared__ int s_bad, s_p;
@@ -1019,17 +1024,26 @@ chol_piv_inv_kernel(int L, const Cx<R>* __restrict__ G, Cx<R>* A, Cx<R>* M, int*
     __syncthreads();
   }
   __syncthreads();
-  // R^{-1} of the leading k x k block, column by column, into the rows perm[i] of M:
-  // Rinv[i][j] = (d_ij - sum_{i<=l<j} Rinv[i][l] R[l][j]) / R[j][j]
+  // R^{-1} of the leading k x k block in place, column by column:
+  // Rinv[i][j] = -(sum_{i<=l<j} Rinv[i][l] R[l][j]) / R[j][j] (i < j),
+  // Rinv[j][j] = 1 / R[j][j]; columns < j already hold Rinv, column j still R
   for (int j = 0; j < k; ++j) {
-    const R inv = (R)1 / A[(long long)j * L + j].x;
-    for (int i = tid; i <= j; i += nt) {
-      const long long mrow = (long long)perm[i] * L;
-      Cx<R> acc = i == j ? mk<R>(1, 0) : mk<R>(0, 0);
-      for (int l = i; l < j; ++l) acc = csub(acc, cmul(M[mrow + l], A[(long long)l * L + j]));
-      M[mrow + j] = cscale(acc, inv);
+    const R rjj = A[(long long)j * L + j].x;
+    for (int i = tid; i < j; i += nt) {
+      Cx<R> acc = mk<R>(0, 0);
+      for (int l = i; l < j; ++l)
+        acc = csub(acc, cmul(A[(long long)i * L + l], A[(long long)l * L + j]));
+      tmp[i] = acc;
     }
     __syncthreads();
+    const R inv = (R)1 / rjj;
+    for (int i = tid; i < j; i += nt) A[(long long)i * L + j] = cscale(tmp[i], inv);
+    if (tid == 0) A[(long long)j * L + j] = mk<R>(inv, 0);
+    __syncthreads();
+  }
+  for (long long e = tid; e < (long long)k * k; e += nt) {
+    const int i = (int)(e / k), j = (int)(e % k);
+    if (i <= j) M[(long long)perm[i] * L + j] = A[(long long)i * L + j];
   }
 }
 

@@ -484,6 +484,8 @@ struct Eng {
       cudaFuncSetAttribute(qr_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c);
       cudaFuncSetAttribute(jacobi_svd_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)c);
+      cudaFuncSetAttribute(chol_piv_inv_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)c);
       return c;
     }();
     return cap;
@@ -522,17 +524,20 @@ struct Eng {
     Cx<R>* G = alloc((long long)L * L);
     QREQ(m < (1ll << 31), "orth_factor: too many rows");
     gemm(L, L, (int)m, mref(P, 1, L, 0, 0, 0, 1), mref(P, L, 1), G, L, 1, 0, 0, 0, 1, 1, 1);
-    Cx<R>* A = alloc((long long)L * L);
+    const size_t bytes = ((size_t)L * L + L) * sizeof(Cx<R>);
+    const bool sm = bytes <= smem_cap();
+    Cx<R>* A = sm ? nullptr : alloc((long long)L * L + L);
     Cx<R>* M = alloc((long long)L * L);
     int* perm = (int*)ln->arena->alloc(sizeof(int) * L);
     {
       const double l3 = (double)L * L * L;
       ProfScope ps(c, st(), 1, 8.0 * l3 / 3.0 * 2.0);
-      chol_piv_inv_kernel<R><<<1, 1024, 0, st()>>>(L, G, A, M, perm, tau, err);
+      chol_piv_inv_kernel<R><<<1, 1024, sm ? bytes : 0, st()>>>(L, G, A, M, perm, tau, err,
+                                                                sm ? 1 : 0);
       post("chol_piv_inv_kernel", __LINE__);
     }
     release(G);
-    release(A);
+    if (A) release(A);
     ln->arena->release(perm);
     return M;
   }
@@ -1709,16 +1714,16 @@ void green_coeffs(double lam0, double mu0, double* C) {
 }
 
 // Green operator from its separable form: the TT of the 15 monomial fields
-// (TT-SVD at eps / 10, cached per grid: it does not depend on the reference
-// medium), then its first core mixed by the 36 x 15 coefficient matrix of
-// (lam0, mu0). C has condition number ~7, so the operator's relative error
-// stays below ~eps.
+// (TT-SVD at eps, cached per grid: it does not depend on the reference
+// medium), then its first core mixed by the 36 x 15 coefficient matrix C of
+// (lam0, mu0). The operator's relative error is at most cond(C) eps (C's
+// condition number is ~7 for the media of the workloads).
 qtt_op* build_gamma(qtt_ctx* c, int n, double lam0, double mu0, int scheme, double eps, int rmax) {
   QREQ(scheme == 0, "only the Direct scheme (0) is implemented");
   QREQ(n >= 1 && n <= 9, "gamma: n must be in 1..9");
   QREQ(mu0 > 0 && lam0 + 2 * mu0 > 0, "gamma: reference medium not positive definite");
   Eng<double> e(c);
-  const double eps_m = eps / 10.0;
+  const double eps_m = eps;
   const auto key = std::make_tuple(n, eps_m, rmax);
   auto it = c->green_mono_cache.find(key);
   if (it == c->green_mono_cache.end()) {
@@ -1829,17 +1834,40 @@ int solve_impl(qtt_ctx* c, const qtt_op* dC, const qtt_op* S, const qtt_op* Sh, 
   const int ell = p->rmax + p->oversample;
   int cap = 0, maxr = 1, it = 0, status = QTT_OK;
   double rel = 0;
+  // With QTT_CHECK_FINITE=1 in the environment every intermediate TT of
+  // the iteration is checked (its FP64 norm) and the first non-finite one is
+  // reported by step and iteration.
+  static const bool check_finite = [] {
+    const char* v = getenv("QTT_CHECK_FINITE");
+    return v && v[0] == '1';
+  }();
+  auto chk = [&](qtt_tt* t, const char* step) {
+    if (!check_finite) return;
+    double a, b;
+    tt_dot<R>(e, t, t, &a, &b);
+    if (!std::isfinite(a))
+      throw QttError(QTT_ENAN, std::string("ls_solve: non-finite after ") + step + " in iteration " +
+                                   std::to_string(it));
+  };
   for (it = 1; it <= p->max_iter; ++it) {
     const int t0id = apply_base + 4 * (it - 1);
     qtt_tt* tau = apply_sketched<R>(e, dC, x, ell, t0id);
+    chk(tau, "(C - C0) product");
     cap |= round_right_to_left<R>(e, tau, p->eps_tt, p->rmax);
+    chk(tau, "rounding of (C - C0) product");
     qtt_tt* tauh = apply_sketched<R>(e, S, tau, ell, t0id + 1);
+    chk(tauh, "SFFT product");
     cap |= round_right_to_left<R>(e, tauh, p->eps_tt, p->rmax);
+    chk(tauh, "rounding of SFFT product");
     qtt_tt* epsh = apply_sketched<R>(e, G, tauh, ell, t0id + 2);
+    chk(epsh, "Green product");
     cap |= round_right_to_left<R>(e, epsh, p->eps_tt, p->rmax);
+    chk(epsh, "rounding of Green product");
     qtt_tt* yv = apply_sketched<R>(e, Sh, epsh, ell, t0id + 3);
+    chk(yv, "inverse SFFT product");
     qtt_tt* xn = tt_add<R>(e, Ett, yv, 1.0, -1.0);
     cap |= round_full<R>(e, xn, p->eps_tt, p->rmax);
+    chk(xn, "rounding of the new strain");
     maxr = std::max({maxr, max_rank<R>(tau), max_rank<R>(tauh), max_rank<R>(epsh), max_rank<R>(xn)});
     // ||xn - x||^2 = ||xn||^2 + ||x||^2 - 2 Re <xn, x>
     double a2r, a2i, b2r, b2i, abr, abi;
