@@ -472,7 +472,10 @@ __global__ void jacobi_svd_kernel(int m, int n, Cx<R>* A, Cx<R>* V, double* sigm
     const Cx<R>* a = A + (long long)j * m;
     for (int i = lane; i < m; i += 32) s2 += cabs2(a[i]);
     s2 = warp_sum(s2);
-    if (lane == 0) snorm[j] = sqrt(s2);
+    // a column at the rounding-noise floor (never rotated, see negl) is not
+    // orthogonal to the others: its singular value is zero to working
+    // precision, so the truncation drops it
+    if (lane == 0) snorm[j] = s2 <= negl ? (R)0 : sqrt(s2);
   }
   __syncthreads();
   // rank of each column in descending order (ties by index); a NaN norm
@@ -602,7 +605,7 @@ __global__ void jacobi_grid_kernel(int m, int n, Cx<R>* A, Cx<R>* V, R* snorm, i
     const Cx<R>* a = A + (long long)j * m;
     for (int i = lane; i < m; i += 32) s2 += cabs2(a[i]);
     s2 = warp_sum(s2);
-    if (lane == 0) snorm[j] = sqrt(s2);
+    if (lane == 0) snorm[j] = s2 <= negl ? (R)0 : sqrt(s2);  // noise-floor column: zero
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) *sweeps_out = sweep;
 }

@@ -145,6 +145,7 @@ struct qtt_ctx {
   std::atomic<uint64_t> launches{0};
   std::mutex prof_mu;
   int concurrent_loads = 1;  // load cases of ls_solve_ceff run side by side
+  std::atomic<int> active_lanes{1};  // lanes of the running solve queue (split-K sizing)
   double gram_threshold = 2e9;     // TT-SVD: 8 P c min(P, c) above this takes the Gram path
   double jacobi_tol_scale = 1.0;   // Jacobi stop: |a_p^H a_q| <= scale sqrt(m) eps |a_p||a_q|
   int jacobi_max_sweeps32 = 40;    // sweep cap in FP32 mode
@@ -380,8 +381,10 @@ struct Eng {
       // CTAs to cover the SMs, partial products summed by a second kernel in
       // a fixed order (deterministic, unlike atomics).
       const long long tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN) * (long long)nb1 * nb2 * nb3;
-      if (g.ksplit == 1 && tiles < kSMs && K >= 256) {
-        long long ks = std::min<long long>((2 * kSMs + tiles - 1) / tiles, K / 128);
+      // with several lanes running, each GEMM aims at its share of the SMs
+      const long long target = std::max<long long>(16, 2 * kSMs / std::max(1, c->active_lanes.load()));
+      if (g.ksplit == 1 && tiles < target / 2 && K >= 256) {
+        long long ks = std::min<long long>((target + tiles - 1) / tiles, K / 128);
         ks = std::min<long long>(ks, 32);
         const long long nbat = (long long)nb1 * nb2 * nb3;
         if (ks >= 2 && ks * nbat <= 65535 && ks * nbat * M * N <= (16ll << 20)) {
@@ -2403,6 +2406,11 @@ void run_jobs(qtt_ctx* ctx, std::vector<SolveJob>& jobs, const qtt_solve_params*
     lanes[0] = ctx->lane0;
   }
   std::atomic<int> next{0};
+  struct LaneCount {
+    qtt_ctx* c;
+    LaneCount(qtt_ctx* ctx, int nl) : c(ctx) { c->active_lanes = nl; }
+    ~LaneCount() { c->active_lanes = 1; }
+  } lane_count(ctx, nl);
   auto worker = [&](int lane_id) {
     cudaSetDevice(ctx->device);
     for (int j = next++; j < nj; j = next++) {
