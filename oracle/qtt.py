@@ -363,9 +363,12 @@ def tto_apply_sketched(op, x, ell: int, seed: int, apply_id: int):
             break
         Z = np.einsum("robt,btp->rop", T, psi[k + 1]).reshape(r * do, -1)
         Q, Rz = np.linalg.qr(Z)
-        # a dropped sketch direction is an exactly zero column of Z; the QR's
-        # direction for it is arbitrary and is removed
-        Q[:, np.abs(np.diag(Rz)) == 0] = 0
+        # a dropped sketch direction is an exactly zero column of Z, and a
+        # residual column at the rounding-noise floor (|R_jj|^2 <= eps^2
+        # ||Z||_F^2) carries nothing either; the QR's direction for such a
+        # column is arbitrary and is removed
+        dead = np.abs(np.diag(Rz)) ** 2 <= (2.220446049250313e-16 ** 2) * np.vdot(Z, Z).real
+        Q[:, dead] = 0
         out.append(Q.reshape(r, do, Q.shape[1]))
         C = np.einsum("mr,rbt->mbt", Q.conj().T, T.reshape(r * do, a1, s1))
     return out

@@ -233,6 +233,7 @@ __global__ void qr_kernel(int m, int n, const Cx<R>* __restrict__ A, long long r
   extern __shared__ __align__(16) unsigned char qr_dyn[];
   Cx<R>* W = use_smem ? (Cx<R>*)qr_dyn : Wg;
   __shared__ R red[32];
+  __shared__ double redd[32];
   __shared__ Cx<R> s_v0;
   __shared__ R s_h;
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -251,28 +252,45 @@ __global__ void qr_kernel(int m, int n, const Cx<R>* __restrict__ A, long long r
     W[e] = v;
   }
   __syncthreads();
+  // squared norms in FP64: a column at the rounding-noise floor of the matrix
+  // (|x|^2 <= eps^2 ||A||_F^2) is treated as zero (R_jj = 0, no reflector);
+  // reflecting it would divide by a norm that can underflow single precision
+  double f2 = 0;
+  for (long long e = tid; e < (long long)m * n; e += nt) f2 += (double)cabs2(W[e]);
+  f2 = block_sum(f2, redd);
+  const double eps_r = sizeof(R) == 8 ? 2.220446049250313e-16 : 1.1920928955078125e-7;
+  const double negl = eps_r * eps_r * f2;
   const int k = min(m, n);
   for (int j = 0; j < k; ++j) {
     Cx<R>* col = W + (long long)j * m;
-    R s2 = 0;
-    for (int i = j + tid; i < m; i += nt) s2 += cabs2(col[i]);
-    s2 = block_sum(s2, red);
+    double s2d = 0;
+    for (int i = j + tid; i < m; i += nt) s2d += (double)col[i].x * col[i].x + (double)col[i].y * col[i].y;
+    s2d = block_sum(s2d, redd);
+    const R s2 = (R)s2d;
     if (tid == 0) {
       const Cx<R> a = col[j];
       const R s = sqrt(s2);
-      if (s == (R)0) {
+      if (!(s2d > negl) || s == (R)0) {
         s_h = 0;
         s_v0 = mk<R>(0, 0);
+        col[j] = mk<R>(0, 0);
       } else {
         // hypot keeps |phase| = 1 when |a| is tiny (no underflow of |a|^2)
         const R aa = hypot(a.x, a.y);
         const Cx<R> ph = aa > (R)0 ? mk<R>(a.x / aa, a.y / aa) : mk<R>(1, 0);
         const Cx<R> beta = mk<R>(-ph.x * s, -ph.y * s);
         const Cx<R> v0 = csub(a, beta);
-        const R vtv = s2 - aa * aa + cabs2(v0);
-        s_h = (R)2 / vtv;
-        s_v0 = v0;
-        col[j] = beta;
+        const double vtv = s2d - (double)aa * aa + (double)v0.x * v0.x + (double)v0.y * v0.y;
+        const double hd = 2.0 / vtv;
+        if (!(hd < (sizeof(R) == 8 ? 1e300 : 1e30))) {  // a matrix at the underflow edge
+          s_h = 0;
+          s_v0 = mk<R>(0, 0);
+          col[j] = mk<R>(0, 0);
+        } else {
+          s_h = (R)hd;
+          s_v0 = v0;
+          col[j] = beta;
+        }
       }
       hbuf[j] = s_h;
       vhead[j] = s_v0;
@@ -1046,7 +1064,11 @@ chol_piv_inv_kernel(int L, const Cx<R>* __restrict__ G, Cx<R>* Wg, Cx<R>* M, int
   }
   for (long long e = tid; e < (long long)k * k; e += nt) {
     const int i = (int)(e / k), j = (int)(e % k);
-    if (i <= j) M[(long long)perm[i] * L + j] = A[(long long)i * L + j];
+    if (i <= j) {
+      const Cx<R> v = A[(long long)i * L + j];
+      if (!isfinite(v.x) || !isfinite(v.y)) atomicExch(err, 2);
+      M[(long long)perm[i] * L + j] = v;
+    }
   }
 }
 

@@ -816,6 +816,16 @@ long long prod_dims(const int* d, int a, int b) {  // prod d[a..b-1], saturating
   return p;
 }
 
+// QTT_CHECK_FINITE=1 in the environment: intermediate results are checked
+// for non-finite values and the first one is reported by where it arose.
+bool debug_finite() {
+  static const bool on = [] {
+    const char* v = getenv("QTT_CHECK_FINITE");
+    return v && v[0] == '1';
+  }();
+  return on;
+}
+
 // y = A x by successive randomized compression (see the oracle's
 // tto_apply_sketched for the statement): right-to-left random sketches Psi,
 // then left-to-right QR of the sketched carries. Output left-orthogonal.
@@ -908,6 +918,13 @@ qtt_tt* apply_sketched(Eng<R>& e, const qtt_op* A, const qtt_tt* x, int ell, int
     }
     psi[k] = Pk;
     Mk[k] = e.orth_factor(Pk, (long long)S0 * A0, L0, drop_tau, oerr);
+    if (debug_finite()) {
+      const double a = e.norm2(Pk, (long long)S0 * A0 * L0), b = e.norm2(Mk[k], (long long)L0 * L0);
+      if (!std::isfinite(a) || !std::isfinite(b))
+        throw QttError(QTT_ENAN, "sketched product: non-finite sketch at core " + std::to_string(k) +
+                                     " (|Psi|^2 " + std::to_string(a) + ", |M|^2 " +
+                                     std::to_string(b) + ")");
+    }
   }
   // ---- left-to-right compression
   qtt_tt* y = new_tt(e.c, e.ln->arena, L, A->dout);
@@ -971,7 +988,12 @@ qtt_tt* apply_sketched(Eng<R>& e, const qtt_op* A, const qtt_tt* x, int ell, int
     const int kq = std::min(mz, L1);
     Cx<R>* Q = e.alloc((long long)mz * kq);
     Cx<R>* Rm = e.alloc((long long)kq * L1);
+    if (debug_finite() && !std::isfinite(e.norm2(Z, (long long)mz * L1)))
+      throw QttError(QTT_ENAN, "sketched product: non-finite compression matrix at core " +
+                                   std::to_string(k));
     e.qr(mz, L1, Z, L1, 1, 0, Q, Rm);
+    if (debug_finite() && !std::isfinite(e.norm2(Q, (long long)mz * kq)))
+      throw QttError(QTT_ENAN, "sketched product: non-finite QR factor at core " + std::to_string(k));
     // a dropped sketch direction gives an exactly zero column of Z: its
     // reflector direction is arbitrary, so it is removed from the output
     zero_dead_cols_kernel<R><<<grid1d((long long)mz * kq), 256, 0, e.st()>>>(Q, mz, kq, Rm, kq);
@@ -1007,7 +1029,8 @@ qtt_tt* apply_sketched(Eng<R>& e, const qtt_op* A, const qtt_tt* x, int ell, int
   e.ln->arena->release(oerr);
   if (herr) {
     free_tt(y);
-    throw QttError(QTT_ENAN, "sketched product: non-finite sketch environment");
+    throw QttError(QTT_ENAN, herr == 2 ? "sketched product: non-finite orthonormalising factor"
+                                       : "sketched product: non-finite sketch environment");
   }
   return y;
 }
@@ -1840,10 +1863,7 @@ int solve_impl(qtt_ctx* c, const qtt_op* dC, const qtt_op* S, const qtt_op* Sh, 
   // With QTT_CHECK_FINITE=1 in the environment every intermediate TT of
   // the iteration is checked (its FP64 norm) and the first non-finite one is
   // reported by step and iteration.
-  static const bool check_finite = [] {
-    const char* v = getenv("QTT_CHECK_FINITE");
-    return v && v[0] == '1';
-  }();
+  const bool check_finite = debug_finite();
   auto chk = [&](qtt_tt* t, const char* step) {
     if (!check_finite) return;
     double a, b;

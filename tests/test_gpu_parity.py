@@ -290,3 +290,45 @@ def test_concurrent_loads_match_sequential(Q, precision):
     tol = 1e-12 if precision == "fp64" else 1e-5
     assert np.abs(C6 - C1).max() <= tol * np.abs(C1).max()
     ctx.close()
+
+
+def test_fp32_products_of_rank_one_fields(Q):
+    """FP32 mode with a truncation threshold below single precision: the
+    products of rank-1 strain fields keep only real directions (columns at
+    the rounding-noise floor of the SVD count as zero). Before that, noise
+    directions were kept with non-orthogonal vectors and the SFFT product of
+    a unit strain came out wrong by a factor ~3."""
+    n = 3
+    lam0 = dense.reference_lame((1.0, 20.0), (0.3, 0.3))
+    ops = {"sfft": oq.sfft_operator(n, 1e-12), "gamma": oq.gamma_qtt(n, *lam0, 1e-8)}
+    ctx = Q.Context(0, Q.QTT_FP32, 1 << 30, seed=SEED)
+    try:
+        for name, op in ops.items():
+            cores, diag = to_lib_op(op)
+            top = ctx.op(cores, diag)
+            for k in (0, 3):
+                x = oq.e_tt(n, np.eye(6)[k])
+                y, rc = Q.qtt_op_apply(ctx, top, ctx.tt(x), 1e-12, 32, 16, apply_id=3)
+                ref = oq.tto_full(op) @ oq.tt_full(x).reshape(-1)
+                assert rel(oq.tt_full(y.cores()).reshape(-1), ref) < 1e-5, (name, k)
+    finally:
+        ctx.close()
+
+
+def test_fp32_laminate_solve(Q):
+    """A laminate (broadcast x1, x2) is solved exactly in two iterations in
+    exact arithmetic; FP32 mode at eps_tt 1e-8 (below single precision)
+    converges the same way and matches the dense oracle."""
+    n = 3
+    phb = synth.laminate(n, 2)
+    E, nu = (1.0, 20.0), (0.3, 0.3)
+    ctx = Q.Context(0, Q.QTT_FP32, 1 << 30, seed=SEED)
+    try:
+        dC = Q.qtt_from_phase_field(ctx, phb, n, E, nu, None, 1e-8)
+        C, infos, rc = Q.ls_solve_ceff(ctx, dC, Q.solve_params(1e-5, 30, 1e-8, 32), loads=[0, 1, 3])
+        Cd, imag, its = dense.ceff(synth.broadcast_dense(phb, n), E, nu, tol=1e-10, loads=[0, 1, 3])
+        assert all(i["iters"] <= 4 for i in infos)
+        for k in (0, 1, 3):
+            assert np.abs(C[:, k] - Cd[:, k]).max() < 1e-5 * np.abs(Cd).max()
+    finally:
+        ctx.close()
