@@ -58,6 +58,8 @@ extern "C" {
 
 #define QTT_FP64 0
 #define QTT_FP32 1
+#define QTT_CONTRACT_SIMT 0
+#define QTT_CONTRACT_TF32X3 1
 
 #define QTT_MAX_CORES 64
 
@@ -265,6 +267,15 @@ int qtt_ctx_set_jacobi(qtt_ctx_t ctx, double tol_scale, int max_sweeps_fp32);
  * ones take an SVD of M itself (QR + one-sided Jacobi). 0 sends every
  * unfolding through the Gram path. Returns QTT_EINVAL for a negative value. */
 int qtt_ctx_set_tt_svd(qtt_ctx_t ctx, double gram_threshold);
+/* Contraction precision of an FP32 context (the split-precision pattern of
+ * the method's mixed mode; the paper itself states no precision):
+ * QTT_CONTRACT_SIMT (default) runs every core contraction as FP32 SIMT
+ * GEMMs; QTT_CONTRACT_TF32X3 runs them on the tensor cores with TF32 inputs
+ * split as x = hi + lo and products hi*hi + hi*lo + lo*hi accumulated in FP32
+ * (FP32-level accuracy). Factorisations, norms and the C_eff average are
+ * unaffected. Returns QTT_EINVAL for an unknown mode or TF32X3 on an FP64
+ * context. */
+int qtt_ctx_set_contraction(qtt_ctx_t ctx, int mode);
 /* C_eff and its derivatives with respect to phase parameters (E or nu of a
  * phase). The Direct-scheme LS operator (with the Nyquist symmetrisation of
  * App. A) is self-adjoint, so the adjoint solution of load l equals its

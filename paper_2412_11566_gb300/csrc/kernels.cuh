@@ -176,6 +176,162 @@ gemm_kernel(GemmArgs g) {
   }
 }
 
+// ------------------------------------------------------------------ split-TF32 tensor-core GEMM
+// Complex FP32 GEMM on the tensor cores (mma.sync m16n8k8, TF32 inputs, FP32
+// accumulation) with split precision: each real operand x = hi + lo with
+// hi = tf32(x), lo = tf32(x - hi), and each real product taken as
+// hi*hi + hi*lo + lo*hi (the dropped lo*lo term is ~2^-22 relative, the
+// level of FP32 rounding). The complex product is four real products:
+// re = Ar Br - Ai Bi, im = Ar Bi + Ai Br, i.e. 12 MMAs per k-step and tile.
+// Same arguments, batching, split-K and epilogue as gemm_kernel<float>.
+// Tile 64 x 64 x 8, four warps of 32 x 32 outputs each.
+__device__ __forceinline__ uint32_t f32_to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
+  hi = f32_to_tf32(x);
+  lo = f32_to_tf32(x - __uint_as_float(hi));
+}
+
+__device__ __forceinline__ void mma_tf32(float* d, const uint32_t* a, const uint32_t* b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 "
+      "{%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__global__ void __launch_bounds__(128) gemm_tf32x3_kernel(GemmArgs g) {
+  constexpr int BM = 64, BN = 64, BK = 8;
+  __shared__ float Ar[BK][BM + 4], Ai[BK][BM + 4];
+  __shared__ float Br[BK][BN + 4], Bi[BK][BN + 4];
+  int z = blockIdx.z;
+  const int ks = z % g.ksplit;
+  z /= g.ksplit;
+  const int b3 = z % g.nb3;
+  z /= g.nb3;
+  const int b2 = z % g.nb2;
+  const int b1 = z / g.nb2;
+  const Cx<float>* A = (const Cx<float>*)g.A + b1 * g.a_b1 + b2 * g.a_b2 + b3 * g.a_b3;
+  const Cx<float>* B = (const Cx<float>*)g.B + b1 * g.b_b1 + b2 * g.b_b2 + b3 * g.b_b3;
+  Cx<float>* C = (Cx<float>*)g.C + b1 * g.c_b1 + b2 * g.c_b2 + b3 * g.c_b3;
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  const int kchunk = ((g.K + g.ksplit - 1) / g.ksplit + BK - 1) / BK * BK;
+  const int kbeg = ks * kchunk;
+  const int kend = min(g.K, kbeg + kchunk);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int gq = lane >> 2, tq = lane & 3;              // group, thread in group
+  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;  // warp tile origin
+  float accr[2][4][4], acci[2][4][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) accr[i][j][q] = acci[i][j][q] = 0.f;
+  const bool a_mfast = (g.a_rs == 1);
+  const bool b_nfast = (g.b_cs == 1);
+  for (int k0 = kbeg; k0 < kend; k0 += BK) {
+    for (int e = tid; e < BM * BK; e += 128) {
+      int mm, kk;
+      if (a_mfast) { mm = e % BM; kk = e / BM; } else { kk = e % BK; mm = e / BK; }
+      const int gm = m0 + mm, gk = k0 + kk;
+      Cx<float> v = mk<float>(0, 0);
+      if (gm < g.M && gk < kend) {
+        v = A[(long long)gm * g.a_rs + (long long)gk * g.a_cs];
+        if (g.conjA) v.y = -v.y;
+      }
+      Ar[kk][mm] = v.x;
+      Ai[kk][mm] = v.y;
+    }
+    for (int e = tid; e < BK * BN; e += 128) {
+      int kk, nn;
+      if (b_nfast) { nn = e % BN; kk = e / BN; } else { kk = e % BK; nn = e / BK; }
+      const int gk = k0 + kk, gn = n0 + nn;
+      Cx<float> v = mk<float>(0, 0);
+      if (gk < kend && gn < g.N) {
+        v = B[(long long)gk * g.b_rs + (long long)gn * g.b_cs];
+        if (g.conjB) v.y = -v.y;
+      }
+      Br[kk][nn] = v.x;
+      Bi[kk][nn] = v.y;
+    }
+    __syncthreads();
+    // A fragments (16 x 8, row-major): a0 (g, t), a1 (g+8, t), a2 (g, t+4), a3 (g+8, t+4)
+    uint32_t arh[2][4], arl[2][4], aih[2][4], ail[2][4], anh[2][4], anl[2][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int r = wm + i * 16 + gq;
+      const float xr[4] = {Ar[tq][r], Ar[tq][r + 8], Ar[tq + 4][r], Ar[tq + 4][r + 8]};
+      const float xi[4] = {Ai[tq][r], Ai[tq][r + 8], Ai[tq + 4][r], Ai[tq + 4][r + 8]};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        split_tf32(xr[q], arh[i][q], arl[i][q]);
+        split_tf32(xi[q], aih[i][q], ail[i][q]);
+        split_tf32(-xi[q], anh[i][q], anl[i][q]);
+      }
+    }
+    // B fragments (8 x 8, k x n): b0 (k = t, n = g), b1 (k = t+4, n = g)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = wn + j * 8 + gq;
+      uint32_t brh[2], brl[2], bih[2], bil[2];
+      split_tf32(Br[tq][c], brh[0], brl[0]);
+      split_tf32(Br[tq + 4][c], brh[1], brl[1]);
+      split_tf32(Bi[tq][c], bih[0], bil[0]);
+      split_tf32(Bi[tq + 4][c], bih[1], bil[1]);
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        // re += Ar Br - Ai Bi
+        mma_tf32(accr[i][j], arh[i], brh);
+        mma_tf32(accr[i][j], arh[i], brl);
+        mma_tf32(accr[i][j], arl[i], brh);
+        mma_tf32(accr[i][j], anh[i], bih);
+        mma_tf32(accr[i][j], anh[i], bil);
+        mma_tf32(accr[i][j], anl[i], bih);
+        // im += Ar Bi + Ai Br
+        mma_tf32(acci[i][j], arh[i], bih);
+        mma_tf32(acci[i][j], arh[i], bil);
+        mma_tf32(acci[i][j], arl[i], bih);
+        mma_tf32(acci[i][j], aih[i], brh);
+        mma_tf32(acci[i][j], aih[i], brl);
+        mma_tf32(acci[i][j], ail[i], brh);
+      }
+    }
+    __syncthreads();
+  }
+  const Cx<float> alpha = mk<float>((float)g.alpha_re, (float)g.alpha_im);
+  const Cx<float> beta = mk<float>((float)g.beta_re, (float)g.beta_im);
+  const bool use_beta = (g.beta_re != 0.0 || g.beta_im != 0.0);
+  // accumulator (16 x 8): c0 (g, 2t), c1 (g, 2t+1), c2 (g+8, 2t), c3 (g+8, 2t+1)
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int gm = m0 + wm + i * 16 + gq + (q >= 2 ? 8 : 0);
+        const int gn = n0 + wn + j * 8 + 2 * tq + (q & 1);
+        if (gm >= g.M || gn >= g.N) continue;
+        Cx<float>* p = C + (long long)gm * g.c_rs + (long long)gn * g.c_cs;
+        Cx<float> v = cmul(alpha, mk<float>(accr[i][j][q], acci[i][j][q]));
+        if (g.part) {
+          const long long nbat = (long long)g.nb1 * g.nb2 * g.nb3;
+          const long long bidx = ((long long)b1 * g.nb2 + b2) * g.nb3 + b3;
+          ((Cx<float>*)g.part)[(((long long)ks * nbat + bidx) * g.M + gm) * g.N + gn] = v;
+        } else if (g.ksplit > 1) {
+          atomicAdd(&p->x, v.x);
+          atomicAdd(&p->y, v.y);
+        } else {
+          if (use_beta) v = cadd(v, cmul(beta, *p));
+          *p = v;
+        }
+      }
+}
+
 // C = sum over the ks splits of part (fixed order) + beta C, for the batch
 // and strides of the GEMM that wrote part (layout in GemmArgs::part).
 template <typename R>
@@ -233,7 +389,6 @@ __global__ void qr_kernel(int m, int n, const Cx<R>* __restrict__ A, long long r
   extern __shared__ __align__(16) unsigned char qr_dyn[];
   Cx<R>* W = use_smem ? (Cx<R>*)qr_dyn : Wg;
   __shared__ R red[32];
-  __shared__ double redd[32];
   __shared__ Cx<R> s_v0;
   __shared__ R s_h;
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -252,21 +407,21 @@ __global__ void qr_kernel(int m, int n, const Cx<R>* __restrict__ A, long long r
     W[e] = v;
   }
   __syncthreads();
-  // squared norms in FP64: a column at the rounding-noise floor of the matrix
-  // (|x|^2 <= eps^2 ||A||_F^2) is treated as zero (R_jj = 0, no reflector);
-  // reflecting it would divide by a norm that can underflow single precision
-  double f2 = 0;
-  for (long long e = tid; e < (long long)m * n; e += nt) f2 += (double)cabs2(W[e]);
-  f2 = block_sum(f2, redd);
+  // a column at the rounding-noise floor of the matrix (|x|^2 <= eps^2
+  // ||A||_F^2) is treated as zero (R_jj = 0, no reflector): reflecting it
+  // would divide by a norm that can underflow single precision
+  R f2 = 0;
+  for (long long e = tid; e < (long long)m * n; e += nt) f2 += cabs2(W[e]);
+  f2 = block_sum(f2, red);
   const double eps_r = sizeof(R) == 8 ? 2.220446049250313e-16 : 1.1920928955078125e-7;
-  const double negl = eps_r * eps_r * f2;
+  const double negl = eps_r * eps_r * (double)f2;
   const int k = min(m, n);
   for (int j = 0; j < k; ++j) {
     Cx<R>* col = W + (long long)j * m;
-    double s2d = 0;
-    for (int i = j + tid; i < m; i += nt) s2d += (double)col[i].x * col[i].x + (double)col[i].y * col[i].y;
-    s2d = block_sum(s2d, redd);
-    const R s2 = (R)s2d;
+    R s2 = 0;
+    for (int i = j + tid; i < m; i += nt) s2 += cabs2(col[i]);
+    s2 = block_sum(s2, red);
+    const double s2d = (double)s2;
     if (tid == 0) {
       const Cx<R> a = col[j];
       const R s = sqrt(s2);

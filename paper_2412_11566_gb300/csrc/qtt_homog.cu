@@ -146,6 +146,7 @@ struct qtt_ctx {
   std::mutex prof_mu;
   int concurrent_loads = 1;  // load cases of ls_solve_ceff run side by side
   std::atomic<int> active_lanes{1};  // lanes of the running solve queue (split-K sizing)
+  int contraction = QTT_CONTRACT_SIMT;  // FP32 mode: SIMT or split-TF32 tensor-core GEMMs
   double gram_threshold = 2e9;     // TT-SVD: 8 P c min(P, c) above this takes the Gram path
   double jacobi_tol_scale = 1.0;   // Jacobi stop: |a_p^H a_q| <= scale sqrt(m) eps |a_p||a_q|
   int jacobi_max_sweeps32 = 40;    // sweep cap in FP32 mode
@@ -311,6 +312,20 @@ struct Eng {
   }
   void release(void* p) { ln->arena->release(p); }
 
+  // One GEMM launch: SIMT FP32/FP64 tiles, or in FP32 mode with the
+  // split-TF32 contraction setting the tensor-core kernel (same tiling and
+  // arguments).
+  void launch_gemm(dim3 grid, const GemmArgs& a) {
+    if (sizeof(R) == 4 && c->contraction == QTT_CONTRACT_TF32X3) {
+      gemm_tf32x3_kernel<<<grid, dim3(128), 0, st()>>>(a);
+      post("gemm_tf32x3_kernel", __LINE__);
+    } else {
+      constexpr int BK = sizeof(R) == 8 ? 8 : 16;
+      gemm_kernel<R, 64, 64, BK, 4, 4><<<grid, dim3(256), 0, st()>>>(a);
+      post("gemm_kernel", __LINE__);
+    }
+  }
+
   // C = alpha op(A) op(B) + beta C over a (nb1, nb2, nb3) batch.
   void gemm(int M, int N, int K, MatRef A, MatRef B, void* C, long long c_rs, long long c_cs,
             long long c_b1, long long c_b2, long long c_b3, int nb1, int nb2, int nb3,
@@ -374,7 +389,7 @@ struct Eng {
     check_span(A.p, span(M, A.rs, K, A.cs, nb1, A.b1, nb2, A.b2, nb3, A.b3), "gemm A");
     check_span(B.p, span(K, B.rs, N, B.cs, nb1, B.b1, nb2, B.b2, nb3, B.b3), "gemm B");
     check_span(C, span(M, c_rs, N, c_cs, nb1, c_b1, nb2, c_b2, nb3, c_b3), "gemm C");
-    constexpr int BM = 64, BN = 64, BK = sizeof(R) == 8 ? 8 : 16;
+    constexpr int BM = 64, BN = 64;
     {
       // Few output tiles and a long K (the sketched carry T Psi: M = 2 r,
       // N = r + oversampling, K = r x operator rank): split K over enough
@@ -396,8 +411,7 @@ struct Eng {
                           (unsigned)(nbat * ks));
           {
             ProfScope ps(c, st(), 0, 8.0 * M * N * (double)K * nbat);
-            gemm_kernel<R, BM, BN, BK, 4, 4><<<grid, dim3(256), 0, st()>>>(g);
-            post("gemm_kernel", __LINE__);
+            launch_gemm(grid, g);
             splitk_reduce_kernel<R><<<grid1d(nbat * M * N), 256, 0, st()>>>(
                 part, (int)ks, nbat, M, N, nb2, nb3, (Cx<R>*)C, c_rs, c_cs, c_b1, c_b2, c_b3,
                 beta.re, beta.im);
@@ -441,8 +455,7 @@ struct Eng {
       }
       const dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)(nb * per_b1));
       ProfScope ps(c, st(), 0, 8.0 * M * N * (double)K * nb * nb2 * nb3);
-      gemm_kernel<R, BM, BN, BK, 4, 4><<<grid, block, 0, st()>>>(h);
-      post("gemm_kernel", __LINE__);
+      launch_gemm(grid, h);
     }
   }
 
@@ -2679,6 +2692,13 @@ int qtt_ctx_set_jacobi(qtt_ctx_t ctx, double tol_scale, int max_sweeps_fp32) {
   if (!ctx || !(tol_scale > 0) || max_sweeps_fp32 < 1 || max_sweeps_fp32 > 200) return QTT_EINVAL;
   ctx->jacobi_tol_scale = tol_scale;
   ctx->jacobi_max_sweeps32 = max_sweeps_fp32;
+  return QTT_OK;
+}
+
+int qtt_ctx_set_contraction(qtt_ctx_t ctx, int mode) {
+  if (!ctx || (mode != QTT_CONTRACT_SIMT && mode != QTT_CONTRACT_TF32X3)) return QTT_EINVAL;
+  if (mode == QTT_CONTRACT_TF32X3 && ctx->prec != QTT_FP32) return QTT_EINVAL;
+  ctx->contraction = mode;
   return QTT_OK;
 }
 

@@ -29,6 +29,7 @@ lib = C.CDLL(LIB_PATH)
 QTT_OK, QTT_EINVAL, QTT_ENOMEM, QTT_ECUDA, QTT_ENAN, QTT_ETIMEOUT = 0, -1, -2, -3, -4, -5
 QTT_WRANKCAP, QTT_WNOCONV = 1, 2
 QTT_FP64, QTT_FP32 = 0, 1
+QTT_CONTRACT_SIMT, QTT_CONTRACT_TF32X3 = 0, 1
 MAXC = 64
 
 _p = C.c_void_p
@@ -98,6 +99,7 @@ _sig("ls_solve", _i, [_p, _p, _dp, C.POINTER(SolveParams), _dp, C.POINTER(SolveI
 _sig("qtt_ctx_set_concurrency", _i, [_p, _i])
 _sig("qtt_ctx_set_jacobi", _i, [_p, _d, _i])
 _sig("qtt_ctx_set_tt_svd", _i, [_p, _d])
+_sig("qtt_ctx_set_contraction", _i, [_p, _i])
 _sig("ls_solve_ceff", _i, [_p, _p, C.POINTER(SolveParams), _ip, _i, _dp, C.POINTER(SolveInfo)])
 _sig("ls_solve_batched", _i, [_p, _i, C.POINTER(_p), C.POINTER(SolveParams), _dp,
                              C.POINTER(SolveInfo)])
@@ -178,6 +180,10 @@ class Context:
 
     def set_jacobi(self, tol_scale: float = 1.0, max_sweeps_fp32: int = 40):
         self.check(lib.qtt_ctx_set_jacobi(self.h, float(tol_scale), int(max_sweeps_fp32)))
+
+    def set_contraction(self, mode: int):
+        """QTT_CONTRACT_SIMT or QTT_CONTRACT_TF32X3 (FP32 contexts)."""
+        self.check(lib.qtt_ctx_set_contraction(self.h, int(mode)))
 
     def set_tt_svd(self, gram_threshold: float = 2e9):
         self.check(lib.qtt_ctx_set_tt_svd(self.h, float(gram_threshold)))

@@ -332,3 +332,47 @@ def test_fp32_laminate_solve(Q):
             assert np.abs(C[:, k] - Cd[:, k]).max() < 1e-5 * np.abs(Cd).max()
     finally:
         ctx.close()
+
+
+def test_tf32x3_contractions_vs_oracle(Q):
+    """Split-TF32 tensor-core contractions (FP32 context, TF32X3 mode): exact
+    products (sketch rank above the product rank) of the Green and SFFT
+    operators against the dense oracle product, at FP32-level accuracy."""
+    n = 3
+    rng = np.random.default_rng(21)
+    ops = {"gamma": oq.gamma_qtt(n, 2.0, 1.0, 1e-12), "sfft": oq.sfft_operator(n)}
+    x = random_tt(rng, qtt_dims(n), [1] + [min(6 * 2 ** k, 2 ** (3 * n - k), 9) for k in range(3 * n)] + [1])
+    x, _ = oq.tt_round(x, 1e-14, 1000)
+    ctx = Q.Context(0, Q.QTT_FP32, 1 << 30, seed=SEED)
+    try:
+        ctx.set_contraction(Q.QTT_CONTRACT_TF32X3)
+        for name, op in ops.items():
+            cores, diag = to_lib_op(op)
+            y, rc = Q.qtt_op_apply(ctx, ctx.op(cores, diag), ctx.tt(x), 1e-12, 200, 16, apply_id=5)
+            exact = oq.tto_full(op) @ oq.tt_full(x).reshape(-1)
+            assert rel(oq.tt_full(y.cores()).reshape(-1), exact) < 1e-5, name
+    finally:
+        ctx.close()
+    c64 = Q.Context(0, Q.QTT_FP64, 1 << 28, seed=SEED)
+    try:
+        with pytest.raises(Q.QttError):
+            c64.set_contraction(Q.QTT_CONTRACT_TF32X3)
+    finally:
+        c64.close()
+
+
+def test_tf32x3_mode_eight_spheres_16(Q):
+    """The 16^3 8-sphere case in FP32 mode with split-TF32 tensor-core
+    contractions meets the same 1e-4 C_eff goal as the SIMT contractions."""
+    w = synth.spheres256(n=4)
+    ctx = Q.Context(0, Q.QTT_FP32, 4 << 30, seed=SEED)
+    try:
+        ctx.set_contraction(Q.QTT_CONTRACT_TF32X3)
+        dC = Q.qtt_from_phase_field(ctx, w.phase, w.n, w.E, w.nu, None, w.eps_tt, w.rmax)
+        C, infos, rc = Q.ls_solve_ceff(ctx, dC, Q.solve_params(w.tol, 80, w.eps_tt, w.rmax),
+                                       loads=[0])
+        Cd, imag, its = dense.ceff(w.phase, w.E, w.nu, tol=1e-8, loads=[0])
+        assert infos[0]["iters"] < 40 and infos[0]["residual"] < w.tol
+        assert np.abs(C[:, 0] - Cd[:, 0]).max() < 1e-4 * np.abs(Cd).max()
+    finally:
+        ctx.close()
