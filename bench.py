@@ -230,9 +230,8 @@ def main():
     ctx.set_profiling(False)
     clk = clocks.stop()
     if dist is not None:
-        t_ = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t_, op=dist.ReduceOp.MAX)
-        ms = float(t_.item())
+        from paper_2412_11566_gb300.replicas import max_over_ranks
+        ms = max_over_ranks(ms, world, device="cuda")
     solves = 6 * args.steps * world
     value = solves / (ms / 1e3)
 
