@@ -111,6 +111,22 @@ DENSE_ITERS = 37
 MAX_ITER = 40
 
 
+def ceff_error_vs_dense(C, path=os.path.join(ROOT, "tests", "golden", "spheres256_ceff_tol0.0001.json")):
+    """Max relative deviation of the computed C_eff columns from the stored
+    dense-oracle columns (written by tests/golden/make_spheres256_ceff.py),
+    per column present in the file; None when the file is absent."""
+    try:
+        ref = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    C = np.asarray(C, dtype=np.float64)
+    out = {}
+    for k, col in ref.get("columns", {}).items():
+        r = np.asarray(col["sigma_bar_re"], dtype=np.float64)
+        out[k] = float(np.abs(C[:, int(k)] - r).max() / np.abs(r).max())
+    return out or None
+
+
 def cpu_oracle_rate(w, iters_per_solve: float, sample_iters: int = 1):
     """Oracle A (dense FFT basic scheme, numpy/scipy fp64, all host cores) on
     the same geometry and load e11: a bounded sample of `sample_iters`
@@ -272,6 +288,7 @@ def main():
                        "residual_per_load": [i["residual"] for i in infos],
                        "rank_cap_hit": any(i["rank_cap_hit"] for i in infos),
                        "ceff_col0": C[:, 0].tolist(),
+                       "ceff_rel_err_vs_dense_oracle": ceff_error_vs_dense(C),
                        "preprocess_s": {"stiffness_tto": round(t_dc, 3),
                                         "first_step_incl_operator_build": round(t_first, 3)}},
             "gpu_launches": int(launches),
