@@ -105,12 +105,12 @@ def workload(seed: int):
     return synth.spheres256(n=8, seed=seed)
 
 
-# Iterations of the dense basic scheme to tol 1e-4 on this geometry (measured
-# with the oracle on the 64^3 rendering of the same seeded spheres: 37). The
+# Iterations of the dense basic scheme to tol 1e-4 on this geometry (the
+# oracle at 256^3, load e11: 35, stored in tests/golden/). The
 # QTT solves are capped at MAX_ITER: with every TT capped at rank 128 the
 # truncation error per iteration stays above the tolerance for this
 # geometry, so the stop test alone would not end them.
-DENSE_ITERS = 37
+DENSE_ITERS = 35
 MAX_ITER = 40
 
 
@@ -167,7 +167,7 @@ def run_reference(args):
                                    "load e11, tol 1e-4"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": "oracle A (dense FFT basic scheme, scipy fp64) one "
-                                       "iteration per step at 256^3, scaled by the 37 iterations "
+                                       "iteration per step at 256^3, scaled by the 35 iterations "
                                        "of a solve to tol 1e-4"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
