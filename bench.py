@@ -29,6 +29,8 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+WORKLOAD = ("spheres256: 256^3 (n=8, 25 cores), 8 spheres seed 2412, r~U(0.05,0.12)L, "
+            "E 1/20, nu 0.3/0.25, 6 loads, tol 1e-4, eps_tt 1e-6, r_max 128, sketch +16")
 METRIC = "LS solves/sec (C_eff rel.err≤1e-4) at 256^3; core-contraction TFLOP/s vs peak"
 UNIT = "LS solves/s"
 
@@ -163,8 +165,8 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "spheres256: 256^3, 8 spheres (seed 2412), contrast 20, "
-                                   "load e11, tol 1e-4"},
+            "config": {"workload": WORKLOAD, "precision": "fp64 (CPU oracle)",
+                       "sample": "one dense iteration of load e11 per step"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": "oracle A (dense FFT basic scheme, scipy fp64) one "
                                        "iteration per step at 256^3, scaled by the 35 iterations "
@@ -280,9 +282,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "c64" if prec == Q.QTT_FP32 else "c128", "data": "synthetic",
-            "config": {"workload": "spheres256: 256^3 (n=8, 25 cores), 8 spheres seed 2412, "
-                                   "r~U(0.05,0.12)L, E 1/20, nu 0.3/0.25, 6 loads, tol 1e-4, "
-                                   "eps_tt 1e-6, r_max 128, sketch +16",
+            "config": {"workload": WORKLOAD,
                        "precision": args.precision,
                        "l2": "256 MB buffer written between timed steps (flush)",
                        "iters_per_load": iters,
