@@ -130,9 +130,13 @@ void qtt_op_free(qtt_op_t op);
  * field (host uint8, C order, shape[3] each 1 or 2^n; an extent of 1 is a
  * broadcast axis) is mapped to the Voigt-matrix field
  * sum_p (C_p - C0) [phase == p] with isotropic phases (E[p], nu[p]),
- * p < nphase, and compressed by TT-SVD at eps_tt with rank cap rmax. lame0 =
- * (lambda0, mu0) of the reference medium, or NULL for the arithmetic mean of
- * the smallest and largest phase Lame parameters. The handle remembers C0. */
+ * p < nphase, and compressed by TT-SVD at eps_tt with rank cap rmax. The
+ * 36 Voigt rows of that field span at most nphase directions (columns of D =
+ * [C_p - C0]); with D = U S V^H the TT-SVD runs on the k-row field S V^H
+ * indexed by phase and U multiplies the first core, which gives the same
+ * decomposition (U has orthonormal columns). lame0 = (lambda0, mu0) of the
+ * reference medium, or NULL for the arithmetic mean of the smallest and
+ * largest phase Lame parameters. The handle remembers C0. */
 int qtt_from_phase_field(qtt_ctx_t ctx, const uint8_t* phase, const int shape[3], int n,
                          int nphase, const double* E, const double* nu,
                          const double* lame0, double eps_tt, int rmax, qtt_op_t* dC);
@@ -166,8 +170,10 @@ int qtt_gamma_operator(qtt_ctx_t ctx, int n, double lambda0, double mu0, int sch
 
 /* y = round(A x): compressed product by randomized sketching with sketch rank
  * rmax + oversample (sketch entries from the context's Philox-4x32-10 stream
- * number apply_id), then TT rounding at (eps_tt, rmax) (Sec. 3, Table 2).
- * The result is right-orthogonal. */
+ * number apply_id; each right-to-left sketch environment is replaced by an
+ * orthonormal basis of its range, from a pivoted Cholesky factor of its Gram
+ * matrix, before the next one is formed), then TT rounding at (eps_tt, rmax)
+ * (Sec. 3, Table 2). The result is right-orthogonal. */
 int qtt_op_apply(qtt_ctx_t ctx, qtt_op_t op, qtt_tt_t in, double eps_tt, int rmax,
                  int oversample, int apply_id, qtt_tt_t* out);
 /* SFFT, inverse SFFT and Green products with the context's cached operators
