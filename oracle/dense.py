@@ -94,13 +94,17 @@ def green_voigt_direct(xi: np.ndarray, lam0: float, mu0: float) -> np.ndarray:
     return out
 
 
-def green_voigt_symmetrised(xi: np.ndarray, lam0: float, mu0: float, N: int) -> np.ndarray:
-    """Gamma_V with the Nyquist symmetrisation of App. A for an even grid of N
-    points per axis: at modes with a component |xi_a| = N/2 the value is the
-    average of Gamma_V(xi) and Gamma_V at xi with those components negated (its
-    aliased partner -xi mod N, Gamma being even); elsewhere Gamma_V(xi)."""
+def green_voigt_symmetrised(xi: np.ndarray, lam0: float, mu0: float, N) -> np.ndarray:
+    """Gamma_V with the Nyquist symmetrisation of App. A: at modes with a
+    component |xi_a| = N_a/2 (the Nyquist frequency of an even axis of N_a
+    points) the value is the average of Gamma_V(xi) and Gamma_V at xi with
+    those components negated (its aliased partner -xi mod N, Gamma being
+    even); elsewhere Gamma_V(xi). N is one extent for a cubic grid or the
+    three extents (N_1, N_2, N_3); an axis of extent 1 has no Nyquist mode."""
     xi = np.asarray(xi, dtype=np.float64)
-    flip = np.where(np.abs(xi) == N / 2, -xi, xi)
+    half = np.broadcast_to(np.asarray(N, dtype=np.float64), (3,)) / 2.0
+    nyq = (np.abs(xi) == half) & (half >= 1.0)
+    flip = np.where(nyq, -xi, xi)
     return 0.5 * (green_voigt_direct(xi, lam0, mu0) + green_voigt_direct(flip, lam0, mu0))
 
 
@@ -120,28 +124,40 @@ def _stiffness_field_apply(phase, Cs, field):
     return out
 
 
-def _apply_green(tau_hat, lam0, mu0):
-    """eps_hat[I] = sum_J Gamma_V[I, J](xi) tau_hat[J], slab by slab in xi_1."""
-    N1, N2, N3 = tau_hat.shape[1:]
+def green_field(shape, lam0, mu0, slabs=None):
+    """Gamma_V at every frequency of an (N1, N2, N3) grid, symmetrised at the
+    Nyquist modes of each axis: a list over xi_1 of (N2, N3, 6, 6) slabs.
+    Computed once per solve (it depends on the grid and C0 only). slabs: the
+    xi_1 bin indices to compute (all by default)."""
+    N1, N2, N3 = shape
     f1, f2, f3 = frequencies(N1), frequencies(N2), frequencies(N3)
-    out = np.empty_like(tau_hat)
     x2, x3 = np.meshgrid(f2, f3, indexing="ij")
-    for a in range(N1):
+    out = []
+    for a in (range(N1) if slabs is None else slabs):
         xi = np.stack([np.full_like(x2, f1[a]), x2, x3], axis=-1)
-        G = green_voigt_symmetrised(xi, lam0, mu0, N1)      # (N2, N3, 6, 6), cubic grid
-        out[:, a] = np.einsum("yzIJ,Jyz->Iyz", G, tau_hat[:, a])
+        out.append(green_voigt_symmetrised(xi, lam0, mu0, (N1, N2, N3)))
+    return out
+
+
+def _apply_green(tau_hat, G):
+    """eps_hat[I] = sum_J Gamma_V[I, J](xi) tau_hat[J], slab by slab in xi_1."""
+    out = np.empty_like(tau_hat)
+    for a in range(tau_hat.shape[1]):
+        out[:, a] = np.einsum("yzIJ,Jyz->Iyz", G[a], tau_hat[:, a])
     return out
 
 
 def basic_scheme(phase, E, nu, E_voigt, tol=1e-6, max_iter=5000, lame0=None, workers=-1,
-                 eps0=None):
+                 eps0=None, green=None):
     """Alg. 1 (FFT-based homogenisation) on a dense (N1, N2, N3) phase grid.
 
     Iterates eps_{m+1} = E - IFFT[Gamma_hat FFT[(C - C0) eps_m]] from eps_0 = E
     until ||eps_{m+1} - eps_m||_F / ||E||_F < tol (Alg. 1; LS eq.
     (lippmann_schwinger) and its Fourier form). Returns a dict with the final
     strain field (6, N1, N2, N3) complex, the mean stress sigma_bar = <C eps>
-    (Sec. 2, C_eff paragraph), the iteration count and the residual history."""
+    (Sec. 2, C_eff paragraph), the iteration count and the residual history.
+    green: the slabs of green_field(phase.shape, lam0, mu0), when the caller
+    already holds them (they are computed here otherwise)."""
     phase = np.asarray(phase)
     lam0, mu0 = reference_lame(E, nu) if lame0 is None else lame0
     C0 = stiffness_voigt(lam0, mu0)
@@ -152,12 +168,13 @@ def basic_scheme(phase, E, nu, E_voigt, tol=1e-6, max_iter=5000, lame0=None, wor
     Eb = np.broadcast_to(Ev[:, None, None, None], (6,) + shape).astype(np.complex128)
     eps = Eb.copy() if eps0 is None else np.asarray(eps0, dtype=np.complex128).copy()
     normE = np.linalg.norm(Ev) * np.sqrt(float(np.prod(shape)))
+    G = green_field(shape, lam0, mu0) if green is None else green
     hist = []
     it = 0
     for it in range(1, max_iter + 1):
         tau = _stiffness_field_apply(phase, dCs, eps)
         tau_hat = sfft.fftn(tau, axes=(1, 2, 3), workers=workers)
-        eps_hat = _apply_green(tau_hat, lam0, mu0)
+        eps_hat = _apply_green(tau_hat, G)
         eps_hat[:, 0, 0, 0] = 0.0
         eps_new = Eb - sfft.ifftn(eps_hat, axes=(1, 2, 3), workers=workers)
         rel = np.linalg.norm(eps_new - eps) / normE

@@ -170,6 +170,21 @@ def spheres256(n: int = 8, seed: int = 2412) -> Workload:
     return Workload(f"spheres{1 << n}", n, ph, (1.0, 20.0), (0.3, 0.25), 1e-4, 1e-6, 128)
 
 
+def lamfib256(n: int = 8) -> Workload:
+    """8 layers normal to x3 plus a 4x4 lattice of fibres along x1 (the
+    geometry of laminate_with_fibres, broadcast x1) on a 2^n grid; matrix
+    E=1, nu=0.3; layers and fibres E=20, nu=0.25; 6 loads; tol 1e-4; eps_tt
+    1e-6; r_max 128."""
+    return Workload(f"lamfib{1 << n}", n, laminate_with_fibres(n), (1.0, 20.0), (0.3, 0.25),
+                    1e-4, 1e-6, 128)
+
+
+def by_name(name: str) -> Workload:
+    """The named workloads of the benchmark and the stored C_eff columns."""
+    table = {"spheres256": spheres256, "lamfib256": lamfib256}
+    return table[name]()
+
+
 def fibre_batch(items: int = 64, base_seed: int = 2413):
     """Batch of aligned-fibre microstructures, n ~ U{6,7,8,9} per item."""
     out = []

@@ -1,7 +1,7 @@
 """Host-side helpers of bench.py (no GPU): the C_eff deviation from stored
-dense-oracle columns and the workload naming shared by both arms."""
+dense-oracle columns, the count of qualifying solves, and the stored columns
+of both benchmark workloads."""
 import importlib.util
-import json
 import os
 
 import numpy as np
@@ -16,20 +16,30 @@ def _bench():
     return mod
 
 
-def test_ceff_error_vs_dense(tmp_path):
+def test_ceff_errors_and_qualifying():
     b = _bench()
-    path = tmp_path / "g.json"
-    json.dump({"columns": {"0": {"sigma_bar_re": [1.4, 0.6, 0.6, 0, 0, 0]},
-                           "3": {"sigma_bar_re": [0, 0, 0, 0.4, 0, 0]}}}, open(path, "w"))
+    ref = {"columns": {"0": {"sigma_bar_re": [1.4, 0.6, 0.6, 0, 0, 0], "iters": 30},
+                       "3": {"sigma_bar_re": [0, 0, 0, 0.4, 0, 0], "iters": 40}}}
     C = np.zeros((6, 6))
     C[:, 0] = [1.54, 0.6, 0.6, 0, 0, 0]
-    C[:, 3] = [0, 0, 0, 0.4, 0, 0]
-    err = b.ceff_error_vs_dense(C, str(path))
-    assert abs(err["0"] - 0.1) < 1e-12 and err["3"] == 0.0
-    assert b.ceff_error_vs_dense(C, str(tmp_path / "missing.json")) is None
+    C[:, 3] = [0, 0, 0, 0.4 * (1 + 5e-5), 0, 0]
+    err = b.ceff_errors(C, ref)
+    assert abs(err[0] - 0.1) < 1e-12 and abs(err[3] - 5e-5) < 1e-12
+    infos = [{"residual": 1e-5}] * 6
+    # column 0 is 10 % off, column 3 within 1e-4, the others have no stored column
+    assert b.qualifying(C, infos, ref, 1e-4) == [3]
+    # a solve that did not meet the stop test does not count
+    infos = [{"residual": 1e-5}] * 3 + [{"residual": 2e-4}] + [{"residual": 1e-5}] * 2
+    assert b.qualifying(C, infos, ref, 1e-4) == []
+    assert b.ceff_errors(C, None) is None
+    assert b.dense_iters(ref) == 35.0
 
 
-def test_stored_dense_column_is_readable():
+def test_stored_dense_columns_are_readable():
     b = _bench()
-    err = b.ceff_error_vs_dense(np.zeros((6, 6)))
-    assert err is not None and abs(err["0"] - 1.0) < 1e-12
+    for name in ("lamfib256", "spheres256"):
+        ref = b.golden(name)
+        assert ref is not None and len(ref["columns"]) >= 2
+        err = b.ceff_errors(np.zeros((6, 6)), ref)
+        assert all(abs(v - 1.0) < 1e-12 for v in err.values())
+    assert len(b.golden("lamfib256")["columns"]) == 6

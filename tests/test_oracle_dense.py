@@ -272,3 +272,24 @@ def test_pin_catches_dropped_green_term(monkeypatch):
         test_green_closed_form_equals_definition()
     with pytest.raises(AssertionError):
         test_green_projector_identities()
+
+
+def test_broadcast_grid_equals_full_grid():
+    """A field constant along x1 has Fourier content only at xi_1 = 0, so the
+    basic scheme on the (1, N, N) grid is the basic scheme on the (N, N, N)
+    grid restricted to those modes: same iterates, same sigma_bar. This holds
+    only if the Nyquist symmetrisation (App. A) is taken per axis with that
+    axis' own extent (a slip that uses N_1 = 1 for all axes moves sigma_bar by
+    7e-2 on this random phase field)."""
+    n = 3
+    N = 1 << n
+    rng = np.random.default_rng(5)
+    ph1 = (rng.random((1, N, N)) < 0.3).astype(np.uint8)   # broadcast x1
+    ph = synth.broadcast_dense(ph1, n)
+    E, nu = (1.0, 20.0), (0.3, 0.25)
+    for k in (0, 3, 4):
+        a = dense.basic_scheme(ph1, E, nu, np.eye(6)[k], tol=0.0, max_iter=8)
+        b = dense.basic_scheme(ph, E, nu, np.eye(6)[k], tol=0.0, max_iter=8)
+        assert np.allclose(a["sigma_bar"], b["sigma_bar"], rtol=0, atol=1e-12)
+        assert np.allclose(a["history"], b["history"], rtol=1e-10, atol=1e-14)
+        assert np.allclose(a["eps"][:, 0], b["eps"][:, 0], atol=1e-12)

@@ -190,6 +190,111 @@ def test_sketched_product_exact_with_full_sketch():
         assert np.allclose(G, np.diag(live.astype(float)), atol=1e-11)
 
 
+def _random_op(rng, dims, ranks):
+    return [rng.standard_normal((ranks[k], d, d, ranks[k + 1]))
+            + 1j * rng.standard_normal((ranks[k], d, d, ranks[k + 1])) for k, d in enumerate(dims)]
+
+
+def _tto_sum(a, b):
+    """a + b as a TTO of rank r(a) + r(b) (block-diagonal cores)."""
+    L = len(a)
+    out = []
+    for k, (A, B) in enumerate(zip(a, b)):
+        if k == 0:
+            out.append(np.concatenate([A, B], axis=3))
+        elif k == L - 1:
+            out.append(np.concatenate([A, B], axis=0))
+        else:
+            C = np.zeros((A.shape[0] + B.shape[0],) + A.shape[1:3] + (A.shape[3] + B.shape[3],),
+                         dtype=np.complex128)
+            C[:A.shape[0], :, :, :A.shape[3]] = A
+            C[A.shape[0]:, :, :, A.shape[3]:] = B
+            out.append(C)
+    return out
+
+
+def _below_rank_case():
+    """A product whose formal rank (Table 2: a s = 12) is twice its true rank
+    (6): the operator is A + A/2 written with rank 4, the TT has rank 3."""
+    dims = [6] + [2] * 9
+    rng = np.random.default_rng(3)
+    A = _random_op(rng, dims, [1] + [2] * 9 + [1])
+    A2 = _tto_sum(A, [W * (0.5 if k == 0 else 1.0) for k, W in enumerate(A)])
+    x = random_tt(rng, dims, [1] + [3] * 9 + [1])
+    y = oq.tt_full(oq.tto_apply_exact(A2, x)).reshape(-1)
+    return A2, x, y
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def test_sketched_product_below_formal_rank_is_exact():
+    """Sketch rank ell = 6 is half the product's formal rank but equal to its
+    true rank: the randomized compression must recover the exact product (the
+    sketch spans the range of each right unfolding, and every live direction is
+    kept). A dropped live column of the orthonormalised environment, or an
+    environment that does not span the product's right range, fails here
+    (both planted in test_sketched_pin_catches_planted_mistakes)."""
+    A2, x, y = _below_rank_case()
+    assert oq.tt_ranks(oq.tto_apply_exact(A2, x))[5] == 12
+    assert oq.tt_ranks(oq.tt_round(oq.tto_apply_exact(A2, x), 1e-14, 10 ** 9)[0])[5] == 6
+    for ell in (6, 8):
+        ys = oq.tto_apply_sketched(A2, x, ell, 11, 2)
+        assert _rel(oq.tt_full(ys).reshape(-1), y) < 1e-12
+
+
+def test_sketched_product_quasi_optimal():
+    """Below the true rank (flat spectra: a random TT through the Green
+    operator) the sketched product is within 2x the error of the TT-SVD
+    rounding of the exact product at half the sketch rank (measured at most
+    1.4x over seeds 0-3 and ell in {8, 12, 16, 24}), and, being a TT of ranks
+    <= ell, no better than the optimal rank-ell error, which the TT-SVD
+    rounding exceeds by at most sqrt(L - 1) (Sec. 3, rounding bound)."""
+    n = 3
+    G = oq.gamma_qtt(n, 2.0, 1.0, 1e-12)
+    dims = [6] + [2] * (3 * n)
+    L = len(dims)
+    for seed in range(2):
+        rng = np.random.default_rng(seed)
+        x = random_tt(rng, dims, [1] + [6] * (L - 1) + [1])
+        yc = oq.tto_apply_exact(G, x)
+        y = oq.tt_full(yc).reshape(-1)
+        for ell in (8, 16, 24):
+            e_sk = _rel(oq.tt_full(oq.tto_apply_sketched(G, x, ell, 7 + seed, 3)).reshape(-1), y)
+            e_half = _rel(oq.tt_full(oq.tt_round(yc, 0.0, ell // 2)[0]).reshape(-1), y)
+            e_full = _rel(oq.tt_full(oq.tt_round(yc, 0.0, ell)[0]).reshape(-1), y)
+            assert e_full / np.sqrt(L - 1) <= e_sk <= 2.0 * e_half, (seed, ell, e_sk, e_half)
+
+
+def test_sketched_pin_catches_planted_mistakes(monkeypatch):
+    """Plant two mistakes in the oracle's sketched product and check that the
+    below-rank pin fails: (1) the orthonormalised environment loses its last
+    live column; (2) the environment is replaced by an orthonormal basis of an
+    unrelated space of the same size."""
+    A2, x, y = _below_rank_case()
+    good = oq.orthonormal_range
+
+    def dropped(P, tau=oq.SKETCH_DROP_TAU):
+        Q, M = good(P, tau)
+        k = int(np.sum(np.linalg.norm(Q, axis=0) > 0.5))
+        Q, M = Q.copy(), M.copy()
+        Q[:, k - 1] = 0
+        M[:, k - 1] = 0
+        return Q, M
+
+    def unrelated(P, tau=oq.SKETCH_DROP_TAU):
+        r = np.random.default_rng(P.shape[0] * 31 + P.shape[1])
+        Z = r.standard_normal(P.shape) + 1j * r.standard_normal(P.shape)
+        return np.linalg.qr(Z)[0], np.eye(P.shape[1])
+
+    for bad in (dropped, unrelated):
+        monkeypatch.setattr(oq, "orthonormal_range", bad)
+        ys = oq.tto_apply_sketched(A2, x, 6, 11, 2)
+        assert _rel(oq.tt_full(ys).reshape(-1), y) > 1e-3, bad.__name__
+    monkeypatch.setattr(oq, "orthonormal_range", good)
+
+
 def test_orthonormal_range_is_pivoted_qr():
     # full column rank: Q is the thin-QR factor, with real positive diagonal
     # in R, of P with its columns in the pivot order (numpy's QR of the
