@@ -60,6 +60,9 @@ extern "C" {
 #define QTT_FP32 1
 #define QTT_CONTRACT_SIMT 0
 #define QTT_CONTRACT_TF32X3 1
+#define QTT_CONTRACT_TC 2
+#define QTT_FACTOR_NATIVE 0
+#define QTT_FACTOR_FP64 1
 
 #define QTT_MAX_CORES 64
 
@@ -91,7 +94,8 @@ uint64_t qtt_ctx_launches(qtt_ctx_t ctx);
  * c in (0 gemm, 1 qr, 2 svd) out[3c] = launches, out[3c+1] = total ms,
  * out[3c+2] = algorithmic real flops (GEMM: 8 M N K per complex product;
  * QR: 8 (2 m n^2 - 2 n^3/3); SVD: one Jacobi sweep's count per launch);
- * out[9] = Jacobi sweeps run over all SVD launches (10 doubles in all);
+ * out[9] = Jacobi sweeps run over all SVD launches, out[10] = GEMMs run on
+ * the tcgen05 tensor-core kernel (11 doubles in all);
  * reset = 1 clears the counters. */
 int qtt_ctx_set_profiling(qtt_ctx_t ctx, int on);
 int qtt_ctx_profile(qtt_ctx_t ctx, int reset, double* out);
@@ -112,6 +116,13 @@ int qtt_tt_from_dense(qtt_ctx_t ctx, int L, const int* dims, const double* dense
 int qtt_tt_shape(qtt_tt_t tt, int* L, int* dims, int* ranks);
 /* Download the cores (interleaved complex doubles, concatenated). */
 int qtt_tt_export(qtt_ctx_t ctx, qtt_tt_t tt, double* cores);
+/* The full tensor a TT represents (eq. (tt_format): the entry at (i_1..i_L)
+ * is the product of the core slices G_k[:, i_k, :]), contracted on the device
+ * left to right and written to `dense` as prod(dims) interleaved complex
+ * doubles in row-major order (caller-owned, 2 prod(dims) doubles). For tests
+ * and small grids: returns QTT_EINVAL above 2^30 entries, QTT_ENOMEM when
+ * the workspace cannot hold the partial products. */
+int qtt_tt_to_dense(qtt_ctx_t ctx, qtt_tt_t tt, double* dense);
 void qtt_tt_free(qtt_tt_t tt);
 
 /* Upload an operator: L cores with d_out[L], d_in[L], ranks[L+1] and
@@ -188,7 +199,10 @@ int gamma0_apply(qtt_ctx_t ctx, const int n[3], double lambda0, double mu0, int 
  * eps_tt ||x|| / sqrt(L - 1) and rank cap rmax. Returns QTT_WRANKCAP when the
  * cap dropped more than the threshold allows. */
 int tt_round(qtt_ctx_t ctx, qtt_tt_t inout, double eps_tt, int rmax);
-/* <a, b> = sum conj(a) b (FP64 accumulation). */
+/* <a, b> = sum conj(a) b (Sec. 3, Table 2: the TT inner product as a
+ * left-to-right sweep of transfer matrices, O(L d r^3); the stop test of
+ * Alg. 2 is formed from three of them). Transfer matrices in FP64 in both
+ * precisions; *re, *im are written after the context stream is synchronised. */
 int qtt_tt_dot(qtt_ctx_t ctx, qtt_tt_t a, qtt_tt_t b, double* re, double* im);
 /* <a, b> for callers that cannot allocate memory during the call -- code
  * that runs while an external framework owns all device memory, a hot loop
@@ -205,8 +219,11 @@ int qtt_tt_dot(qtt_ctx_t ctx, qtt_tt_t a, qtt_tt_t b, double* re, double* im);
  * and caches it; make that first call before any stream capture. All calls
  * share the one array: calls whose work overlaps on the GPU (other streams or
  * host threads) race and must be serialised by the caller. Work is ordered on
- * `cuda_stream` (NULL = legacy default stream); the call synchronises it
- * before writing *re, *im. */
+ * `cuda_stream`; NULL means the stream of the TTs' context, which is already
+ * ordered after the library work that wrote a and b (another stream must be
+ * ordered after that work by the caller). The call synchronises the stream
+ * before writing *re, *im, runs on the context's device and leaves the
+ * caller's current device as it found it. */
 #define QTT_NOALLOC_MAX_RANK 64
 #define QTT_NOALLOC_MAX_DIM 6
 int qtt_tt_dot_noalloc(qtt_tt_t a, qtt_tt_t b, void* cuda_stream, double* re, double* im);
@@ -215,8 +232,11 @@ int qtt_tt_dot_noalloc(qtt_tt_t a, qtt_tt_t b, void* cuda_stream, double* re, do
  * cores raised. */
 int qtt_op_sandwich_mean(qtt_ctx_t ctx, qtt_op_t op, qtt_tt_t y, qtt_tt_t x, double* re,
                          double* im);
-/* Grid mean of A x without forming A x; writes 2 * d_out[0] doubles
- * (interleaved complex, one per component of the first core). */
+/* Grid mean of A x without forming A x (Sec. 2, the C_eff paragraph: the
+ * volume average <(C - C0) eps> of the polarisation, which with C0 E gives
+ * sigma_bar): every binary core is contracted with the averaging vector
+ * (1/2, 1/2) in an FP64 sweep; writes 2 * d_out[0] doubles (interleaved
+ * complex, one per component of the first core). */
 int qtt_op_mean_apply(qtt_ctx_t ctx, qtt_op_t op, qtt_tt_t x, double* out);
 
 /* ---------------------------------------------------------------- solver */
@@ -278,10 +298,23 @@ int qtt_ctx_set_tt_svd(qtt_ctx_t ctx, double gram_threshold);
  * QTT_CONTRACT_SIMT (default) runs every core contraction as FP32 SIMT
  * GEMMs; QTT_CONTRACT_TF32X3 runs them on the tensor cores with TF32 inputs
  * split as x = hi + lo and products hi*hi + hi*lo + lo*hi accumulated in FP32
- * (FP32-level accuracy). Factorisations, norms and the C_eff average are
- * unaffected. Returns QTT_EINVAL for an unknown mode or TF32X3 on an FP64
- * context. */
+ * (FP32-level accuracy); QTT_CONTRACT_TC runs every unbatched contraction
+ * with M >= 64, N >= 32, K >= 64 on the 5th-generation tensor cores
+ * (tcgen05.mma kind::tf32, TMA-staged operands, TMEM accumulators; the same
+ * hi/lo split with the hi*hi products and the corrections in separate
+ * accumulators) and the other contractions as FP32 SIMT GEMMs. Factorisations, norms and the C_eff average are unaffected. Returns
+ * QTT_EINVAL for an unknown mode or a tensor-core mode on an FP64 context. */
 int qtt_ctx_set_contraction(qtt_ctx_t ctx, int mode);
+/* Factorisation precision of an FP32 context (the mixed mode of the
+ * method's precision pattern: bulk contractions in FP32, the QR and SVD
+ * steps of TT rounding in FP64; Sec. 3 rounding, whose per-bond threshold
+ * eps_tt ||x|| / sqrt(L - 1) is 2e-7 ||x|| at eps_tt 1e-6 on 25 cores, at
+ * the FP32 rounding level): QTT_FACTOR_NATIVE (default) factorises in the
+ * context's precision; QTT_FACTOR_FP64 widens every QR, SVD and sketch
+ * Cholesky operand of an FP32 context to FP64, factorises it with the FP64
+ * kernels and rounds the factors back (cores stay complex64). No effect on
+ * an FP64 context. Returns QTT_EINVAL for an unknown mode. */
+int qtt_ctx_set_factorization(qtt_ctx_t ctx, int mode);
 /* C_eff and its derivatives with respect to phase parameters (E or nu of a
  * phase). The Direct-scheme LS operator (with the Nyquist symmetrisation of
  * App. A) is self-adjoint, so the adjoint solution of load l equals its

@@ -183,6 +183,10 @@ gemm_kernel(GemmArgs g) {
 // hi*hi + hi*lo + lo*hi (the dropped lo*lo term is ~2^-22 relative, the
 // level of FP32 rounding). The complex product is four real products:
 // re = Ar Br - Ai Bi, im = Ar Bi + Ai Br, i.e. 12 MMAs per k-step and tile.
+// The hi*hi products and the ~2^-11 smaller correction products go to
+// separate accumulators, summed in the epilogue: the tensor core aligns the
+// addends of one MMA to the largest before adding, so corrections added into
+// the hi*hi accumulator would lose their low bits.
 // Same arguments, batching, split-K and epilogue as gemm_kernel<float>.
 // Tile 64 x 64 x 8, four warps of 32 x 32 outputs each.
 __device__ __forceinline__ uint32_t f32_to_tf32(float x) {
@@ -225,13 +229,14 @@ __global__ void __launch_bounds__(128) gemm_tf32x3_kernel(GemmArgs g) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int gq = lane >> 2, tq = lane & 3;              // group, thread in group
   const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;  // warp tile origin
-  float accr[2][4][4], acci[2][4][4];
+  float accr[2][4][4], acci[2][4][4];  // hi*hi products
+  float corr[2][4][4], cori[2][4][4];  // hi*lo and lo*hi corrections
 #pragma unroll
   for (int i = 0; i < 2; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) accr[i][j][q] = acci[i][j][q] = 0.f;
+      for (int q = 0; q < 4; ++q) accr[i][j][q] = acci[i][j][q] = corr[i][j][q] = cori[i][j][q] = 0.f;
   const bool a_mfast = (g.a_rs == 1);
   const bool b_nfast = (g.b_cs == 1);
   for (int k0 = kbeg; k0 < kend; k0 += BK) {
@@ -287,18 +292,18 @@ __global__ void __launch_bounds__(128) gemm_tf32x3_kernel(GemmArgs g) {
       for (int i = 0; i < 2; ++i) {
         // re += Ar Br - Ai Bi
         mma_tf32(accr[i][j], arh[i], brh);
-        mma_tf32(accr[i][j], arh[i], brl);
-        mma_tf32(accr[i][j], arl[i], brh);
         mma_tf32(accr[i][j], anh[i], bih);
-        mma_tf32(accr[i][j], anh[i], bil);
-        mma_tf32(accr[i][j], anl[i], bih);
+        mma_tf32(corr[i][j], arh[i], brl);
+        mma_tf32(corr[i][j], arl[i], brh);
+        mma_tf32(corr[i][j], anh[i], bil);
+        mma_tf32(corr[i][j], anl[i], bih);
         // im += Ar Bi + Ai Br
         mma_tf32(acci[i][j], arh[i], bih);
-        mma_tf32(acci[i][j], arh[i], bil);
-        mma_tf32(acci[i][j], arl[i], bih);
         mma_tf32(acci[i][j], aih[i], brh);
-        mma_tf32(acci[i][j], aih[i], brl);
-        mma_tf32(acci[i][j], ail[i], brh);
+        mma_tf32(cori[i][j], arh[i], bil);
+        mma_tf32(cori[i][j], arl[i], bih);
+        mma_tf32(cori[i][j], aih[i], brl);
+        mma_tf32(cori[i][j], ail[i], brh);
       }
     }
     __syncthreads();
@@ -317,7 +322,8 @@ __global__ void __launch_bounds__(128) gemm_tf32x3_kernel(GemmArgs g) {
         const int gn = n0 + wn + j * 8 + 2 * tq + (q & 1);
         if (gm >= g.M || gn >= g.N) continue;
         Cx<float>* p = C + (long long)gm * g.c_rs + (long long)gn * g.c_cs;
-        Cx<float> v = cmul(alpha, mk<float>(accr[i][j][q], acci[i][j][q]));
+        Cx<float> v = cmul(alpha, mk<float>(accr[i][j][q] + corr[i][j][q],
+                                            acci[i][j][q] + cori[i][j][q]));
         if (g.part) {
           const long long nbat = (long long)g.nb1 * g.nb2 * g.nb3;
           const long long bidx = ((long long)b1 * g.nb2 + b2) * g.nb3 + b3;

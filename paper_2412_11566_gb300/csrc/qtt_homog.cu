@@ -23,6 +23,7 @@
 
 #include "../../include/qtt_homog.h"
 #include "kernels.cuh"
+#include "tc_gemm.cuh"
 
 using namespace qtt;
 
@@ -120,13 +121,93 @@ struct Arena {
   }
 };
 
-// An execution lane: a stream, the arena its temporaries come from, and a
-// pinned host buffer for small readbacks. Work on one lane is stream-ordered,
-// so arena memory released on a lane can be reused by that lane at once.
+// Kernel-class timing of one lane (class: 0 gemm, 1 qr, 2 svd): CUDA
+// events recorded around launches on the lane's stream, resolved in batches
+// by the lane's own host thread, so that lanes never share a lock while they
+// launch. The totals are merged into the context when the lanes finish.
+struct ProfBuf {
+  struct Ev {
+    cudaEvent_t a, b;
+    int cls;
+    double flops;
+  };
+  std::vector<Ev> evs;
+  double ms[3] = {0, 0, 0};
+  double flops[3] = {0, 0, 0};
+  long long n[3] = {0, 0, 0};
+  double sweeps = 0;  // Jacobi sweeps run
+  double tc_launches = 0;  // GEMMs run on the tcgen05 kernel
+  std::vector<cudaEvent_t> pool;  // resolved events, reused
+  cudaEvent_t take() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+  void resolve() {
+    for (auto& e : evs) {
+      float t = 0;
+      if (cudaEventSynchronize(e.b) == cudaSuccess && cudaEventElapsedTime(&t, e.a, e.b) == cudaSuccess) {
+        ms[e.cls] += t;
+        flops[e.cls] += e.flops;
+        n[e.cls] += 1;
+      }
+      pool.push_back(e.a);
+      pool.push_back(e.b);
+    }
+    evs.clear();
+  }
+  void release_events() {
+    resolve();
+    for (cudaEvent_t e : pool) cudaEventDestroy(e);
+    pool.clear();
+  }
+  void merge_into(ProfBuf& o) {
+    resolve();
+    for (int i = 0; i < 3; ++i) {
+      o.ms[i] += ms[i];
+      o.flops[i] += flops[i];
+      o.n[i] += n[i];
+      ms[i] = flops[i] = 0;
+      n[i] = 0;
+    }
+    o.sweeps += sweeps;
+    o.tc_launches += tc_launches;
+    sweeps = tc_launches = 0;
+  }
+};
+
+// An execution lane: a stream, the arena its temporaries come from, a
+// pinned host buffer for small readbacks and its profile buffer. Work on one
+// lane is stream-ordered, so arena memory released on a lane can be reused
+// by that lane at once.
 struct Lane {
   Arena* arena = nullptr;
   cudaStream_t stream = nullptr;
   void* pinned = nullptr;
+  ProfBuf prof;
+  // Host waits on the lane use this event, created with blocking
+  // synchronisation: the waiting thread sleeps instead of spinning, so many
+  // lanes can wait at once on a few host cores.
+  cudaEvent_t wait_ev = nullptr;
+  cudaError_t wait() {
+    if (!wait_ev) {
+      const cudaError_t e =
+          cudaEventCreateWithFlags(&wait_ev, cudaEventBlockingSync | cudaEventDisableTiming);
+      if (e != cudaSuccess) return e;
+    }
+    const cudaError_t e = cudaEventRecord(wait_ev, stream);
+    if (e != cudaSuccess) return e;
+    return cudaEventSynchronize(wait_ev);
+  }
+  void destroy_wait() {
+    if (wait_ev) cudaEventDestroy(wait_ev);
+    wait_ev = nullptr;
+  }
 };
 
 }  // namespace
@@ -143,27 +224,19 @@ struct qtt_ctx {
   Lane lane0;  // the context's own stream and arena
   std::string err;
   std::atomic<uint64_t> launches{0};
-  std::mutex prof_mu;
+  std::mutex prof_mu;  // guards prof (the merged totals) and lane0.prof
   int concurrent_loads = 1;  // load cases of ls_solve_ceff run side by side
   std::atomic<int> active_lanes{1};  // lanes of the running solve queue (split-K sizing)
   int contraction = QTT_CONTRACT_SIMT;  // FP32 mode: SIMT or split-TF32 tensor-core GEMMs
+  int factor = QTT_FACTOR_NATIVE;       // FP32 mode: factorisations in FP32 or in FP64
   double gram_threshold = 2e9;     // TT-SVD: 8 P c min(P, c) above this takes the Gram path
   double jacobi_tol_scale = 1.0;   // Jacobi stop: |a_p^H a_q| <= scale sqrt(m) eps |a_p||a_q|
   int jacobi_max_sweeps32 = 40;    // sweep cap in FP32 mode
   void* pinned = nullptr;  // small host readback buffer
-  // Optional per-kernel-class timing: events recorded around launches,
-  // resolved lazily (class: 0 gemm, 1 qr, 2 svd).
+  // Optional per-kernel-class timing (see ProfBuf): totals of the finished
+  // lanes; lane0 keeps its own buffer.
   int profiling = 0;
-  struct Ev {
-    cudaEvent_t a, b;
-    int cls;
-    double flops;
-  };
-  std::vector<Ev> evs;
-  double prof_ms[3] = {0, 0, 0};
-  double prof_sweeps = 0;  // Jacobi sweeps run (sum over SVD launches)
-  double prof_flops[3] = {0, 0, 0};
-  long long prof_n[3] = {0, 0, 0};
+  ProfBuf prof;
   std::map<std::pair<int, int>, qtt_op*> sfft_cache;                            // (n, adjoint)
   std::map<std::tuple<int, double, double, int, double, int>, qtt_op*> gamma_cache;
   // TT of the 15 Green monomial fields per (n, eps, rmax), FP64, in the arena
@@ -176,39 +249,28 @@ struct qtt_ctx {
 };
 
 static void prof_flush(qtt_ctx* c) {
-  for (auto& e : c->evs) {
-    float ms = 0;
-    if (cudaEventSynchronize(e.b) == cudaSuccess && cudaEventElapsedTime(&ms, e.a, e.b) == cudaSuccess) {
-      c->prof_ms[e.cls] += ms;
-      c->prof_flops[e.cls] += e.flops;
-      c->prof_n[e.cls] += 1;
-    }
-    cudaEventDestroy(e.a);
-    cudaEventDestroy(e.b);
-  }
-  c->evs.clear();
+  c->lane0.prof.merge_into(c->prof);
 }
 
 struct ProfScope {
-  qtt_ctx* c;
-  qtt_ctx::Ev e{};
+  Lane* ln;
+  ProfBuf::Ev e{};
   bool on;
   cudaStream_t s;
-  ProfScope(qtt_ctx* ctx, cudaStream_t stream, int cls, double flops)
-      : c(ctx), on(ctx->profiling != 0), s(stream) {
+  ProfScope(qtt_ctx* ctx, Lane* lane, int cls, double flops)
+      : ln(lane), on(ctx->profiling != 0), s(lane->stream) {
     if (!on) return;
     e.cls = cls;
     e.flops = flops;
-    cudaEventCreate(&e.a);
-    cudaEventCreate(&e.b);
+    e.a = ln->prof.take();
+    e.b = ln->prof.take();
     cudaEventRecord(e.a, s);
   }
   ~ProfScope() {
     if (!on) return;
     cudaEventRecord(e.b, s);
-    std::lock_guard<std::mutex> g(c->prof_mu);
-    c->evs.push_back(e);
-    if (c->evs.size() > 4096) prof_flush(c);
+    ln->prof.evs.push_back(e);
+    if (ln->prof.evs.size() > 4096) ln->prof.resolve();
   }
 };
 
@@ -312,6 +374,103 @@ struct Eng {
   }
   void release(void* p) { ln->arena->release(p); }
 
+  // cuTensorMapEncodeTiled from the driver, looked up once.
+  typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                    const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                    const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                    CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  static EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = [] {
+      void* f = nullptr;
+      cudaDriverEntryPointQueryResult q{};
+      if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                           &q) != cudaSuccess ||
+          q != cudaDriverEntryPointSuccess)
+        f = nullptr;
+      return (EncodeTiledFn)f;
+    }();
+    return fn;
+  }
+  // 2-D FP32 tensor map over a rows x cols row-major array (cols a multiple
+  // of 32, so rows start on 128-byte boundaries), box 32 x 128, 128-byte
+  // swizzle, zero fill outside.
+  static void tc_map(CUtensorMap* m, float* p, long long rows, long long cols) {
+    EncodeTiledFn enc = encode_fn();
+    QREQ(enc, "tensor-core GEMM: cuTensorMapEncodeTiled unavailable");
+    QREQ(((uintptr_t)p & 15) == 0 && cols % 32 == 0, "tensor-core GEMM: misaligned operand");
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)cols * 4};
+    cuuint32_t box[2] = {(cuuint32_t)tc::BK, (cuuint32_t)tc::BM};
+    cuuint32_t es[2] = {1, 1};
+    const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, p, dims, strides, box, es,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+      throw QttError(QTT_ECUDA, "tensor-core GEMM: tensor map encoding failed (" +
+                                    std::to_string((int)r) + ")");
+  }
+
+  // One unbatched complex FP32 GEMM on the tcgen05 tensor cores (see
+  // tc_gemm.cuh): operands split into TF32 hi/lo planes by two preparation
+  // kernels, then one 128 x 128 tile per CTA.
+  void gemm_tc(int M, int N, int K, MatRef A, MatRef B, void* C, long long c_rs, long long c_cs,
+               Cplx alpha, Cplx beta) {
+    const int Kp = (2 * K + tc::BK - 1) / tc::BK * tc::BK;
+    float* Ah = (float*)ln->arena->alloc((size_t)M * Kp * 4);
+    float* Al = (float*)ln->arena->alloc((size_t)M * Kp * 4);
+    float* Bh = (float*)ln->arena->alloc((size_t)2 * N * Kp * 4);
+    float* Bl = (float*)ln->arena->alloc((size_t)2 * N * Kp * 4);
+    int* err = (int*)ln->arena->alloc(sizeof(int));
+    QCHECK(cudaMemsetAsync(err, 0, sizeof(int), st()));
+    tc::tc_prep_a_kernel<<<grid1d((long long)M * (Kp / 2)), 256, 0, st()>>>(
+        (const Cx<float>*)A.p, A.rs, A.cs, A.conj, M, K, Kp, Ah, Al);
+    post("tc_prep_a_kernel", __LINE__);
+    tc::tc_prep_b_kernel<<<grid1d((long long)N * (Kp / 2)), 256, 0, st()>>>(
+        (const Cx<float>*)B.p, B.rs, B.cs, B.conj, N, K, Kp, Bh, Bl);
+    post("tc_prep_b_kernel", __LINE__);
+    CUtensorMap mAh, mAl, mBh, mBl;
+    tc_map(&mAh, Ah, M, Kp);
+    tc_map(&mAl, Al, M, Kp);
+    tc_map(&mBh, Bh, 2ll * N, Kp);
+    tc_map(&mBl, Bl, 2ll * N, Kp);
+    static const bool attr = [] {
+      cudaFuncSetAttribute(tc::tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           tc::SMEM_BYTES);
+      return true;
+    }();
+    (void)attr;
+    tc::TcEpilogue ep{};
+    ep.C = (Cx<float>*)C;
+    ep.c_rs = c_rs;
+    ep.c_cs = c_cs;
+    ep.M = M;
+    ep.N = N;
+    ep.alpha_re = (float)alpha.re;
+    ep.alpha_im = (float)alpha.im;
+    ep.beta_re = (float)beta.re;
+    ep.beta_im = (float)beta.im;
+    ep.use_beta = (beta.re != 0.0 || beta.im != 0.0);
+    ep.err = err;
+    const dim3 grid((unsigned)((M + tc::BM - 1) / tc::BM), (unsigned)((2 * N + tc::BN - 1) / tc::BN));
+    {
+      ProfScope ps(c, ln, 0, 8.0 * M * N * (double)K);
+      tc::tc_gemm_kernel<<<grid, 128, tc::SMEM_BYTES, st()>>>(mAh, mAl, mBh, mBl, Kp, ep);
+      post("tc_gemm_kernel", __LINE__);
+    }
+    if (c->profiling) ln->prof.tc_launches += 1;
+    int h = 0;
+    QCHECK(cudaMemcpyAsync(ln->pinned, err, sizeof(int), cudaMemcpyDeviceToHost, st()));
+    QCHECK(ln->wait());
+    memcpy(&h, ln->pinned, sizeof(int));
+    ln->arena->release(Ah);
+    ln->arena->release(Al);
+    ln->arena->release(Bh);
+    ln->arena->release(Bl);
+    ln->arena->release(err);
+    if (h) throw QttError(QTT_ETIMEOUT, "tensor-core GEMM: a device wait ran out (code " +
+                                            std::to_string(h) + ")");
+  }
+
   // One GEMM launch: SIMT FP32/FP64 tiles, or in FP32 mode with the
   // split-TF32 contraction setting the tensor-core kernel (same tiling and
   // arguments).
@@ -350,6 +509,14 @@ struct Eng {
             copy_kernel<R><<<grid1d((long long)M * N), 256, 0, st()>>>(cp, cp, a, (long long)M * N);
             post("copy_kernel", __LINE__);
           }
+      return;
+    }
+    if (sizeof(R) == 4 && c->contraction == QTT_CONTRACT_TC && nb1 == 1 && nb2 == 1 &&
+        nb3 == 1 && ksplit == 1 && M >= 64 && N >= 32 && K >= 64) {
+      check_span(A.p, span(M, A.rs, K, A.cs), "gemm A");
+      check_span(B.p, span(K, B.rs, N, B.cs), "gemm B");
+      check_span(C, span(M, c_rs, N, c_cs), "gemm C");
+      gemm_tc(M, N, K, A, B, C, c_rs, c_cs, alpha, beta);
       return;
     }
     GemmArgs g{};
@@ -410,7 +577,7 @@ struct Eng {
           const dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)((N + BN - 1) / BN),
                           (unsigned)(nbat * ks));
           {
-            ProfScope ps(c, st(), 0, 8.0 * M * N * (double)K * nbat);
+            ProfScope ps(c, ln, 0, 8.0 * M * N * (double)K * nbat);
             launch_gemm(grid, g);
             splitk_reduce_kernel<R><<<grid1d(nbat * M * N), 256, 0, st()>>>(
                 part, (int)ks, nbat, M, N, nb2, nb3, (Cx<R>*)C, c_rs, c_cs, c_b1, c_b2, c_b3,
@@ -454,7 +621,7 @@ struct Eng {
             }
       }
       const dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)(nb * per_b1));
-      ProfScope ps(c, st(), 0, 8.0 * M * N * (double)K * nb * nb2 * nb3);
+      ProfScope ps(c, ln, 0, 8.0 * M * N * (double)K * nb * nb2 * nb3);
       launch_gemm(grid, h);
     }
   }
@@ -509,8 +676,42 @@ struct Eng {
 
   // Householder QR of the strided m x n matrix A: Q (m x k) and Rm (k x n),
   // column-major, k = min(m, n).
+  bool factor64() const { return sizeof(R) == 4 && c->factor == QTT_FACTOR_FP64; }
+
+  // FP32 context with FP64 factorisations: the operand is widened to FP64,
+  // factorised by the FP64 kernels on the same lane, and the factors are
+  // rounded back to FP32.
+  Cx<double>* widen(const Cx<R>* p, long long cnt) {
+    Cx<double>* w = (Cx<double>*)ln->arena->alloc((size_t)cnt * sizeof(Cx<double>));
+    convert_kernel<R, double><<<grid1d(cnt), 256, 0, st()>>>(p, w, cnt);
+    post("convert_kernel", __LINE__);
+    return w;
+  }
+  void narrow(const Cx<double>* w, Cx<R>* p, long long cnt) {
+    convert_kernel<double, R><<<grid1d(cnt), 256, 0, st()>>>(w, p, cnt);
+    post("convert_kernel", __LINE__);
+  }
+
   void qr(int m, int n, const void* A, long long rs, long long cs, int conj, Cx<R>* Q, Cx<R>* Rm) {
     const int k = std::min(m, n);
+    if (factor64()) {
+      check_span(A, span(m, rs, n, cs), "qr A");
+      Cx<R>* Ac = alloc((long long)m * n);  // column-major FP32 copy, then FP64
+      const long long sz[2] = {m, n}, ist[2] = {rs, cs}, ost[2] = {1, m};
+      copy(A, Ac, 2, sz, ist, ost, conj);
+      Cx<double>* A64 = widen(Ac, (long long)m * n);
+      release(Ac);
+      Eng<double> d(c, ln);
+      Cx<double>* Q64 = d.alloc((long long)m * k);
+      Cx<double>* R64 = d.alloc((long long)k * n);
+      d.qr(m, n, A64, 1, m, 0, Q64, R64);
+      narrow(Q64, Q, (long long)m * k);
+      narrow(R64, Rm, (long long)k * n);
+      d.release(A64);
+      d.release(Q64);
+      d.release(R64);
+      return;
+    }
     check_span(A, span(m, rs, n, cs), "qr A");
     check_span(Q, (long long)m * k - 1, "qr Q");
     check_span(Rm, (long long)k * n - 1, "qr R");
@@ -521,7 +722,7 @@ struct Eng {
       // complex Householder QR with explicit Q: 4 x (2 m n^2 - 2 n^3 / 3) real
       // flops for the factor plus as many for forming Q (LAPACK operation counts)
       const double kk = k;
-      ProfScope ps(c, st(), 1, 2.0 * 4.0 * (2.0 * m * kk * kk - 2.0 * kk * kk * kk / 3.0));
+      ProfScope ps(c, ln, 1, 2.0 * 4.0 * (2.0 * m * kk * kk - 2.0 * kk * kk * kk / 3.0));
       const size_t bytes = (size_t)m * n * sizeof(Cx<R>);
       const bool sm = bytes <= smem_cap();
       qr_kernel<R><<<1, 1024, sm ? bytes : 0, st()>>>(m, n, (const Cx<R>*)A, rs, cs, conj, W, Q,
@@ -537,6 +738,16 @@ struct Eng {
   // row-major m x L matrix P: Gram matrix by GEMM, then one CTA factors it
   // (pivoted Cholesky stopped at dependent columns) and inverts the factor.
   Cx<R>* orth_factor(const Cx<R>* P, long long m, int L, double tau, int* err) {
+    if (factor64()) {
+      Cx<double>* P64 = widen(P, m * L);
+      Eng<double> d(c, ln);
+      Cx<double>* M64 = d.orth_factor(P64, m, L, tau, err);
+      d.release(P64);
+      Cx<R>* M = alloc((long long)L * L);
+      narrow(M64, M, (long long)L * L);
+      d.release(M64);
+      return M;
+    }
     Cx<R>* G = alloc((long long)L * L);
     QREQ(m < (1ll << 31), "orth_factor: too many rows");
     gemm(L, L, (int)m, mref(P, 1, L, 0, 0, 0, 1), mref(P, L, 1), G, L, 1, 0, 0, 0, 1, 1, 1);
@@ -547,7 +758,7 @@ struct Eng {
     int* perm = (int*)ln->arena->alloc(sizeof(int) * L);
     {
       const double l3 = (double)L * L * L;
-      ProfScope ps(c, st(), 1, 8.0 * l3 / 3.0 * 2.0);
+      ProfScope ps(c, ln, 1, 8.0 * l3 / 3.0 * 2.0);
       chol_piv_inv_kernel<R><<<1, 1024, sm ? bytes : 0, st()>>>(L, G, A, M, perm, tau, err,
                                                                 sm ? 1 : 0);
       post("chol_piv_inv_kernel", __LINE__);
@@ -568,6 +779,19 @@ struct Eng {
   // rotations); the caller forms what it needs from U by a GEMM.
   int svd(int m, int n, Cx<R>* A, Cx<R>* U, double* sigma, Cx<R>* V, double delta2, int rmax,
           int* cap_hit, bool squares = false) {
+    if (factor64()) {
+      Cx<double>* A64 = widen(A, (long long)m * n);
+      Eng<double> d(c, ln);
+      Cx<double>* U64 = d.alloc((long long)m * n);
+      Cx<double>* V64 = V ? d.alloc((long long)n * n) : nullptr;
+      const int k = d.svd(m, n, A64, U64, sigma, V64, delta2, rmax, cap_hit, squares);
+      narrow(U64, U, (long long)m * n);
+      if (V) narrow(V64, V, (long long)n * n);
+      d.release(A64);
+      d.release(U64);
+      if (V64) d.release(V64);
+      return k;
+    }
     if (squares || m <= n + n / 4) return svd_direct(m, n, A, U, sigma, V, delta2, rmax, cap_hit, squares);
     Cx<R>* Q = alloc((long long)m * n);
     Cx<R>* Rf = alloc((long long)n * n);
@@ -601,7 +825,7 @@ struct Eng {
       // flops counted for the sweeps actually run are not known here; the
       // profile records one sweep's count (n^2/2 pairs x (3 dots + 2
       // rotations of length m + 2 of length n) x 8 real flops) per launch
-      ProfScope ps(c, st(), 2, 0.5 * n * (double)n * (5.0 * m + 2.0 * n) * 8.0);
+      ProfScope ps(c, ln, 2, 0.5 * n * (double)n * (5.0 * m + 2.0 * n) * 8.0);
       const size_t bytes = (size_t)m * n * sizeof(Cx<R>);
       const bool sm = bytes <= smem_cap();
       if (sm || n < 64) {
@@ -644,7 +868,7 @@ struct Eng {
     post("svd_finish_kernel", __LINE__);
     int h[8];
     QCHECK(cudaMemcpyAsync(ln->pinned, tr, sizeof(int) * 8, cudaMemcpyDeviceToHost, st()));
-    QCHECK(cudaStreamSynchronize(st()));
+    QCHECK(ln->wait());
     memcpy(h, ln->pinned, sizeof(int) * 8);
     if (Vw) release(Vw);
     release(perm);
@@ -655,9 +879,8 @@ struct Eng {
     if (cap_hit) *cap_hit = h[1];
     if (c->profiling) {
       // the launch was counted with one sweep; add the further sweeps run
-      std::lock_guard<std::mutex> g(c->prof_mu);
-      if (h[2] > 1) c->prof_flops[2] += (h[2] - 1) * 0.5 * n * (double)n * (5.0 * m + 2.0 * n) * 8.0;
-      c->prof_sweeps += h[2];
+      if (h[2] > 1) ln->prof.flops[2] += (h[2] - 1) * 0.5 * n * (double)n * (5.0 * m + 2.0 * n) * 8.0;
+      ln->prof.sweeps += h[2];
     }
     return h[0];
   }
@@ -668,7 +891,7 @@ struct Eng {
     norm2_kernel<R><<<grid1d(count), 256, 0, st()>>>((const Cx<R>*)p, count, d);
     post("norm2_kernel", __LINE__);
     QCHECK(cudaMemcpyAsync(ln->pinned, d, sizeof(double), cudaMemcpyDeviceToHost, st()));
-    QCHECK(cudaStreamSynchronize(st()));
+    QCHECK(ln->wait());
     double v;
     memcpy(&v, ln->pinned, sizeof(double));
     release(d);
@@ -863,7 +1086,10 @@ qtt_tt* apply_sketched(Eng<R>& e, const qtt_op* A, const qtt_tt* x, int ell, int
   // number does not compound over the cores (a product of random cores loses
   // ~10x per core, more than single precision can hold after a few cores).
   std::vector<Cx<R>*> Mk(L + 1, nullptr);
-  const double drop_tau = sizeof(R) == 8 ? 1e-11 : 1e-6;
+  // relative Cholesky pivot below which a sketch direction is dropped: the
+  // reach of the Gram matrix's working precision (FP64 factors in an FP32
+  // context see FP32 data, whose own rounding sets the floor)
+  const double drop_tau = sizeof(R) == 8 ? 1e-11 : (e.factor64() ? 1e-9 : 1e-6);
   int* oerr = (int*)e.ln->arena->alloc(sizeof(int));
   QCHECK(cudaMemsetAsync(oerr, 0, sizeof(int), e.st()));
   psi[L] = e.alloc(1);
@@ -1037,7 +1263,7 @@ qtt_tt* apply_sketched(Eng<R>& e, const qtt_op* A, const qtt_tt* x, int ell, int
   }
   int herr = 0;
   QCHECK(cudaMemcpyAsync(e.ln->pinned, oerr, sizeof(int), cudaMemcpyDeviceToHost, e.st()));
-  QCHECK(cudaStreamSynchronize(e.st()));
+  QCHECK(e.ln->wait());
   memcpy(&herr, e.ln->pinned, sizeof(int));
   e.ln->arena->release(oerr);
   if (herr) {
@@ -1127,7 +1353,7 @@ void tt_dot(Eng<R>& e, const qtt_tt* a, const qtt_tt* b, double* re, double* im)
   }
   double h[2];
   QCHECK(cudaMemcpyAsync(e.ln->pinned, E, 16, cudaMemcpyDeviceToHost, e.st()));
-  QCHECK(cudaStreamSynchronize(e.st()));
+  QCHECK(e.ln->wait());
   memcpy(h, e.ln->pinned, 16);
   d.release(E);
   *re = h[0];
@@ -1185,7 +1411,7 @@ void op_mean(Eng<R>& e, const qtt_op* A, const qtt_tt* x, std::vector<double>& o
   out.assign(2 * Do, 0.0);
   std::vector<double> h(2 * Do);
   QCHECK(cudaMemcpyAsync(e.ln->pinned, V, 16 * Do, cudaMemcpyDeviceToHost, e.st()));
-  QCHECK(cudaStreamSynchronize(e.st()));
+  QCHECK(e.ln->wait());
   memcpy(h.data(), e.ln->pinned, 16 * Do);
   d.release(V);
   out = h;
@@ -1259,7 +1485,7 @@ void op_sandwich(Eng<R>& e, const qtt_op* A, const qtt_tt* y, const qtt_tt* x, d
     T = Tp;
   }
   QCHECK(cudaMemcpyAsync(e.ln->pinned, V, 16, cudaMemcpyDeviceToHost, e.st()));
-  QCHECK(cudaStreamSynchronize(e.st()));
+  QCHECK(e.ln->wait());
   memcpy(out2, e.ln->pinned, 16);
   d.release(V);
 }
@@ -1382,7 +1608,7 @@ std::vector<Cx<double>*> tt_svd_device(Eng<double>& e, Cx<double>* T, const std:
     e.post("colnorm2_kernel", __LINE__);
     std::vector<double> h(c);
     QCHECK(cudaMemcpyAsync(e.ln->pinned, cn, sizeof(double) * c, cudaMemcpyDeviceToHost, e.st()));
-    QCHECK(cudaStreamSynchronize(e.st()));
+    QCHECK(e.ln->wait());
     memcpy(h.data(), e.ln->pinned, sizeof(double) * c);
     e.ln->arena->release(cn);
     std::vector<int> perm(c);
@@ -1424,7 +1650,7 @@ std::vector<Cx<double>*> tt_svd_device(Eng<double>& e, Cx<double>* T, const std:
     {
       int hg = 0;
       QCHECK(cudaMemcpyAsync(e.ln->pinned, gerr, sizeof(int), cudaMemcpyDeviceToHost, e.st()));
-      QCHECK(cudaStreamSynchronize(e.st()));
+      QCHECK(e.ln->wait());
       memcpy(&hg, e.ln->pinned, sizeof(int));
       e.ln->arena->release(gerr);
       if (hg) throw QttError(QTT_EINVAL, "TT-SVD: column index out of range (kernel skipped access)");
@@ -1503,6 +1729,37 @@ qtt_tt* op_apply_impl(qtt_ctx* c, const qtt_op* op, const qtt_tt* in, double eps
   return y;
 }
 
+// Full tensor of a TT by left-to-right contraction of the cores, as
+// complex128 on the host (prod(dims) entries, row-major).
+template <typename R>
+void to_dense_impl(qtt_ctx* c, const qtt_tt* t, double* out) {
+  Eng<R> e(c);
+  long long rows = t->dims[0];  // running product of the leading dims
+  QREQ(t->ranks[0] == 1, "qtt_tt_to_dense: ranks[0] must be 1");
+  Cx<R>* cur = e.alloc(t->count(0));
+  QCHECK(cudaMemcpyAsync(cur, t->core[0], t->count(0) * sizeof(Cx<R>), cudaMemcpyDeviceToDevice,
+                         e.st()));
+  for (int k = 1; k < t->L; ++k) {
+    const int r0 = t->ranks[k], d = t->dims[k], r1 = t->ranks[k + 1];
+    QREQ(rows * d <= (1ll << 30) && rows < (1ll << 31), "qtt_tt_to_dense: tensor too large");
+    Cx<R>* nx = e.alloc(rows * d * r1);
+    // nx (rows x d r1) = cur (rows x r0) core_k (r0 x d r1)
+    e.gemm((int)rows, d * r1, r0, mref(cur, r0, 1), mref(t->core[k], (long long)d * r1, 1), nx,
+           (long long)d * r1, 1, 0, 0, 0, 1, 1, 1);
+    e.release(cur);
+    cur = nx;
+    rows *= d;
+  }
+  std::vector<Cx<R>> h(rows);
+  QCHECK(cudaMemcpyAsync(h.data(), cur, rows * sizeof(Cx<R>), cudaMemcpyDeviceToHost, e.st()));
+  QCHECK(e.ln->wait());
+  e.release(cur);
+  for (long long i = 0; i < rows; ++i) {
+    out[2 * i] = (double)h[i].x;
+    out[2 * i + 1] = (double)h[i].y;
+  }
+}
+
 template <typename R>
 int round_impl(qtt_ctx* c, qtt_tt* x, double eps, int rmax) {
   Eng<R> e(c);
@@ -1559,7 +1816,7 @@ qtt_op* build_sfft(qtt_ctx* c, int n, int adjoint, double eps) {
     std::vector<double> h(72, 0.0);
     for (int i = 0; i < 6; ++i) h[2 * (i * 6 + i)] = 1.0;
     QCHECK(cudaMemcpyAsync(I6, h.data(), 72 * 8, cudaMemcpyHostToDevice, e.st()));
-    QCHECK(cudaStreamSynchronize(e.st()));
+    QCHECK(e.ln->wait());
   }
   cores[0] = I6;
   for (int a = 0; a < 3; ++a)
@@ -1638,7 +1895,7 @@ qtt_op* assemble_raised(qtt_ctx* c, Eng<double>& e, std::vector<Cx<double>*>& tc
         QCHECK(cudaMemcpyAsync(d1, one.data(), 16, cudaMemcpyHostToDevice, e.st()));
         const long long sz[2] = {r, 2}, ist[2] = {0, 0}, ost[2] = {2ll * r + 1, r};
         e.copy(d1, I, 2, sz, ist, ost);
-        QCHECK(cudaStreamSynchronize(e.st()));
+        QCHECK(e.ln->wait());
         e.release(d1);
         cores[k] = I;
         R[k + 1] = r;
@@ -1795,7 +2052,7 @@ qtt_op* build_gamma(qtt_ctx* c, int n, double lam0, double mu0, int scheme, doub
     QCHECK(cudaMemcpyAsync(tc[k], gm.cores[k], cnt * sizeof(Cx<double>), cudaMemcpyDeviceToDevice,
                            e.st()));
   }
-  QCHECK(cudaStreamSynchronize(e.st()));
+  QCHECK(e.ln->wait());
   e.release(Cd);
   const int bc[3] = {0, 0, 0};
   qtt_op* o = assemble_raised(c, e, tc, gm.ranks, n, bc);
@@ -1841,9 +2098,25 @@ qtt_tt* e_field(qtt_ctx* c, Lane* ln, int L, const int* dims, const double* Ev) 
     t->core[k] = e.alloc(dims[k]);
     QCHECK(cudaMemcpyAsync(t->core[k], h.data(), sizeof(Cx<R>) * dims[k], cudaMemcpyHostToDevice,
                            e.st()));
-    QCHECK(cudaStreamSynchronize(e.st()));
+    QCHECK(e.ln->wait());
   }
   return t;
+}
+
+// QTT_TRACE=1 in the environment: every LS iteration prints its residual
+// and the largest rank of each intermediate TT to stderr.
+bool trace_on() {
+  static const bool on = [] {
+    const char* v = getenv("QTT_TRACE");
+    return v && v[0] == '1';
+  }();
+  return on;
+}
+
+int trace_load(const double* Ev) {
+  for (int i = 0; i < 6; ++i)
+    if (Ev[i] != 0.0) return i;
+  return -1;
 }
 
 template <typename R>
@@ -1905,6 +2178,8 @@ int solve_impl(qtt_ctx* c, const qtt_op* dC, const qtt_op* S, const qtt_op* Sh, 
     cap |= round_full<R>(e, xn, p->eps_tt, p->rmax);
     chk(xn, "rounding of the new strain");
     maxr = std::max({maxr, max_rank<R>(tau), max_rank<R>(tauh), max_rank<R>(epsh), max_rank<R>(xn)});
+    const int rk_tau = max_rank<R>(tau), rk_tauh = max_rank<R>(tauh), rk_epsh = max_rank<R>(epsh),
+              rk_x = max_rank<R>(xn);
     // ||xn - x||^2 = ||xn||^2 + ||x||^2 - 2 Re <xn, x>
     double a2r, a2i, b2r, b2i, abr, abi;
     tt_dot<R>(e, xn, xn, &a2r, &a2i);
@@ -1916,6 +2191,9 @@ int solve_impl(qtt_ctx* c, const qtt_op* dC, const qtt_op* S, const qtt_op* Sh, 
     const double floor2 = 64.0 * 2.220446049250313e-16 * (a2r + b2r);
     const double d2 = std::max(floor2, a2r + b2r - 2.0 * abr);
     rel = std::sqrt(d2) / normE;
+    if (trace_on())
+      fprintf(stderr, "[qtt] load %d iter %d residual %.4e ranks tau %d tauh %d epsh %d eps %d\n",
+              trace_load(Ev), it, rel, rk_tau, rk_tauh, rk_epsh, rk_x);
     free_tt(tau);
     free_tt(tauh);
     free_tt(epsh);
@@ -1952,7 +2230,7 @@ int solve_impl(qtt_ctx* c, const qtt_op* dC, const qtt_op* S, const qtt_op* Sh, 
       QCHECK(cudaMemcpyAsync(k->core[b], x->core[b], x->count(b) * sizeof(Cx<R>),
                              cudaMemcpyDeviceToDevice, e.st()));
     }
-    QCHECK(cudaStreamSynchronize(e.st()));
+    QCHECK(e.ln->wait());
     *keep = k;
   }
   free_tt(x);
@@ -2008,6 +2286,8 @@ void qtt_ctx_destroy(qtt_ctx_t c) {
   for (auto& kv : c->green_mono_cache)
     for (void* p : kv.second.cores) c->arena.release(p);
   if (c->pinned) cudaFreeHost(c->pinned);
+  c->lane0.destroy_wait();
+  c->lane0.prof.release_events();
   delete c;
 }
 
@@ -2026,15 +2306,13 @@ int qtt_ctx_profile(qtt_ctx_t c, int reset, double* out) {
   std::lock_guard<std::mutex> g(c->prof_mu);
   prof_flush(c);
   for (int i = 0; i < 3; ++i) {
-    out[3 * i] = (double)c->prof_n[i];
-    out[3 * i + 1] = c->prof_ms[i];
-    out[3 * i + 2] = c->prof_flops[i];
+    out[3 * i] = (double)c->prof.n[i];
+    out[3 * i + 1] = c->prof.ms[i];
+    out[3 * i + 2] = c->prof.flops[i];
   }
-  out[9] = c->prof_sweeps;
-  if (reset) {
-    for (int i = 0; i < 3; ++i) c->prof_n[i] = 0, c->prof_ms[i] = 0, c->prof_flops[i] = 0;
-    c->prof_sweeps = 0;
-  }
+  out[9] = c->prof.sweeps;
+  out[10] = c->prof.tc_launches;
+  if (reset) c->prof = ProfBuf();
   return QTT_OK;
 }
 size_t qtt_ctx_bytes_in_use(qtt_ctx_t c) { return c ? c->arena.used : 0; }
@@ -2132,6 +2410,16 @@ int qtt_tt_export(qtt_ctx_t ctx, qtt_tt_t t, double* cores) {
     off += cnt;
   }
   QCHECK(cudaStreamSynchronize(ctx->stream));
+  return QTT_OK;
+  API_END
+}
+
+int qtt_tt_to_dense(qtt_ctx_t ctx, qtt_tt_t t, double* dense) {
+  API_BEGIN(ctx)
+  QREQ(ctx && t && dense, "qtt_tt_to_dense: null argument");
+  QREQ(t->ctx == ctx, "qtt_tt_to_dense: TT from another context");
+  QREQ(t->ranks[t->L] == 1, "qtt_tt_to_dense: ranks[L] must be 1");
+  DISPATCH(ctx, to_dense_impl, ctx, t, dense);
   return QTT_OK;
   API_END
 }
@@ -2435,9 +2723,9 @@ void run_jobs(qtt_ctx* ctx, std::vector<SolveJob>& jobs, const qtt_solve_params*
       QCHECK(cudaStreamCreateWithFlags(&lanes[l].stream, cudaStreamNonBlocking));
       QCHECK(cudaMallocHost(&lanes[l].pinned, 1 << 16));
     }
-  } else {
-    lanes[0] = ctx->lane0;
   }
+  // one lane: the context's own (its stream, arena and profile buffer)
+  auto lane_of = [&](int l) { return nl > 1 ? &lanes[l] : &ctx->lane0; };
   std::atomic<int> next{0};
   struct LaneCount {
     qtt_ctx* c;
@@ -2452,7 +2740,7 @@ void run_jobs(qtt_ctx* ctx, std::vector<SolveJob>& jobs, const qtt_solve_params*
       Ev[J.load] = 1.0;
       try {
         J.status = DISPATCH(ctx, solve_impl, ctx, J.dC, J.S, J.Sh, J.G, J.dC->C0, Ev, p, J.sig,
-                            &J.inf, 0, &lanes[lane_id], keep ? &J.keep : nullptr);
+                            &J.inf, 0, lane_of(lane_id), keep ? &J.keep : nullptr);
       } catch (const QttError& ex) {
         J.status = ex.code;
         J.err = ex.what();
@@ -2468,6 +2756,12 @@ void run_jobs(qtt_ctx* ctx, std::vector<SolveJob>& jobs, const qtt_solve_params*
     for (auto& t : th) t.join();
     for (int l = 0; l < nl; ++l) {
       cudaStreamSynchronize(lanes[l].stream);
+      lanes[l].destroy_wait();
+      {
+        std::lock_guard<std::mutex> g(ctx->prof_mu);
+        lanes[l].prof.merge_into(ctx->prof);
+      }
+      lanes[l].prof.release_events();
       cudaStreamDestroy(lanes[l].stream);
       cudaFreeHost(lanes[l].pinned);
       ctx->arena.release(blocks[l]);
@@ -2696,9 +2990,21 @@ int qtt_ctx_set_jacobi(qtt_ctx_t ctx, double tol_scale, int max_sweeps_fp32) {
 }
 
 int qtt_ctx_set_contraction(qtt_ctx_t ctx, int mode) {
-  if (!ctx || (mode != QTT_CONTRACT_SIMT && mode != QTT_CONTRACT_TF32X3)) return QTT_EINVAL;
-  if (mode == QTT_CONTRACT_TF32X3 && ctx->prec != QTT_FP32) return QTT_EINVAL;
+  if (!ctx || (mode != QTT_CONTRACT_SIMT && mode != QTT_CONTRACT_TF32X3 &&
+               mode != QTT_CONTRACT_TC))
+    return QTT_EINVAL;
+  if (mode != QTT_CONTRACT_SIMT && ctx->prec != QTT_FP32) return QTT_EINVAL;
   ctx->contraction = mode;
+  return QTT_OK;
+}
+
+int qtt_ctx_set_factorization(qtt_ctx_t ctx, int mode) {
+  if (!ctx) return QTT_EINVAL;
+  if (mode != QTT_FACTOR_NATIVE && mode != QTT_FACTOR_FP64) {
+    ctx->err = "qtt_ctx_set_factorization: unknown mode";
+    return QTT_EINVAL;
+  }
+  ctx->factor = mode;
   return QTT_OK;
 }
 
@@ -2816,13 +3122,23 @@ extern "C" int qtt_tt_dot_noalloc(qtt_tt_t a, qtt_tt_t b, void* cuda_stream, dou
     if (a->ranks[k] > kNoAllocMaxRank || b->ranks[k] > kNoAllocMaxRank)
       return fail(QTT_EINVAL, "qtt_tt_dot_noalloc: TT rank above the maximum " +
                                   std::to_string(kNoAllocMaxRank));
+  // the work runs on the context's device; the caller's current device is
+  // restored on every return
+  int prev_dev = -1;
+  if (cudaGetDevice(&prev_dev) != cudaSuccess)
+    return fail(QTT_ECUDA, "qtt_tt_dot_noalloc: cudaGetDevice failed");
+  struct RestoreDevice {
+    int dev;
+    ~RestoreDevice() { cudaSetDevice(dev); }
+  } restore{prev_dev};
   if (cudaSetDevice(c->device) != cudaSuccess)
     return fail(QTT_ECUDA, "qtt_tt_dot_noalloc: cudaSetDevice failed");
   Cx<double>* base = nullptr;
   std::string err;
   const int rc = noalloc_scratch(&base, err);
   if (rc != QTT_OK) return fail(rc, err);
-  cudaStream_t st = (cudaStream_t)cuda_stream;
+  // NULL: the context's stream, which is ordered after the work that wrote a and b
+  cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : c->stream;
   Cx<double>* E = base;
   Cx<double>* F = base + kNoAllocRR;
   Cx<double>* EB = base + 2 * kNoAllocRR;

@@ -29,7 +29,8 @@ lib = C.CDLL(LIB_PATH)
 QTT_OK, QTT_EINVAL, QTT_ENOMEM, QTT_ECUDA, QTT_ENAN, QTT_ETIMEOUT = 0, -1, -2, -3, -4, -5
 QTT_WRANKCAP, QTT_WNOCONV = 1, 2
 QTT_FP64, QTT_FP32 = 0, 1
-QTT_CONTRACT_SIMT, QTT_CONTRACT_TF32X3 = 0, 1
+QTT_CONTRACT_SIMT, QTT_CONTRACT_TF32X3, QTT_CONTRACT_TC = 0, 1, 2
+QTT_FACTOR_NATIVE, QTT_FACTOR_FP64 = 0, 1
 MAXC = 64
 
 _p = C.c_void_p
@@ -71,6 +72,7 @@ _sig("qtt_tt_create", _i, [_p, _i, _ip, _ip, _dp, C.POINTER(_p)])
 _sig("qtt_tt_from_dense", _i, [_p, _i, _ip, _dp, _d, _i, C.POINTER(_p)])
 _sig("qtt_tt_shape", _i, [_p, _ip, _ip, _ip])
 _sig("qtt_tt_export", _i, [_p, _p, _dp])
+_sig("qtt_tt_to_dense", _i, [_p, _p, _dp])
 _sig("qtt_tt_free", None, [_p])
 _sig("qtt_op_create", _i, [_p, _i, _ip, _ip, _ip, _ip, _dp, C.POINTER(_p)])
 _sig("qtt_op_shape", _i, [_p, _ip, _ip, _ip, _ip, _ip])
@@ -100,6 +102,7 @@ _sig("qtt_ctx_set_concurrency", _i, [_p, _i])
 _sig("qtt_ctx_set_jacobi", _i, [_p, _d, _i])
 _sig("qtt_ctx_set_tt_svd", _i, [_p, _d])
 _sig("qtt_ctx_set_contraction", _i, [_p, _i])
+_sig("qtt_ctx_set_factorization", _i, [_p, _i])
 _sig("ls_solve_ceff", _i, [_p, _p, C.POINTER(SolveParams), _ip, _i, _dp, C.POINTER(SolveInfo)])
 _sig("ls_solve_batched", _i, [_p, _i, C.POINTER(_p), C.POINTER(SolveParams), _dp,
                              C.POINTER(SolveInfo)])
@@ -182,8 +185,12 @@ class Context:
         self.check(lib.qtt_ctx_set_jacobi(self.h, float(tol_scale), int(max_sweeps_fp32)))
 
     def set_contraction(self, mode: int):
-        """QTT_CONTRACT_SIMT or QTT_CONTRACT_TF32X3 (FP32 contexts)."""
+        """QTT_CONTRACT_SIMT, QTT_CONTRACT_TF32X3 or QTT_CONTRACT_TC (FP32 contexts)."""
         self.check(lib.qtt_ctx_set_contraction(self.h, int(mode)))
+
+    def set_factorization(self, mode: int):
+        """QTT_FACTOR_NATIVE or QTT_FACTOR_FP64 (FP32 contexts)."""
+        self.check(lib.qtt_ctx_set_factorization(self.h, int(mode)))
 
     def set_tt_svd(self, gram_threshold: float = 2e9):
         self.check(lib.qtt_ctx_set_tt_svd(self.h, float(gram_threshold)))
@@ -193,11 +200,12 @@ class Context:
 
     def profile(self, reset: bool = False):
         """{class: (launches, total_ms, algorithmic_flops)} for gemm, qr, svd."""
-        out = np.zeros(10)
+        out = np.zeros(11)
         self.check(lib.qtt_ctx_profile(self.h, int(reset), out.ctypes.data_as(_dp)))
         d = {name: (int(out[3 * i]), float(out[3 * i + 1]), float(out[3 * i + 2]))
              for i, name in enumerate(("gemm", "qr", "svd"))}
         self.last_sweeps = float(out[9])
+        self.last_tc_launches = int(out[10])
         return d
 
     # ------------------------------------------------------------ handles
@@ -257,6 +265,13 @@ class TT:
             out.append(z[off:off + n].reshape(ranks[k], dims[k], ranks[k + 1]).copy())
             off += n
         return out
+
+    def to_dense(self):
+        """qtt_tt_to_dense: the full tensor (complex128, shape dims)."""
+        dims, _ = self.shape()
+        buf = np.empty(2 * int(np.prod(dims)), dtype=np.float64)
+        self.ctx.check(lib.qtt_tt_to_dense(self.ctx.h, self.h, buf.ctypes.data_as(_dp)))
+        return buf.view(np.complex128).reshape(dims)
 
     def free(self):
         if self.h and self.ctx.h:

@@ -131,19 +131,22 @@ def laminate(n: int, layers: int = 2, stiff_first: bool = True) -> np.ndarray:
     return stiff.astype(np.uint8).reshape(1, 1, N)
 
 
-def laminate_with_fibres(n: int) -> np.ndarray:
-    """8 layers normal to x3 (stiff in layers 0, 2, 4, 6) plus a 4x4 lattice of
-    stiff fibres along x1 centred at ((j+1/2)/4, (k+1/2)/4 + 1/16) in (x2, x3),
-    radius 0.06 L. Shape (1, N, N): broadcast x1."""
+def laminate_with_fibres(n: int, radius: float = 0.06, offset=(0.0, 1.0 / 16),
+                         layer_offset: float = 0.0) -> np.ndarray:
+    """8 layers normal to x3 (stiff in layers 0, 2, 4, 6, the layer pattern
+    shifted by layer_offset along x3) plus a 4x4 lattice of stiff fibres along
+    x1 centred at ((j+1/2)/4 + offset[0], (k+1/2)/4 + offset[1]) in (x2, x3),
+    radius `radius` L. Shape (1, N, N): broadcast x1. The defaults are the
+    large QTT-only workload's geometry."""
     N = 1 << n
     c = _centres(N)
-    lay = ((np.floor(c * 8).astype(np.int64) % 2) == 0)
+    lay = ((np.floor((c - layer_offset) * 8).astype(np.int64) % 2) == 0)
     out = np.broadcast_to(lay[None, :], (N, N)).copy()
     for j in range(4):
         for k in range(4):
-            cy, cz = (j + 0.5) / 4, (k + 0.5) / 4 + 1.0 / 16
+            cy, cz = (j + 0.5) / 4 + offset[0], (k + 0.5) / 4 + offset[1]
             d2 = _periodic(c - cy)[:, None] ** 2 + _periodic(c - cz)[None, :] ** 2
-            out |= d2 <= 0.06 ** 2
+            out |= d2 <= radius ** 2
     return out.astype(np.uint8).reshape(1, N, N)
 
 
@@ -177,6 +180,23 @@ def lamfib256(n: int = 8) -> Workload:
     1e-6; r_max 128."""
     return Workload(f"lamfib{1 << n}", n, laminate_with_fibres(n), (1.0, 20.0), (0.3, 0.25),
                     1e-4, 1e-6, 128)
+
+
+def lamfib_family(n: int = 8, items: int = 64, base_seed: int = 2412):
+    """Laminate-with-fibres microstructures for batched C_eff: item i draws
+    (seed base_seed + i) the fibre radius U(0.045, 0.075) L, the lattice
+    offset U[0, 1/4)^2 and the layer offset U[0, 1/8); materials and solver
+    settings as lamfib256. Every item is periodic with period L/4 in x2 and
+    x3."""
+    out = []
+    for i in range(items):
+        rng = np.random.default_rng(base_seed + i)
+        r = float(rng.uniform(0.045, 0.075))
+        off = (float(rng.uniform(0.0, 0.25)), float(rng.uniform(0.0, 0.25)))
+        lo = float(rng.uniform(0.0, 0.125))
+        out.append(Workload(f"lamfib{1 << n}_{i}", n, laminate_with_fibres(n, r, off, lo),
+                            (1.0, 20.0), (0.3, 0.25), 1e-4, 1e-6, 128))
+    return out
 
 
 def by_name(name: str) -> Workload:

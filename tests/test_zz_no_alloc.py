@@ -6,6 +6,7 @@ so that a run stopping at the first failure has run every other test."""
 import numpy as np
 import pytest
 
+from oracle import qtt as oq
 from tests._helpers import random_tt
 
 pytestmark = pytest.mark.gpu
@@ -23,13 +24,20 @@ def test_noalloc_dot_matches_dot_twice(Q, precision):
     rng = np.random.default_rng(11)
     dims = [6] + [2] * 9
     ranks = [1, 6, 12, 24, 48, 64, 40, 16, 8, 4, 1]
-    a = ctx.tt(random_tt(rng, dims, ranks))
-    b = ctx.tt(random_tt(rng, dims, [1, 5, 10, 20, 40, 64, 32, 16, 8, 2, 1]))
+    ac = random_tt(rng, dims, ranks)
+    bc = random_tt(rng, dims, [1, 5, 10, 20, 40, 64, 32, 16, 8, 2, 1])
+    if precision == "fp32":  # the values the FP32 context holds
+        ac = [c.astype(np.complex64).astype(np.complex128) for c in ac]
+        bc = [c.astype(np.complex64).astype(np.complex128) for c in bc]
+    a, b = ctx.tt(ac), ctx.tt(bc)
     tol = 1e-11 if precision == "fp64" else 1e-9
     ref = Q.qtt_tt_dot(ctx, a, b)
+    exact = np.vdot(oq.tt_full(ac).reshape(-1), oq.tt_full(bc).reshape(-1))
+    assert abs(ref - exact) <= tol * abs(exact)
     for _ in range(2):  # two calls in a row: the shared array keeps old data
         got = Q.qtt_tt_dot_noalloc(ctx, a, b)
         assert abs(got - ref) <= tol * abs(ref)
+        assert abs(got - exact) <= tol * abs(exact)
     # self inner product, then a different pair: no state leaks between calls
     assert abs(Q.qtt_tt_dot_noalloc(ctx, a, a) - Q.qtt_tt_dot(ctx, a, a)) <= tol * abs(
         Q.qtt_tt_dot(ctx, a, a))
