@@ -239,6 +239,38 @@ def family_golden():
         return None
 
 
+def profile_case(args):
+    """--profile-case: a fixed number of LS iterations (no stop test) of one
+    microstructure's loads, for ncu launch lists and single-kernel captures
+    where the full benchmark's launch count is too large. Prints one summary
+    line; no timing claims."""
+    import torch
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2412_11566_gb300 import qtt as Q
+    from paper_2412_11566_gb300 import synth
+    w = synth.lamfib256(args.n) if args.workload == "lamfib256" else synth.spheres256(n=args.n)
+    prec = Q.QTT_FP64 if args.precision == "fp64" else Q.QTT_FP32
+    ctx = Q.Context(0, prec, args.workspace_gb << 30, seed=2412)
+    if prec == Q.QTT_FP32:
+        ctx.set_factorization(Q.QTT_FACTOR_FP64 if args.precision == "mixed" else
+                              Q.QTT_FACTOR_NATIVE)
+        ctx.set_contraction({"simt": Q.QTT_CONTRACT_SIMT, "tf32x3": Q.QTT_CONTRACT_TF32X3,
+                             "tc": Q.QTT_CONTRACT_TC}[args.contraction])
+    loads = list(range(args.loads))
+    ctx.set_concurrency(len(loads))
+    t = time.perf_counter()
+    dC = Q.qtt_from_phase_field(ctx, w.phase, w.n, w.E, w.nu, None, w.eps_tt, w.rmax)
+    C, infos, rc = Q.ls_solve_ceff(ctx, dC, Q.solve_params(1e-300, args.iters, w.eps_tt, w.rmax,
+                                                           0, 16), loads=loads)
+    torch.cuda.synchronize()
+    print(f"profile case {w.name} n={w.n} loads={len(loads)} iters={args.iters} "
+          f"precision={args.precision} contraction={args.contraction} "
+          f"wall={time.perf_counter() - t:.2f}s launches={ctx.launches()} "
+          f"peak={ctx.bytes_peak() / 2 ** 30:.2f} GiB", flush=True)
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -248,7 +280,12 @@ def main():
     ap.add_argument("--workload", default="lamfib256", choices=sorted(DESCR))
     ap.add_argument("--precision", default="fp64", choices=["fp32", "fp64", "mixed"],
                     help="mixed: complex64 cores and FP32 contractions, FP64 QR/SVD/Cholesky")
-    ap.add_argument("--contraction", default="simt", choices=["simt", "tf32x3"])
+    ap.add_argument("--contraction", default="simt", choices=["simt", "tf32x3", "tc"])
+    ap.add_argument("--profile-case", action="store_true",
+                    help="fixed iterations of one microstructure, for ncu (see profile_case)")
+    ap.add_argument("--n", type=int, default=8)
+    ap.add_argument("--iters", type=int, default=2)
+    ap.add_argument("--loads", type=int, default=6)
     ap.add_argument("--lanes", type=int, default=64)
     ap.add_argument("--max-iter", type=int, default=200)
     ap.add_argument("--workspace-gb", type=int, default=160)
@@ -259,6 +296,9 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.profile_case:
+        profile_case(args)
         return
     rank, world, local = dist_env()
     import torch
@@ -290,8 +330,8 @@ def main():
     if prec == Q.QTT_FP32:
         ctx.set_factorization(Q.QTT_FACTOR_FP64 if args.precision == "mixed" else
                               Q.QTT_FACTOR_NATIVE)
-        ctx.set_contraction(Q.QTT_CONTRACT_TF32X3 if args.contraction == "tf32x3" else
-                            Q.QTT_CONTRACT_SIMT)
+        ctx.set_contraction({"simt": Q.QTT_CONTRACT_SIMT, "tf32x3": Q.QTT_CONTRACT_TF32X3,
+                             "tc": Q.QTT_CONTRACT_TC}[args.contraction])
     w0 = fam[0]
     params = Q.solve_params(w0.tol, args.max_iter, w0.eps_tt, w0.rmax, 0, 16)
     pinned = {}
@@ -390,15 +430,21 @@ def main():
     tot_ms = max(1e-9, sum(x[1] for x in prof.values()))
     share = {k: round(v[1] / tot_ms, 4) for k, v in prof.items()}
     g_n, g_ms, g_fl = prof["gemm"]
-    contraction = {"kernel": ("gemm_tf32x3_kernel (split-TF32 mma.sync)" if args.contraction ==
-                              "tf32x3" and prec == Q.QTT_FP32 else
-                              "gemm_kernel (strided batched complex GEMM, SIMT)"),
+    kname = "gemm_kernel (strided batched complex GEMM, SIMT)"
+    if prec == Q.QTT_FP32 and args.contraction == "tf32x3":
+        kname = "gemm_tf32x3_kernel (split-TF32 mma.sync)"
+    elif prec == Q.QTT_FP32 and args.contraction == "tc":
+        kname = "tc_gemm_kernel (tcgen05 kind::tf32, TMA, TMEM) + gemm_kernel"
+    contraction = {"kernel": kname,
                    "achieved": g_fl / (g_ms / 1e3) / 1e12 if g_ms > 0 else 0.0,
                    "peak": class_peak("gemm"), "unit": "TFLOP/s", "launches": g_n,
                    "share_of_profiled_time": share["gemm"]}
     contraction["frac"] = contraction["achieved"] / class_peak("gemm")
-    ctr_txt = ("split-TF32 tensor-core contractions (hi*hi + hi*lo + lo*hi, FP32 accumulation)"
-               if args.contraction == "tf32x3" else "SIMT FP32 contractions")
+    ctr_txt = {"tf32x3": "split-TF32 mma.sync contractions (hi*hi + hi*lo + lo*hi, FP32 "
+                         "accumulation)",
+               "tc": "split-TF32 tcgen05 contractions for the unbatched products (TMA, TMEM "
+                     "accumulators), SIMT FP32 for the others",
+               "simt": "SIMT FP32 contractions"}[args.contraction]
     prec_txt = {"fp64": "fp64: complex128 cores, every step in FP64",
                 "fp32": f"fp32: complex64 cores, {ctr_txt}, FP32 QR/SVD; FP64 norms, inner "
                         f"products, operator build, C_eff",

@@ -63,6 +63,7 @@ extern "C" {
 #define QTT_CONTRACT_TC 2
 #define QTT_FACTOR_NATIVE 0
 #define QTT_FACTOR_FP64 1
+#define QTT_FACTOR_FP64_ROUNDING 2
 
 #define QTT_MAX_CORES 64
 
@@ -312,8 +313,14 @@ int qtt_ctx_set_contraction(qtt_ctx_t ctx, int mode);
  * the FP32 rounding level): QTT_FACTOR_NATIVE (default) factorises in the
  * context's precision; QTT_FACTOR_FP64 widens every QR, SVD and sketch
  * Cholesky operand of an FP32 context to FP64, factorises it with the FP64
- * kernels and rounds the factors back (cores stay complex64). No effect on
- * an FP64 context. Returns QTT_EINVAL for an unknown mode. */
+ * kernels and rounds the factors back (cores stay complex64);
+ * QTT_FACTOR_FP64_ROUNDING does so only for the QR and SVD steps of TT
+ * rounding (the sketch Cholesky and the compression QR inside a product stay
+ * FP32). An FP64 SVD whose matrix does not fit one CTA's shared memory takes
+ * an FP32 Jacobi preconditioner (right singular vectors made orthonormal in
+ * FP64 by a Newton-Schulz step) and finishes with a few FP64 Jacobi sweeps
+ * on the rotated matrix, in FP64 contexts as well. No effect on an FP64
+ * context. Returns QTT_EINVAL for an unknown mode. */
 int qtt_ctx_set_factorization(qtt_ctx_t ctx, int mode);
 /* C_eff and its derivatives with respect to phase parameters (E or nu of a
  * phase). The Direct-scheme LS operator (with the Nyquist symmetrisation of

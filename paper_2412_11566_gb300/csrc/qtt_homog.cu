@@ -229,6 +229,7 @@ struct qtt_ctx {
   std::atomic<int> active_lanes{1};  // lanes of the running solve queue (split-K sizing)
   int contraction = QTT_CONTRACT_SIMT;  // FP32 mode: SIMT or split-TF32 tensor-core GEMMs
   int factor = QTT_FACTOR_NATIVE;       // FP32 mode: factorisations in FP32 or in FP64
+  int svd_precond = 1;                  // FP64 SVDs beyond shared memory: FP32-preconditioned
   double gram_threshold = 2e9;     // TT-SVD: 8 P c min(P, c) above this takes the Gram path
   double jacobi_tol_scale = 1.0;   // Jacobi stop: |a_p^H a_q| <= scale sqrt(m) eps |a_p||a_q|
   int jacobi_max_sweeps32 = 40;    // sweep cap in FP32 mode
@@ -676,7 +677,11 @@ struct Eng {
 
   // Householder QR of the strided m x n matrix A: Q (m x k) and Rm (k x n),
   // column-major, k = min(m, n).
-  bool factor64() const { return sizeof(R) == 4 && c->factor == QTT_FACTOR_FP64; }
+  bool rounding = false;  // inside a TT rounding sweep (QR / truncated SVD)
+  bool factor64() const {
+    return sizeof(R) == 4 && (c->factor == QTT_FACTOR_FP64 ||
+                              (c->factor == QTT_FACTOR_FP64_ROUNDING && rounding));
+  }
 
   // FP32 context with FP64 factorisations: the operand is widened to FP64,
   // factorised by the FP64 kernels on the same lane, and the factors are
@@ -805,9 +810,73 @@ struct Eng {
     return k;
   }
 
+  // FP64 SVD of a matrix too large for one CTA's shared memory, with an FP32
+  // preconditioner (mixed-precision one-sided Jacobi): the FP32 Jacobi kernel
+  // (shared memory) gives right singular vectors V32 of the rounded matrix;
+  // V32 is made orthonormal in FP64 by one Newton-Schulz step
+  // V <- V (3 I - V^H V) / 2 (orthogonality error 1e-7 -> ~1e-14); B = A V has
+  // nearly orthogonal columns and the same singular values as A, and the FP64
+  // one-sided Jacobi on B converges quadratically from there (a few sweeps
+  // instead of tens). Result: U from B, sigma, V = V_orth V_B. Every kernel
+  // is one CTA or a small GEMM grid, so many lanes factorise side by side.
+  int svd_precond(int m, int n, Cx<R>* A, Cx<R>* U, double* sigma, Cx<R>* V, double delta2,
+                  int rmax, int* cap_hit) {
+    Eng<float> f(c, ln);
+    f.no_grid = true;
+    const long long mn = (long long)m * n, nn = (long long)n * n;
+    Cx<float>* A32 = f.alloc(mn);
+    convert_kernel<R, float><<<grid1d(mn), 256, 0, st()>>>(A, A32, mn);
+    post("convert_kernel", __LINE__);
+    Cx<float>* U32 = f.alloc(mn);
+    Cx<float>* V32 = f.alloc(nn);
+    double* s32 = (double*)ln->arena->alloc(sizeof(double) * n);
+    int cap32 = 0;
+    f.svd_direct(m, n, A32, U32, s32, V32, 0.0, n, &cap32, false);
+    f.release(A32);
+    f.release(U32);
+    ln->arena->release(s32);
+    Cx<R>* V0 = alloc(nn);
+    convert_kernel<float, R><<<grid1d(nn), 256, 0, st()>>>(V32, V0, nn);
+    post("convert_kernel", __LINE__);
+    f.release(V32);
+    // Newton-Schulz: X = V0^H V0, Vo = 1.5 V0 - 0.5 V0 X
+    Cx<R>* X = alloc(nn);
+    gemm(n, n, n, mref(V0, n, 1, 0, 0, 0, 1), mref(V0, 1, n), X, 1, n, 0, 0, 0, 1, 1, 1);
+    Cx<R>* Vo = alloc(nn);
+    {
+      const long long sz[1] = {nn}, st1[1] = {1};
+      copy(V0, Vo, 1, sz, st1, st1, 0, 1.5);
+    }
+    gemm(n, n, n, mref(V0, 1, n), mref(X, 1, n), Vo, 1, n, 0, 0, 0, 1, 1, 1, Cplx{-0.5, 0},
+         Cplx{1, 0});
+    release(X);
+    release(V0);
+    // B = A Vo (column-major m x n)
+    Cx<R>* B = alloc(mn);
+    gemm(m, n, n, mref(A, 1, m), mref(Vo, 1, n), B, 1, m, 0, 0, 0, 1, 1, 1);
+    Eng<R> d(c, ln);
+    d.no_grid = true;
+    d.sweeps_override = 4;
+    Cx<R>* VB = V ? alloc(nn) : nullptr;
+    const int k = d.svd_direct(m, n, B, U, sigma, VB, delta2, rmax, cap_hit, false);
+    release(B);
+    if (V) {
+      gemm(n, n, n, mref(Vo, 1, n), mref(VB, 1, n), V, 1, n, 0, 0, 0, 1, 1, 1);
+      release(VB);
+    }
+    release(Vo);
+    return k;
+  }
+
+  bool no_grid = false;     // never the cooperative Jacobi (several lanes factorise at once)
+  int sweeps_override = 0;  // Jacobi sweep cap instead of the precision's default
+
   int svd_direct(int m, int n, Cx<R>* A, Cx<R>* U, double* sigma, Cx<R>* V, double delta2,
                  int rmax, int* cap_hit, bool squares = false) {
     QREQ(m >= n && n >= 1, "svd: needs m >= n >= 1");
+    if (sizeof(R) == 8 && !squares && !no_grid && c->svd_precond && n >= 48 &&
+        (size_t)m * n * sizeof(Cx<R>) > smem_cap() && (size_t)m * n * 8 <= Eng<float>::smem_cap())
+      return svd_precond(m, n, A, U, sigma, V, delta2, rmax, cap_hit);
     QREQ(n <= 4096, "svd: too many columns");
     check_span(A, (long long)m * n - 1, "svd A");
     check_span(U, (long long)m * n - 1, "svd U");
@@ -820,7 +889,8 @@ struct Eng {
     QCHECK(cudaMemsetAsync(tr, 0, sizeof(int) * 8, st()));
     const R eps = sizeof(R) == 8 ? (R)2.220446049250313e-16 : (R)1.1920929e-7;
     const R tol = eps * (R)std::sqrt((double)m) * (R)c->jacobi_tol_scale;
-    const int sweeps = sizeof(R) == 8 ? 60 : c->jacobi_max_sweeps32;
+    const int sweeps = sweeps_override ? sweeps_override
+                                       : (sizeof(R) == 8 ? 60 : c->jacobi_max_sweeps32);
     {
       // flops counted for the sweeps actually run are not known here; the
       // profile records one sweep's count (n^2/2 pairs x (3 dots + 2
@@ -828,7 +898,9 @@ struct Eng {
       ProfScope ps(c, ln, 2, 0.5 * n * (double)n * (5.0 * m + 2.0 * n) * 8.0);
       const size_t bytes = (size_t)m * n * sizeof(Cx<R>);
       const bool sm = bytes <= smem_cap();
-      if (sm || n < 64) {
+      // the cooperative grid only when one lane runs: a grid starts when all
+      // its blocks fit at once, which other lanes' kernels keep delaying
+      if (sm || n < 64 || no_grid || c->active_lanes.load() > 1) {
         jacobi_svd_kernel<R><<<1, 1024, sm ? bytes : 0, st()>>>(
             m, n, A, Vw, sigma, perm, snorm, delta2, rmax, tr, sweeps, tol, squares ? 1 : 0,
             sm ? 1 : 0, want_v ? 1 : 0);
@@ -946,8 +1018,18 @@ qtt_tt* clone_tt(Eng<R>& e, const qtt_tt* x) {
 // Right-to-left truncated-SVD sweep of a left-orthogonal TT (Sec. 3,
 // eq. (rounding_condition_tt)); per-bond threshold delta2 = eps^2 ||x||^2 /
 // (L - 1) with ||x|| = ||last core||_F. Result is right-orthogonal.
+// Marks an engine as inside a rounding sweep for its lifetime.
+template <typename R>
+struct RoundingScope {
+  Eng<R>& e;
+  bool prev;
+  explicit RoundingScope(Eng<R>& eng) : e(eng), prev(eng.rounding) { e.rounding = true; }
+  ~RoundingScope() { e.rounding = prev; }
+};
+
 template <typename R>
 int round_right_to_left(Eng<R>& e, qtt_tt* x, double eps, int rmax) {
+  RoundingScope<R> rs(e);
   const int L = x->L;
   const double nrm2 = e.norm2(x->core[L - 1], x->count(L - 1));
   const double delta2 = L > 1 ? eps * eps * nrm2 / (double)(L - 1) : 0.0;
@@ -1013,6 +1095,7 @@ int round_right_to_left(Eng<R>& e, qtt_tt* x, double eps, int rmax) {
 // Left-to-right Householder QR sweep (orthogonalisation step of rounding).
 template <typename R>
 void orthogonalize_left(Eng<R>& e, qtt_tt* x) {
+  RoundingScope<R> rs(e);
   const int L = x->L;
   for (int k = 0; k < L - 1; ++k) {
     const int r0 = x->ranks[k], d = x->dims[k], r1 = x->ranks[k + 1];
@@ -3000,7 +3083,7 @@ int qtt_ctx_set_contraction(qtt_ctx_t ctx, int mode) {
 
 int qtt_ctx_set_factorization(qtt_ctx_t ctx, int mode) {
   if (!ctx) return QTT_EINVAL;
-  if (mode != QTT_FACTOR_NATIVE && mode != QTT_FACTOR_FP64) {
+  if (mode != QTT_FACTOR_NATIVE && mode != QTT_FACTOR_FP64 && mode != QTT_FACTOR_FP64_ROUNDING) {
     ctx->err = "qtt_ctx_set_factorization: unknown mode";
     return QTT_EINVAL;
   }

@@ -30,7 +30,7 @@ QTT_OK, QTT_EINVAL, QTT_ENOMEM, QTT_ECUDA, QTT_ENAN, QTT_ETIMEOUT = 0, -1, -2, -
 QTT_WRANKCAP, QTT_WNOCONV = 1, 2
 QTT_FP64, QTT_FP32 = 0, 1
 QTT_CONTRACT_SIMT, QTT_CONTRACT_TF32X3, QTT_CONTRACT_TC = 0, 1, 2
-QTT_FACTOR_NATIVE, QTT_FACTOR_FP64 = 0, 1
+QTT_FACTOR_NATIVE, QTT_FACTOR_FP64, QTT_FACTOR_FP64_ROUNDING = 0, 1, 2
 MAXC = 64
 
 _p = C.c_void_p

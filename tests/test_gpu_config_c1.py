@@ -7,8 +7,12 @@ a matrix E 1 (nu 0.3 both), load e11, stop tolerance 1e-6, eps_tt 1e-8.
     iteration cannot reach 1e-6: the converged dense strain of this geometry
     has QTT rank 354 at eps 1e-8 (245 at 1e-4), measured from the dense
     oracle's solution, so both sides level off at the cap's truncation error
-    (a residual of ~3e-2); the comparison is therefore taken after a fixed
-    number of iterations.
+    (a residual of ~3e-2). The cap cuts from the first iteration on (the
+    Green TTO alone has rank 240 here), inside a flat part of the spectrum:
+    which 64 directions survive then depends on rounding-level differences,
+    and the two sides drift apart over the iterations (measured on the GPU:
+    6e-9 in sigma_bar after 2 iterations, 1 % in the residual after 8). The
+    comparison is taken after the first iteration.
   * The same geometry and settings at 16^3 (n = 4), where r_max 128 is the
     full rank of every bond: converged to 1e-6 through the public path
     (operators built on the device from the phase field), C_eff column e11
@@ -38,12 +42,13 @@ def test_c1_vs_qtt_oracle(Q):
     S, Sh = oq.sfft_operator(w.n), oq.sfft_operator(w.n, adjoint=True)
     C0 = dense.stiffness_voigt(*lam0)
     Ev = np.eye(6)[0]
-    m = 8
+    m = 1
     ref = oq.ls_solve(dC, G, S, Sh, Ev, w.n, 1e-300, w.eps_tt, w.rmax, max_iter=m, lame0=lam0,
                       seed=SEED)
-    # a stop tolerance between the residuals of iterations m-1 and m: both
-    # sides stop after exactly m iterations
-    tol = float(np.sqrt(ref["history"][m - 2] * ref["history"][m - 1]))
+    # a stop tolerance above the first residual (0.36): both sides stop after
+    # the first iteration
+    assert ref["history"][0] < 0.5
+    tol = 0.5
     ctx = Q.Context(0, Q.QTT_FP64, 8 << 30, seed=SEED)
     try:
         dc, dd = to_lib_op(dC)
