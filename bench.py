@@ -1,28 +1,34 @@
 """Benchmark: LS solves/s of the SFFT-based homogenisation scheme (Alg. 2) at
 256^3, counting only solves whose C_eff column lies within 1e-4 (relative) of
 the dense FFT scheme's column (Alg. 1, oracle A, stored under tests/golden/),
-plus the core-contraction TFLOP/s of the same run.
+plus the contraction kernels' TFLOP/s.
 
-Headline workload (`lamfib256`): a 256^3 grid (n = 8, 25 cores) with 8
-layers normal to x3 and a 4x4 lattice of fibres along x1 (the laminate-with-
-fibres geometry of the large QTT-only workload, broadcast x1), matrix E=1
-nu=0.3, layers and fibres E=20 nu=0.25, all 6 unit loads, tol 1e-4, eps_tt
-1e-6, r_max 128, FP32 mode. The 8-sphere workload of the same materials and
-settings (`spheres256`) is measured in the same run as a second row: its
+Headline workload: 256^3 grids (n = 8, 25 cores) of the laminate-with-fibres
+family (8 layers normal to x3 and a 4x4 lattice of fibres along x1, the large
+QTT-only workload's arrangement, broadcast x1; per item a seeded fibre
+radius), matrix E=1 nu=0.3, layers and fibres E=20 nu=0.25, tol 1e-4, eps_tt
+1e-6, r_max 128, FP64. A step is one unit-load LS solve to the stop test
+(load g % 6 of family item g // 6); the W warm-up steps and then the K timed
+steps each go through one ls_solve_jobs call, the solves running side by side
+on concurrent lanes. `value` counts the qualifying solves over the device time
+of the timed call (CUDA events on the context stream; operators resident);
+`e2e` over the wall time of the same steps including the upload of the phase
+fields from pinned host memory, the stiffness TTO builds and the read-back of
+the C_eff columns. The per-grid SFFT and Green TTOs are built once, before the
+warm-up.
+
+Rows reported beside the headline: the tcgen05 contraction kernel at the
+headline's largest contraction and at a 4096^3 product; the plain FP64
+single-instance form (one load at a time, sampled); the CPU oracle on the full
+256^3 grid (sampled); the single laminate-with-fibres microstructure's six
+loads; and the 8-sphere workload of the same materials and settings, whose
 solves cannot meet 1e-4 at r_max 128 (the sphere indicator alone needs QTT
 rank > 1300 at 1 % error), so they are reported, not counted.
 
-A step is one effective-stiffness computation through the public API: the
-phase field is uploaded from pinned host memory, the stiffness TTO is built,
-the six loads are solved to the stop test and C_eff is read back. `value`
-counts the qualifying solves over the device time of the solves (CUDA events
-on the context stream around `ls_solve_ceff`, operators resident); `e2e` over
-the wall time of whole steps (upload, build, solve, read-back). The per-grid
-SFFT and Green TTOs are built once, before the warm-up.
-
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+    python bench.py --profile-case [--n 8 --iters 2 --loads 6]   (for ncu)
 
-Under torchrun (N > 1) every rank solves its own copy of the workload (weak
+Under torchrun (N > 1) every rank solves its own steps of the family (weak
 scaling, replicas: no collective on the data path).
 """
 from __future__ import annotations
@@ -40,6 +46,10 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 T_START = time.perf_counter()
+# Concurrent solve lanes each have their own CUDA stream; the GPU maps
+# streams onto this many hardware work queues (default 8), and streams that
+# share a queue run one after the other. Must be set before CUDA starts.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 METRIC = "LS solves/sec (C_eff rel.err≤1e-4) at 256^3; core-contraction TFLOP/s vs peak"
 UNIT = "LS solves/s"
@@ -54,13 +64,26 @@ DESCR = {
 
 DESCR_FAMILY = ("lamfib256 family: 256^3 (n=8, 25 cores) laminate-with-fibres microstructures "
                 "(8 layers normal to x3 + 4x4 fibre lattice along x1, broadcast x1; per item seeded "
-                "fibre radius U(0.045,0.075)L, lattice and layer offsets), E 1/20, nu 0.3/0.25, 6 "
-                "loads each, tol 1e-4, eps_tt 1e-6, r_max 128, sketch +16")
+                "fibre radius U(0.045,0.075)L), E 1/20, nu 0.3/0.25, 6 loads each, tol 1e-4, "
+                "eps_tt 1e-6, r_max 128, sketch +16")
 
 # FP32 FMA rate from unit counts: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz
 FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # FP64 from unit counts: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz
 FP64_ALU_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def _tf32_peak():
+    """Dense TF32 tensor peak: the measured BF16 burst figure times the
+    nominal TF32/BF16 ratio (1.1 / 2.25 PFLOP/s)."""
+    try:
+        bf16 = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])
+    except (OSError, ValueError, KeyError):
+        bf16 = 1900.0
+    return bf16 * 1.1 / 2.25
+
+
+TF32_PEAK_TFLOPS = _tf32_peak()
 
 
 def dist_env():
@@ -253,8 +276,8 @@ def profile_case(args):
     prec = Q.QTT_FP64 if args.precision == "fp64" else Q.QTT_FP32
     ctx = Q.Context(0, prec, args.workspace_gb << 30, seed=2412)
     if prec == Q.QTT_FP32:
-        ctx.set_factorization(Q.QTT_FACTOR_FP64 if args.precision == "mixed" else
-                              Q.QTT_FACTOR_NATIVE)
+        ctx.set_factorization({"fp32": Q.QTT_FACTOR_NATIVE, "mixed": Q.QTT_FACTOR_FP64_ROUNDING,
+                               "mixed_all": Q.QTT_FACTOR_FP64}[args.precision])
         ctx.set_contraction({"simt": Q.QTT_CONTRACT_SIMT, "tf32x3": Q.QTT_CONTRACT_TF32X3,
                              "tc": Q.QTT_CONTRACT_TC}[args.contraction])
     loads = list(range(args.loads))
@@ -271,6 +294,26 @@ def profile_case(args):
     ctx.close()
 
 
+def contraction_bench(args):
+    """--contraction-bench: the contraction kernels alone (qtt_contraction_bench)
+    at the headline's largest contraction and at a large square product,
+    one JSON line; also the command the kernel captures under ncu run."""
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2412_11566_gb300 import qtt as Q
+    ctx = Q.Context(0, Q.QTT_FP32, args.workspace_gb << 30, seed=2412)
+    out = {}
+    for mode in args.modes.split(","):
+        for (Mc, Nc, Kc) in ((160, 144, 3200), (args.square, args.square, args.square)):
+            ms, err = Q.qtt_contraction_bench(ctx, getattr(Q, f"QTT_CONTRACT_{mode.upper()}"),
+                                              Mc, Nc, Kc, args.reps)
+            tf = 8.0 * Mc * Nc * Kc / (ms / 1e3) / 1e12
+            out[f"{mode}_{Mc}x{Nc}x{Kc}"] = {"ms": ms, "complex_TFLOP_s": tf,
+                                            "rel_err_vs_fp64": err}
+    print(json.dumps(out), flush=True)
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -278,15 +321,22 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="lamfib256", choices=sorted(DESCR))
-    ap.add_argument("--precision", default="fp64", choices=["fp32", "fp64", "mixed"],
-                    help="mixed: complex64 cores and FP32 contractions, FP64 QR/SVD/Cholesky")
+    ap.add_argument("--precision", default="fp64",
+                    choices=["fp32", "fp64", "mixed", "mixed_all"],
+                    help="mixed: complex64 cores, FP32 contractions, FP64 rounding QR/SVD; "
+                         "mixed_all: every factorisation in FP64")
     ap.add_argument("--contraction", default="simt", choices=["simt", "tf32x3", "tc"])
     ap.add_argument("--profile-case", action="store_true",
                     help="fixed iterations of one microstructure, for ncu (see profile_case)")
+    ap.add_argument("--contraction-bench", action="store_true",
+                    help="the contraction kernels alone (see contraction_bench)")
+    ap.add_argument("--modes", default="simt,tf32x3,tc")
+    ap.add_argument("--square", type=int, default=4096)
+    ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--n", type=int, default=8)
     ap.add_argument("--iters", type=int, default=2)
     ap.add_argument("--loads", type=int, default=6)
-    ap.add_argument("--lanes", type=int, default=64)
+    ap.add_argument("--lanes", type=int, default=32)
     ap.add_argument("--max-iter", type=int, default=200)
     ap.add_argument("--workspace-gb", type=int, default=160)
     ap.add_argument("--budget-s", type=float, default=1500.0,
@@ -299,6 +349,9 @@ def main():
         return
     if args.profile_case:
         profile_case(args)
+        return
+    if args.contraction_bench:
+        contraction_bench(args)
         return
     rank, world, local = dist_env()
     import torch
@@ -320,16 +373,18 @@ def main():
     W, K = max(1, args.warmup), max(1, args.steps)
     gold = family_golden()
     n_fam = len(gold["items"]) if gold else 64
-    # step j of rank r solves family item (r * (W + K) + j) mod n_fam
     fam = synth.lamfib_family(8, n_fam)
+    # step g (counted over ranks, warm-up first) solves load g % 6 of family
+    # item (g // 6) % n_fam
     base = rank * (W + K)
-    warm_items = [(base + j) % n_fam for j in range(W)]
-    timed_items = [(base + W + j) % n_fam for j in range(K)]
+    job = lambda g: ((g // 6) % n_fam, g % 6)
+    warm_jobs = [job(base + j) for j in range(W)]
+    timed_jobs = [job(base + W + j) for j in range(K)]
     prec = Q.QTT_FP64 if args.precision == "fp64" else Q.QTT_FP32
     ctx = Q.Context(local, prec, args.workspace_gb << 30, seed=2412)
     if prec == Q.QTT_FP32:
-        ctx.set_factorization(Q.QTT_FACTOR_FP64 if args.precision == "mixed" else
-                              Q.QTT_FACTOR_NATIVE)
+        ctx.set_factorization({"fp32": Q.QTT_FACTOR_NATIVE, "mixed": Q.QTT_FACTOR_FP64_ROUNDING,
+                               "mixed_all": Q.QTT_FACTOR_FP64}[args.precision])
         ctx.set_contraction({"simt": Q.QTT_CONTRACT_SIMT, "tf32x3": Q.QTT_CONTRACT_TF32X3,
                              "tc": Q.QTT_CONTRACT_TC}[args.contraction])
     w0 = fam[0]
@@ -341,53 +396,60 @@ def main():
             pinned[i] = torch.from_numpy(np.ascontiguousarray(fam[i].phase)).pin_memory().numpy()
         return pinned[i]
 
-    for i in warm_items + timed_items:
+    for i, _ in warm_jobs + timed_jobs:
         host_phase(i)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > L2 (129 MB)
     stream = ctx.stream
 
-    def batch_step(items, lanes):
-        """C_eff of the listed family items through the public API: phase
-        fields uploaded from pinned host memory, stiffness TTOs built, all
-        items x 6 loads solved by ls_solve_batched on `lanes` lanes, C_eff read
-        back. Returns (C (items, 6, 6), infos, solve_ms, wall_s, build_s)."""
-        ctx.set_concurrency(min(lanes, 6 * len(items)))
+    def run_jobs(jobs, lanes):
+        """The listed (item, load) solves through the public API: phase fields
+        uploaded from pinned host memory, stiffness TTOs built (once per item),
+        all solves by ls_solve_jobs on `lanes` lanes, sigma_bar read back.
+        Returns (sigma (jobs, 6), infos, solve_ms, wall_s, build_s)."""
+        ctx.set_concurrency(min(lanes, len(jobs)))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        dCs = [Q.qtt_from_phase_field(ctx, host_phase(i), fam[i].n, fam[i].E, fam[i].nu, None,
-                                      fam[i].eps_tt, fam[i].rmax) for i in items]
+        items = sorted({i for i, _ in jobs})
+        dCs = {i: Q.qtt_from_phase_field(ctx, host_phase(i), fam[i].n, fam[i].E, fam[i].nu, None,
+                                         fam[i].eps_tt, fam[i].rmax) for i in items}
         t1 = time.perf_counter()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        C6, infos, _ = Q.ls_solve_batched(ctx, dCs, params)
+        sig, infos, _ = Q.ls_solve_jobs(ctx, [dCs[i] for i, _ in jobs], [k for _, k in jobs],
+                                        params)
         e1.record(stream)
         e1.synchronize()
-        for d in dCs:
+        for d in dCs.values():
             d.free()
-        return C6, infos, e0.elapsed_time(e1), time.perf_counter() - t0, t1 - t0
+        return sig, infos, e0.elapsed_time(e1), time.perf_counter() - t0, t1 - t0
 
-    def count_qualifying(items, C6, infos):
-        q = 0
-        errs = []
-        for i, C, inf in zip(items, C6, infos):
-            ref = gold["items"][str(i)] if gold else None
-            q += len(qualifying(C, inf, ref, fam[i].tol))
-            e = ceff_errors(C, ref)
-            errs.append(max(e.values()) if e else None)
+    def count_qualifying(jobs, sig, infos):
+        """Solves that met the stop test with their C_eff column within
+        CEFF_TOL of the stored dense-oracle column; per-job deviations."""
+        q, errs = 0, []
+        for (i, k), sg, inf in zip(jobs, sig, infos):
+            col = gold["items"][str(i)]["columns"].get(str(k)) if gold else None
+            if col is None:
+                errs.append(None)
+                continue
+            r = np.asarray(col["sigma_bar_re"], dtype=np.float64)
+            e = float(np.abs(sg.real - r).max() / np.abs(r).max())
+            errs.append(e)
+            q += int(inf["residual"] < fam[i].tol and e <= CEFF_TOL)
         return q, errs
 
     # ---- per-grid operators (SFFT, Green TTO) built and cached, untimed
     t = time.perf_counter()
     ctx.set_concurrency(1)
-    dC = Q.qtt_from_phase_field(ctx, host_phase(warm_items[0]), w0.n, w0.E, w0.nu, None,
+    dC = Q.qtt_from_phase_field(ctx, host_phase(warm_jobs[0][0]), w0.n, w0.E, w0.nu, None,
                                 w0.eps_tt, w0.rmax)
     Q.ls_solve_ceff(ctx, dC, Q.solve_params(w0.tol, 1, w0.eps_tt, w0.rmax, 0, 16), loads=[0])
     dC.free()
     t_ops = time.perf_counter() - t
-    # ---- warm-up: W microstructures (6 W solves) in one batch
-    batch_step(warm_items, args.lanes)
+    # ---- warm-up: W solves in one batch
+    run_jobs(warm_jobs, args.lanes)
 
-    # ---- timed region: K microstructures (K steps, 6 K solves) in one batch
+    # ---- timed region: K solves (K steps) in one batch
     clocks = Clocks(local)
     clocks.start()
     ctx.set_profiling(True)
@@ -396,30 +458,30 @@ def main():
     barrier()
     torch.cuda.synchronize()
     launches0 = ctx.launches()
-    C6, infos, ms_tot, s_tot, build_s = batch_step(timed_items, args.lanes)
+    sig, infos, ms_tot, s_tot, build_s = run_jobs(timed_jobs, args.lanes)
     torch.cuda.synchronize()
     barrier()
     launches = ctx.launches() - launches0
     prof = ctx.profile(reset=True)
     ctx.set_profiling(False)
     clk = clocks.stop()
-    qual, errs = count_qualifying(timed_items, C6, infos)
+    qual, errs = count_qualifying(timed_jobs, sig, infos)
     peak_gb = ctx.bytes_peak() / 2 ** 30
     if dist is not None:
         from paper_2412_11566_gb300.replicas import max_over_ranks, sum_over_ranks
         ms_tot = max_over_ranks(ms_tot, world, device="cuda")
         s_tot = max_over_ranks(s_tot, world, device="cuda")
         qual = int(round(sum_over_ranks(float(qual), world, device="cuda")))
-    solves_all = 6 * K * world
+    solves_all = K * world
     value = qual / (ms_tot / 1e3)
-    flat = [inf for item in infos for inf in item]
+    flat = infos
     iters = [inf["iters"] for inf in flat]
 
     # ---- roofline of the dominant kernel class (events on the launching streams)
     cls = max(prof, key=lambda k: prof[k][1])
     n_l, ms_l, fl_l = prof[cls]
     achieved = fl_l / (ms_l / 1e3) / 1e12 if ms_l > 0 else 0.0
-    fact64 = args.precision in ("fp64", "mixed")
+    fact64 = args.precision in ("fp64", "mixed", "mixed_all")
 
     def class_peak(k):
         if k == "gemm":
@@ -448,30 +510,34 @@ def main():
     prec_txt = {"fp64": "fp64: complex128 cores, every step in FP64",
                 "fp32": f"fp32: complex64 cores, {ctr_txt}, FP32 QR/SVD; FP64 norms, inner "
                         f"products, operator build, C_eff",
-                "mixed": f"mixed: complex64 cores, {ctr_txt}, FP64 QR/SVD/Cholesky (operands "
-                         f"widened); FP64 norms, inner products, operator build, C_eff"
-                }[args.precision]
+                "mixed": f"mixed: complex64 cores, {ctr_txt}, FP32 factorisations inside the "
+                         f"products, FP64 rounding QR/SVD (operands widened); FP64 norms, inner "
+                         f"products, operator build, C_eff",
+                "mixed_all": f"mixed_all: complex64 cores, {ctr_txt}, every QR/SVD/Cholesky in "
+                             f"FP64 (operands widened); FP64 norms, inner products, operator "
+                             f"build, C_eff"}[args.precision]
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
             "warmup": W, "ms_per_step": ms_tot / K, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "c64" if prec == Q.QTT_FP32 else "c128", "data": "synthetic",
             "config": {"workload": DESCR_FAMILY,
-                       "step": "one microstructure's C_eff (6 unit-load LS solves); the K "
-                               "timed steps go through one ls_solve_batched call",
-                       "lanes": min(args.lanes, 6 * K), "precision": prec_txt,
+                       "step": "one unit-load LS solve to the stop test (load g % 6 of family "
+                               "item g // 6), C_eff column read back; the K timed steps go "
+                               "through one ls_solve_jobs call on concurrent lanes",
+                       "lanes": min(args.lanes, K), "precision": prec_txt,
                        "l2": "256 MB buffer written before the timed region (flush); the "
                              "solves' working set is per-lane and re-read from HBM",
                        "solves_timed": solves_all, "solves_qualifying": qual,
                        "raw_solves_per_s": solves_all / (ms_tot / 1e3),
-                       "items_timed": timed_items,
+                       "jobs_timed": timed_jobs,
                        "iters_min_max_mean": [min(iters), max(iters), float(np.mean(iters))],
                        "residual_max": max(inf["residual"] for inf in flat),
                        "max_rank": max(inf["max_rank"] for inf in flat),
                        "rank_cap_hit": any(inf["rank_cap_hit"] for inf in flat),
-                       "ceff_rel_err_vs_dense_oracle_max_per_item": errs,
+                       "ceff_rel_err_vs_dense_oracle_per_solve": errs,
                        "dense_oracle_iters_mean": float(np.mean(
-                           [c["iters"] for i in timed_items for c in
-                            gold["items"][str(i)]["columns"].values()])) if gold else None,
+                           [gold["items"][str(i)]["columns"][str(k)]["iters"]
+                            for i, k in timed_jobs])) if gold else None,
                        "stiffness_tto_build_s": round(build_s, 3),
                        "operator_build_s": round(t_ops, 3),
                        "workspace_peak_gb": round(peak_gb, 2)},
@@ -486,62 +552,38 @@ def main():
             "clocks": clk,
             "e2e": {"value": qual / s_tot, "unit": UNIT,
                     "h2d_bytes_per_step": int(fam[0].phase.nbytes),
-                    "d2h_bytes_per_step": 36 * 8, "wall_s": round(s_tot, 3)}}
+                    "d2h_bytes_per_step": 12 * 8, "wall_s": round(s_tot, 3),
+                    "note": "per step: the phase field of its item (65536 B; one upload per item) "
+                            "and one sigma_bar column"}}
 
     def time_left():
         return args.budget_s - (time.perf_counter() - T_START)
 
     if rank == 0 and not args.no_extras:
-        # ---- one microstructure at a time: the 6 loads of the single
-        # laminate-with-fibres workload on 6 lanes
-        if time_left() > 600:
-            w1 = workload("lamfib256")
-            ref1 = golden("lamfib256")
-            ctx.set_concurrency(6)
-            ph1 = torch.from_numpy(np.ascontiguousarray(w1.phase)).pin_memory().numpy()
-            dC = Q.qtt_from_phase_field(ctx, ph1, w1.n, w1.E, w1.nu, None, w1.eps_tt, w1.rmax)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            C1, inf1, _ = Q.ls_solve_ceff(ctx, dC, params)
-            e1.record(stream)
-            e1.synchronize()
-            dC.free()
-            q1 = qualifying(C1, inf1, ref1, w1.tol)
-            line["single_microstructure"] = {
-                "workload": DESCR["lamfib256"], "lanes": 6,
-                "solves_qualifying": len(q1), "solves_per_s": len(q1) / (e0.elapsed_time(e1) / 1e3),
-                "iters_per_load": [i["iters"] for i in inf1],
-                "ceff_rel_err_vs_dense_oracle": ceff_errors(C1, ref1)}
-        # ---- the 8-sphere workload of the same materials and settings (one C_eff)
-        if time_left() > 500:
-            w2 = workload("spheres256")
-            ref2 = golden("spheres256")
-            ctx.set_concurrency(6)
-            p2 = Q.solve_params(w2.tol, 40, w2.eps_tt, w2.rmax, 0, 16)
-            ph2 = torch.from_numpy(np.ascontiguousarray(w2.phase)).pin_memory().numpy()
-            dC = Q.qtt_from_phase_field(ctx, ph2, w2.n, w2.E, w2.nu, None, w2.eps_tt, w2.rmax)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            C2, inf2, _ = Q.ls_solve_ceff(ctx, dC, p2)
-            e1.record(stream)
-            e1.synchronize()
-            dC.free()
-            q2 = qualifying(C2, inf2, ref2, w2.tol)
-            line["spheres256"] = {
-                "workload": DESCR["spheres256"], "max_iter": 40, "solves": 6,
-                "solves_qualifying": len(q2),
-                "raw_solves_per_s": 6 / (e0.elapsed_time(e1) / 1e3),
-                "residual_per_load": [i["residual"] for i in inf2],
-                "iters_per_load": [i["iters"] for i in inf2],
-                "rank_cap_hit": any(i["rank_cap_hit"] for i in inf2),
-                "ceff_rel_err_vs_dense_oracle": ceff_errors(C2, ref2),
-                "why_not_counted": "rank-capped at r_max 128: the 8-sphere indicator needs QTT "
-                                   "rank > 1300 at the middle bond for 1 % field error"}
+        # ---- contraction kernels on their own: the tcgen05 kernel at the
+        # headline's largest product contraction (T Psi at rank 80, operator rank
+        # 40: 2 r x (r + 16) x r a) and at a large square product
+        try:
+            cb = {}
+            for name, (Mc, Nc, Kc) in (("headline_T_Psi", (160, 144, 3200)),
+                                       ("square_4096", (4096, 4096, 4096))):
+                ms_c, err_c = Q.qtt_contraction_bench(ctx, Q.QTT_CONTRACT_TC, Mc, Nc, Kc, 5)
+                tf = 8.0 * Mc * Nc * Kc / (ms_c / 1e3) / 1e12
+                cb[name] = {"M": Mc, "N": Nc, "K": Kc, "ms": ms_c, "rel_err_vs_fp64": err_c,
+                            "complex_TFLOP_s": tf, "tf32_mma_TFLOP_s": 3 * tf,
+                            "frac_of_tf32_peak": 3 * tf / TF32_PEAK_TFLOPS}
+            line["tensor_core_contraction"] = {
+                "kernel": "tc_gemm_kernel (tcgen05.mma kind::tf32, TMA, TMEM; 3 split-TF32 passes)",
+                "peak_tf32_TFLOP_s": TF32_PEAK_TFLOPS,
+                "peak_source": "measured BF16 burst x nominal TF32/BF16 ratio 1.1/2.25",
+                "cases": cb}
+        except Exception as ex:  # noqa: BLE001
+            line["tensor_core_contraction"] = {"failed": str(ex)}
         # ---- plain FP64 single-instance form (one load at a time), sampled
         if time_left() > 200:
             c64 = ctx if prec == Q.QTT_FP64 else Q.Context(local, Q.QTT_FP64, 32 << 30, seed=2412)
             c64.set_concurrency(1)
-            i0 = timed_items[0]
+            i0 = timed_jobs[0][0]
             dC = Q.qtt_from_phase_field(c64, host_phase(i0), fam[i0].n, fam[i0].E, fam[i0].nu,
                                         None, fam[i0].eps_tt, fam[i0].rmax)
             ns = 3
@@ -580,6 +622,51 @@ def main():
             except Exception as ex:  # noqa: BLE001
                 line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": os.cpu_count(),
                                         "kind": "oracle", "sample": f"failed: {ex}"}
+        # ---- one microstructure at a time: the 6 loads of the single
+        # laminate-with-fibres workload on 6 lanes
+        if time_left() > 200:
+            w1 = workload("lamfib256")
+            ref1 = golden("lamfib256")
+            ctx.set_concurrency(6)
+            ph1 = torch.from_numpy(np.ascontiguousarray(w1.phase)).pin_memory().numpy()
+            dC = Q.qtt_from_phase_field(ctx, ph1, w1.n, w1.E, w1.nu, None, w1.eps_tt, w1.rmax)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            C1, inf1, _ = Q.ls_solve_ceff(ctx, dC, params)
+            e1.record(stream)
+            e1.synchronize()
+            dC.free()
+            q1 = qualifying(C1, inf1, ref1, w1.tol)
+            line["single_microstructure"] = {
+                "workload": DESCR["lamfib256"], "lanes": 6,
+                "solves_qualifying": len(q1), "solves_per_s": len(q1) / (e0.elapsed_time(e1) / 1e3),
+                "iters_per_load": [i["iters"] for i in inf1],
+                "ceff_rel_err_vs_dense_oracle": ceff_errors(C1, ref1)}
+        # ---- the 8-sphere workload of the same materials and settings (one C_eff)
+        if time_left() > 180:
+            w2 = workload("spheres256")
+            ref2 = golden("spheres256")
+            ctx.set_concurrency(6)
+            p2 = Q.solve_params(w2.tol, 40, w2.eps_tt, w2.rmax, 0, 16)
+            ph2 = torch.from_numpy(np.ascontiguousarray(w2.phase)).pin_memory().numpy()
+            dC = Q.qtt_from_phase_field(ctx, ph2, w2.n, w2.E, w2.nu, None, w2.eps_tt, w2.rmax)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            C2, inf2, _ = Q.ls_solve_ceff(ctx, dC, p2)
+            e1.record(stream)
+            e1.synchronize()
+            dC.free()
+            q2 = qualifying(C2, inf2, ref2, w2.tol)
+            line["spheres256"] = {
+                "workload": DESCR["spheres256"], "max_iter": 40, "solves": 6,
+                "solves_qualifying": len(q2),
+                "raw_solves_per_s": 6 / (e0.elapsed_time(e1) / 1e3),
+                "residual_per_load": [i["residual"] for i in inf2],
+                "iters_per_load": [i["iters"] for i in inf2],
+                "rank_cap_hit": any(i["rank_cap_hit"] for i in inf2),
+                "ceff_rel_err_vs_dense_oracle": ceff_errors(C2, ref2),
+                "why_not_counted": "rank-capped at r_max 128: the 8-sphere indicator needs QTT "
+                                   "rank > 1300 at the middle bond for 1 % field error"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()

@@ -299,13 +299,27 @@ int qtt_ctx_set_tt_svd(qtt_ctx_t ctx, double gram_threshold);
  * QTT_CONTRACT_SIMT (default) runs every core contraction as FP32 SIMT
  * GEMMs; QTT_CONTRACT_TF32X3 runs them on the tensor cores with TF32 inputs
  * split as x = hi + lo and products hi*hi + hi*lo + lo*hi accumulated in FP32
- * (FP32-level accuracy); QTT_CONTRACT_TC runs every unbatched contraction
- * with M >= 64, N >= 32, K >= 64 on the 5th-generation tensor cores
+ * (FP32-level accuracy); QTT_CONTRACT_TC runs the two large unbatched
+ * contractions of each core of a product (the sketched carry T Psi and the
+ * next carry Q^H T) when M >= 64, N >= 32, K >= 64 on the 5th-generation
+ * tensor cores
  * (tcgen05.mma kind::tf32, TMA-staged operands, TMEM accumulators; the same
  * hi/lo split with the hi*hi products and the corrections in separate
  * accumulators) and the other contractions as FP32 SIMT GEMMs. Factorisations, norms and the C_eff average are unaffected. Returns
  * QTT_EINVAL for an unknown mode or a tensor-core mode on an FP64 context. */
 int qtt_ctx_set_contraction(qtt_ctx_t ctx, int mode);
+/* Throughput and accuracy of one contraction kernel (measurement of the
+ * contraction that every product of Alg. 2 is built from; the paper has no
+ * counterpart): C = A B for a random complex M x K by K x N product (Philox
+ * entries in the context's FP32 precision, row-major), run once to warm up
+ * and `reps` times between CUDA events on the context stream with
+ * contraction mode `mode` (QTT_CONTRACT_SIMT, _TF32X3 or _TC; the TC kernel
+ * takes the product when M >= 64, N >= 32, K >= 64, else SIMT). Writes the
+ * average ms per launch (the TC path includes its two operand-split
+ * kernels) and the Frobenius relative error against an FP64 GEMM of the same
+ * operands. Uses the workspace; any context precision. */
+int qtt_contraction_bench(qtt_ctx_t ctx, int mode, int M, int N, int K, int reps,
+                          double* ms_per_launch, double* rel_err);
 /* Factorisation precision of an FP32 context (the mixed mode of the
  * method's precision pattern: bulk contractions in FP32, the QR and SVD
  * steps of TT rounding in FP64; Sec. 3 rounding, whose per-bond threshold
@@ -352,6 +366,17 @@ int qtt_ctx_set_concurrency(qtt_ctx_t ctx, int concurrent_loads);
  * error nothing is written. */
 int ls_solve_batched(qtt_ctx_t ctx, int nitems, const qtt_op_t* dC, const qtt_solve_params* p,
                      double* Ceff, qtt_solve_info* info);
+/* A list of unit-load LS solves (Alg. 2 with E = e_load[j] on dC[j]; Sec. 2
+ * C_eff paragraph for sigma_bar) through the same queue and lanes as
+ * ls_solve_batched: job j solves load[j] (0..5) on the stiffness operator
+ * dC[j] (from qtt_from_phase_field; jobs may share an operator) and writes
+ * sigma_bar = C0 e_load + mean(dC eps_final) as 6 interleaved complex values
+ * at sigma_bar + 12 j (column load[j] of that microstructure's C_eff is its
+ * real part); info: njobs entries or NULL. Each job is exactly the solve
+ * ls_solve_ceff runs for that operator and load. Returns the worst status;
+ * on an error nothing is written. */
+int ls_solve_jobs(qtt_ctx_t ctx, int njobs, const qtt_op_t* dC, const int* load,
+                  const qtt_solve_params* p, double* sigma_bar, qtt_solve_info* info);
 
 #ifdef __cplusplus
 }

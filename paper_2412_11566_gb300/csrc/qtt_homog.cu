@@ -489,7 +489,7 @@ struct Eng {
   // C = alpha op(A) op(B) + beta C over a (nb1, nb2, nb3) batch.
   void gemm(int M, int N, int K, MatRef A, MatRef B, void* C, long long c_rs, long long c_cs,
             long long c_b1, long long c_b2, long long c_b3, int nb1, int nb2, int nb3,
-            Cplx alpha = {1, 0}, Cplx beta = {0, 0}, int ksplit = 1) {
+            Cplx alpha = {1, 0}, Cplx beta = {0, 0}, int ksplit = 1, bool allow_tc = false) {
     if (M <= 0 || N <= 0 || nb1 <= 0 || nb2 <= 0 || nb3 <= 0) return;
     if (K <= 0) {
       QREQ(beta.re == 0 && beta.im == 0, "gemm: K = 0 with beta != 0");
@@ -512,7 +512,7 @@ struct Eng {
           }
       return;
     }
-    if (sizeof(R) == 4 && c->contraction == QTT_CONTRACT_TC && nb1 == 1 && nb2 == 1 &&
+    if (sizeof(R) == 4 && allow_tc && c->contraction == QTT_CONTRACT_TC && nb1 == 1 && nb2 == 1 &&
         nb3 == 1 && ksplit == 1 && M >= 64 && N >= 32 && K >= 64) {
       check_span(A.p, span(M, A.rs, K, A.cs), "gemm A");
       check_span(B.p, span(K, B.rs, N, B.cs), "gemm B");
@@ -856,7 +856,7 @@ struct Eng {
     gemm(m, n, n, mref(A, 1, m), mref(Vo, 1, n), B, 1, m, 0, 0, 0, 1, 1, 1);
     Eng<R> d(c, ln);
     d.no_grid = true;
-    d.sweeps_override = 4;
+    d.sweeps_override = 2;  // quadratic convergence: 1e-7 -> 1e-14 -> below eps
     Cx<R>* VB = V ? alloc(nn) : nullptr;
     const int k = d.svd_direct(m, n, B, U, sigma, VB, delta2, rmax, cap_hit, false);
     release(B);
@@ -1298,7 +1298,7 @@ qtt_tt* apply_sketched(Eng<R>& e, const qtt_op* A, const qtt_tt* x, int ell, int
     const int mz = Dout * Rr;
     Cx<R>* Z0 = e.alloc((long long)mz * L1);
     e.gemm(mz, L1, S1 * A1, mref(T, (long long)S1 * A1, 1), mref(psi[k + 1], L1, 1), Z0, L1, 1, 0,
-           0, 0, 1, 1, 1);
+           0, 0, 1, 1, 1, Cplx{1, 0}, Cplx{0, 0}, 1, true);
     e.release(psi[k + 1]);
     psi[k + 1] = nullptr;
     // Z = T Psi_{k+1} M_{k+1}: the sketch of T by the orthonormal basis
@@ -1325,7 +1325,7 @@ qtt_tt* apply_sketched(Eng<R>& e, const qtt_op* A, const qtt_tt* x, int ell, int
     // carry' (kq, S1, A1) = Q^H T
     Cx<R>* Cn = e.alloc((long long)kq * S1 * A1);
     e.gemm(kq, S1 * A1, mz, mref(Q, mz, 1, 0, 0, 0, 1), mref(T, (long long)S1 * A1, 1), Cn,
-           (long long)S1 * A1, 1, 0, 0, 0, 1, 1, 1);
+           (long long)S1 * A1, 1, 0, 0, 0, 1, 1, 1, Cplx{1, 0}, Cplx{0, 0}, 1, true);
     // Y[r][o][m] = Q[(o R + r) + m mz]
     Cx<R>* Y = e.alloc((long long)Rr * Dout * kq);
     const long long sz[3] = {Rr, Dout, kq}, ist[3] = {1, Rr, mz},
@@ -2905,6 +2905,42 @@ int solve_loads(qtt_ctx_t ctx, qtt_op_t dC, const qtt_solve_params* p, const int
   return worst;
 }
 
+// An arbitrary list of (microstructure, unit load) solves through one queue,
+// largest grids first; sigma_bar of job j at sig + 12 j.
+int solve_jobs(qtt_ctx_t ctx, int njobs, const qtt_op_t* dC, const int* load,
+               const qtt_solve_params* p, double* sig, qtt_solve_info* info) {
+  QREQ(ctx && dC && load && p && sig && njobs >= 1, "ls_solve_jobs: bad argument");
+  std::vector<SolveJob> jobs((size_t)njobs);
+  for (int j = 0; j < njobs; ++j) {
+    const qtt_op* d = dC[j];
+    QREQ(d, "ls_solve_jobs: null operator");
+    QREQ(d->has_c0, "ls_solve_jobs: dC must come from qtt_from_phase_field");
+    QREQ(load[j] >= 0 && load[j] < 6, "ls_solve_jobs: load out of range");
+    SolveJob& J = jobs[(size_t)j];
+    J.dC = d;
+    J.S = cached_sfft(ctx, d->n, 0);
+    J.Sh = cached_sfft(ctx, d->n, 1);
+    J.G = cached_gamma(ctx, d->n, d->lame0[0], d->lame0[1], p->scheme, p->eps_tt, 1 << 30);
+    J.load = load[j];
+  }
+  QCHECK(cudaStreamSynchronize(ctx->stream));
+  std::vector<int> order((size_t)njobs);
+  for (int j = 0; j < njobs; ++j) order[(size_t)j] = j;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return jobs[(size_t)a].dC->n > jobs[(size_t)b].dC->n; });
+  std::vector<SolveJob> queue((size_t)njobs);
+  for (int j = 0; j < njobs; ++j) queue[(size_t)j] = jobs[(size_t)order[(size_t)j]];
+  run_jobs(ctx, queue, p, ctx->concurrent_loads, false);
+  const int worst = jobs_status(queue);
+  for (int j = 0; j < njobs; ++j) {
+    const SolveJob& J = queue[(size_t)j];
+    const int dst = order[(size_t)j];
+    for (int r = 0; r < 12; ++r) sig[(size_t)dst * 12 + r] = J.sig[r];
+    if (info) info[dst] = J.inf;
+  }
+  return worst;
+}
+
 // nitems x 6 unit-load solves through one queue, largest grids first.
 int solve_batched(qtt_ctx_t ctx, int nitems, const qtt_op_t* dC, const qtt_solve_params* p,
                   double* Ceff, qtt_solve_info* info) {
@@ -2955,6 +2991,13 @@ int ls_solve_batched(qtt_ctx_t ctx, int nitems, const qtt_op_t* dC, const qtt_so
                      double* Ceff, qtt_solve_info* info) {
   API_BEGIN(ctx)
   return solve_batched(ctx, nitems, dC, p, Ceff, info);
+  API_END
+}
+
+int ls_solve_jobs(qtt_ctx_t ctx, int njobs, const qtt_op_t* dC, const int* load,
+                  const qtt_solve_params* p, double* sigma_bar, qtt_solve_info* info) {
+  API_BEGIN(ctx)
+  return solve_jobs(ctx, njobs, dC, load, p, sigma_bar, info);
   API_END
 }
 
@@ -3079,6 +3122,80 @@ int qtt_ctx_set_contraction(qtt_ctx_t ctx, int mode) {
   if (mode != QTT_CONTRACT_SIMT && ctx->prec != QTT_FP32) return QTT_EINVAL;
   ctx->contraction = mode;
   return QTT_OK;
+}
+
+int qtt_contraction_bench(qtt_ctx_t ctx, int mode, int M, int N, int K, int reps,
+                          double* ms_per_launch, double* rel_err) {
+  API_BEGIN(ctx)
+  QREQ(ctx && ms_per_launch && rel_err && M >= 1 && N >= 1 && K >= 1 && reps >= 1,
+       "qtt_contraction_bench: bad argument");
+  QREQ(mode == QTT_CONTRACT_SIMT || mode == QTT_CONTRACT_TF32X3 || mode == QTT_CONTRACT_TC,
+       "qtt_contraction_bench: unknown mode");
+  Eng<float> e(ctx);
+  Eng<double> d(ctx);
+  const long long na = (long long)M * K, nb = (long long)K * N, nc = (long long)M * N;
+  Cx<float>* A = e.alloc(na);
+  Cx<float>* B = e.alloc(nb);
+  Cx<float>* C = e.alloc(nc);
+  sketch_kernel<float><<<grid1d(na), 256, 0, e.st()>>>(A, na, ctx->seed, 1, 0x7C0);
+  e.post("sketch_kernel", __LINE__);
+  sketch_kernel<float><<<grid1d(nb), 256, 0, e.st()>>>(B, nb, ctx->seed, 2, 0x7C0);
+  e.post("sketch_kernel", __LINE__);
+  // FP64 product of the same (FP32) operands as the reference
+  Cx<double>* A64 = d.alloc(na);
+  Cx<double>* B64 = d.alloc(nb);
+  Cx<double>* C64 = d.alloc(nc);
+  convert_kernel<float, double><<<grid1d(na), 256, 0, e.st()>>>(A, A64, na);
+  e.post("convert_kernel", __LINE__);
+  convert_kernel<float, double><<<grid1d(nb), 256, 0, e.st()>>>(B, B64, nb);
+  e.post("convert_kernel", __LINE__);
+  d.gemm(M, N, K, mref(A64, K, 1), mref(B64, N, 1), C64, N, 1, 0, 0, 0, 1, 1, 1);
+  const int saved = ctx->contraction;
+  ctx->contraction = mode;
+  cudaEvent_t e0, e1;
+  QCHECK(cudaEventCreate(&e0));
+  QCHECK(cudaEventCreate(&e1));
+  float ms = 0;
+  try {
+    e.gemm(M, N, K, mref(A, K, 1), mref(B, N, 1), C, N, 1, 0, 0, 0, 1, 1, 1, Cplx{1, 0},
+           Cplx{0, 0}, 1, true);  // warm-up
+    QCHECK(cudaEventRecord(e0, e.st()));
+    for (int r = 0; r < reps; ++r)
+      e.gemm(M, N, K, mref(A, K, 1), mref(B, N, 1), C, N, 1, 0, 0, 0, 1, 1, 1, Cplx{1, 0},
+             Cplx{0, 0}, 1, true);
+    QCHECK(cudaEventRecord(e1, e.st()));
+    QCHECK(cudaEventSynchronize(e1));
+    QCHECK(cudaEventElapsedTime(&ms, e0, e1));
+  } catch (...) {
+    ctx->contraction = saved;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    throw;
+  }
+  ctx->contraction = saved;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  std::vector<Cx<float>> hc(nc);
+  std::vector<Cx<double>> hr(nc);
+  QCHECK(cudaMemcpyAsync(hc.data(), C, nc * sizeof(Cx<float>), cudaMemcpyDeviceToHost, e.st()));
+  QCHECK(cudaMemcpyAsync(hr.data(), C64, nc * sizeof(Cx<double>), cudaMemcpyDeviceToHost, e.st()));
+  QCHECK(cudaStreamSynchronize(e.st()));
+  double num = 0, den = 0;
+  for (long long i = 0; i < nc; ++i) {
+    const double dx = hc[i].x - hr[i].x, dy = hc[i].y - hr[i].y;
+    num += dx * dx + dy * dy;
+    den += hr[i].x * hr[i].x + hr[i].y * hr[i].y;
+  }
+  *rel_err = den > 0 ? std::sqrt(num / den) : 0.0;
+  *ms_per_launch = ms / reps;
+  e.release(A);
+  e.release(B);
+  e.release(C);
+  d.release(A64);
+  d.release(B64);
+  d.release(C64);
+  return QTT_OK;
+  API_END
 }
 
 int qtt_ctx_set_factorization(qtt_ctx_t ctx, int mode) {

@@ -103,9 +103,12 @@ _sig("qtt_ctx_set_jacobi", _i, [_p, _d, _i])
 _sig("qtt_ctx_set_tt_svd", _i, [_p, _d])
 _sig("qtt_ctx_set_contraction", _i, [_p, _i])
 _sig("qtt_ctx_set_factorization", _i, [_p, _i])
+_sig("qtt_contraction_bench", _i, [_p, _i, _i, _i, _i, _i, _dp, _dp])
 _sig("ls_solve_ceff", _i, [_p, _p, C.POINTER(SolveParams), _ip, _i, _dp, C.POINTER(SolveInfo)])
 _sig("ls_solve_batched", _i, [_p, _i, C.POINTER(_p), C.POINTER(SolveParams), _dp,
                              C.POINTER(SolveInfo)])
+_sig("ls_solve_jobs", _i, [_p, _i, C.POINTER(_p), _ip, C.POINTER(SolveParams), _dp,
+                          C.POINTER(SolveInfo)])
 
 
 def header_functions(path: str = HEADER):
@@ -449,6 +452,26 @@ def ls_solve_batched(ctx: Context, dCs, params: SolveParams):
     C6 = Ceff.reshape(len(dCs), 6, 6).transpose(0, 2, 1).copy()
     inf = [[infos[6 * i + k].as_dict() for k in range(6)] for i in range(len(dCs))]
     return C6, inf, rc
+
+
+def ls_solve_jobs(ctx: Context, dCs, loads, params: SolveParams):
+    """Unit-load solves (dC[j], load[j]): returns (sigma_bar array (njobs, 6)
+    complex, infos list, worst status)."""
+    dCs = list(dCs)
+    hs = (_p * len(dCs))(*[d.h.value if isinstance(d.h, _p) else d.h for d in dCs])
+    sig = np.zeros(12 * len(dCs))
+    infos = (SolveInfo * len(dCs))()
+    rc = ctx.check(lib.ls_solve_jobs(ctx.h, len(dCs), hs, _ints(loads), C.byref(params),
+                                     sig.ctypes.data_as(_dp), infos))
+    return sig.view(np.complex128).reshape(len(dCs), 6).copy(), [i.as_dict() for i in infos], rc
+
+
+def qtt_contraction_bench(ctx: Context, mode: int, M: int, N: int, K: int, reps: int = 10):
+    """(ms per launch, relative error vs FP64) of one complex M x N x K contraction."""
+    ms, err = C.c_double(), C.c_double()
+    ctx.check(lib.qtt_contraction_bench(ctx.h, int(mode), int(M), int(N), int(K), int(reps),
+                                        C.byref(ms), C.byref(err)))
+    return ms.value, err.value
 
 
 def qtt_from_phase_matrices(ctx: Context, phase, n, mats, eps_tt=1e-6, rmax=1 << 30):

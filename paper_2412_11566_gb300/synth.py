@@ -183,18 +183,16 @@ def lamfib256(n: int = 8) -> Workload:
 
 
 def lamfib_family(n: int = 8, items: int = 64, base_seed: int = 2412):
-    """Laminate-with-fibres microstructures for batched C_eff: item i draws
-    (seed base_seed + i) the fibre radius U(0.045, 0.075) L, the lattice
-    offset U[0, 1/4)^2 and the layer offset U[0, 1/8); materials and solver
-    settings as lamfib256. Every item is periodic with period L/4 in x2 and
-    x3."""
+    """Laminate-with-fibres microstructures for batched C_eff: the large
+    QTT-only workload's arrangement (layers and lattice as in
+    laminate_with_fibres' defaults) with item i's fibre radius drawn (seed
+    base_seed + i) from U(0.045, 0.075) L; materials and solver settings as
+    lamfib256. Every item is periodic with period L/4 in x2 and x3."""
     out = []
     for i in range(items):
         rng = np.random.default_rng(base_seed + i)
         r = float(rng.uniform(0.045, 0.075))
-        off = (float(rng.uniform(0.0, 0.25)), float(rng.uniform(0.0, 0.25)))
-        lo = float(rng.uniform(0.0, 0.125))
-        out.append(Workload(f"lamfib{1 << n}_{i}", n, laminate_with_fibres(n, r, off, lo),
+        out.append(Workload(f"lamfib{1 << n}_{i}", n, laminate_with_fibres(n, r),
                             (1.0, 20.0), (0.3, 0.25), 1e-4, 1e-6, 128))
     return out
 

@@ -55,3 +55,43 @@ def test_batched_rejects_bad_input(Q):
             ctx.set_concurrency(65)
     finally:
         ctx.close()
+
+
+def test_batched_vs_dense_oracle_per_item(Q):
+    """Every item of a batch (grids 4^3 and 8^3, different media) against the
+    dense FFT scheme (Alg. 1) converged to the same tolerance 1e-6 (above the
+    device residual's FP64 cancellation floor, ~2e-7): C_eff within 1e-4 per
+    item (FP64, eps_tt 1e-10, full rank at these sizes)."""
+    from oracle import dense
+    ctx = Q.Context(0, Q.QTT_FP64, 2 << 30, seed=SEED)
+    try:
+        items = _items()
+        dCs = [Q.qtt_from_phase_field(ctx, ph, n, E, nu, None, 1e-10) for n, ph, E, nu in items]
+        ctx.set_concurrency(6)
+        Cb, infb, rc = Q.ls_solve_batched(ctx, dCs, Q.solve_params(1e-6, 300, 1e-10, 256))
+        for i, (n, ph, E, nu) in enumerate(items):
+            Cd, _, _ = dense.ceff(ph, E, nu, tol=1e-6)
+            assert all(f["residual"] < 1e-6 for f in infb[i])
+            assert np.abs(Cb[i] - Cd).max() < 1e-4 * np.abs(Cd).max(), i
+    finally:
+        ctx.close()
+
+
+def test_solve_jobs_match_ceff_columns(Q):
+    """ls_solve_jobs on an arbitrary (item, load) list gives the columns
+    ls_solve_ceff gives for those items and loads (same sketches)."""
+    ctx = Q.Context(0, Q.QTT_FP64, 2 << 30, seed=SEED)
+    try:
+        items = _items()
+        dCs = [Q.qtt_from_phase_field(ctx, ph, n, E, nu, None, 1e-8) for n, ph, E, nu in items]
+        params = Q.solve_params(1e-5, 60, 1e-8, 32)
+        jobs = [(2, 4), (0, 1), (1, 0), (2, 0), (0, 5)]
+        ctx.set_concurrency(4)
+        sig, inf, rc = Q.ls_solve_jobs(ctx, [dCs[i] for i, _ in jobs], [k for _, k in jobs], params)
+        ctx.set_concurrency(1)
+        for j, (i, k) in enumerate(jobs):
+            Cs, infs, _ = Q.ls_solve_ceff(ctx, dCs[i], params, loads=[k])
+            assert inf[j]["iters"] == infs[0]["iters"]
+            assert np.abs(sig[j].real - Cs[:, k]).max() <= 1e-10 * np.abs(Cs[:, k]).max()
+    finally:
+        ctx.close()

@@ -2,7 +2,7 @@
 a matrix E 1 (nu 0.3 both), load e11, stop tolerance 1e-6, eps_tt 1e-8.
 
   * At 32^3 (n = 5, 16 cores) with r_max 64, on the oracle's own operators:
-    sigma_bar within 1e-10 of the QTT oracle (Alg. 2 with the same Philox
+    sigma_bar within 1e-8 of the QTT oracle (Alg. 2 with the same Philox
     sketches) after the same number of iterations. At this rank cap the
     iteration cannot reach 1e-6: the converged dense strain of this geometry
     has QTT rank 354 at eps 1e-8 (245 at 1e-4), measured from the dense
@@ -12,7 +12,10 @@ a matrix E 1 (nu 0.3 both), load e11, stop tolerance 1e-6, eps_tt 1e-8.
     which 64 directions survive then depends on rounding-level differences,
     and the two sides drift apart over the iterations (measured on the GPU:
     6e-9 in sigma_bar after 2 iterations, 1 % in the residual after 8). The
-    comparison is taken after the first iteration.
+    comparison is taken after the first iteration, and its bound is set by
+    the truncation's own condition: perturbing the oracle's Green cores by
+    1e-15 (relative, random) moves its first-iteration sigma_bar by 3.8e-9,
+    so no implementation can be held to 1e-10 here; the bound is 1e-8.
   * The same geometry and settings at 16^3 (n = 4), where r_max 128 is the
     full rank of every bond: converged to 1e-6 through the public path
     (operators built on the device from the phase field), C_eff column e11
@@ -57,8 +60,8 @@ def test_c1_vs_qtt_oracle(Q):
                                        ctx.op(gc, gd), C0, Ev,
                                        Q.solve_params(tol, 500, w.eps_tt, w.rmax))
         assert info["iters"] == m
-        assert abs(info["residual"] - ref["history"][-1]) < 1e-6 * ref["history"][-1]
-        assert np.abs(sig - ref["sigma_bar"]).max() < 1e-10 * np.abs(ref["sigma_bar"]).max()
+        assert abs(info["residual"] - ref["history"][-1]) < 1e-7 * ref["history"][-1]
+        assert np.abs(sig - ref["sigma_bar"]).max() < 1e-8 * np.abs(ref["sigma_bar"]).max()
     finally:
         ctx.close()
 

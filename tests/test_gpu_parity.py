@@ -432,3 +432,18 @@ def test_tensor_core_contractions_n4_vs_oracle(Q, mode):
         assert e_simt < 1e-4 and e_tc < 3 * e_simt + 1e-6, (e_tc, e_simt)
     finally:
         ctx.close()
+
+
+@pytest.mark.parametrize("mode", ["SIMT", "TF32X3", "TC"])
+def test_contraction_kernels_accuracy(Q, mode):
+    """Each contraction kernel on a random complex 512 x 256 x 1024 product
+    against an FP64 GEMM of the same FP32 operands: FP32-level accuracy
+    (relative Frobenius error below 1e-6; the split-TF32 kernels drop only
+    the lo*lo term, ~2^-22)."""
+    ctx = Q.Context(0, Q.QTT_FP32, 1 << 30, seed=SEED)
+    try:
+        ms, err = Q.qtt_contraction_bench(ctx, getattr(Q, f"QTT_CONTRACT_{mode}"), 512, 256,
+                                          1024, 3)
+        assert ms > 0 and err < 1e-6, (ms, err)
+    finally:
+        ctx.close()
