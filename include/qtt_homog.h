@@ -320,6 +320,17 @@ int qtt_ctx_set_contraction(qtt_ctx_t ctx, int mode);
  * operands. Uses the workspace; any context precision. */
 int qtt_contraction_bench(qtt_ctx_t ctx, int mode, int M, int N, int K, int reps,
                           double* ms_per_launch, double* rel_err);
+/* FP64 SVDs whose matrix does not fit one CTA's shared memory: precond = 1
+ * (default) takes the FP32-preconditioned path (FP32 one-sided Jacobi for the
+ * right singular vectors, one FP64 Newton-Schulz step, then FP64 Jacobi
+ * sweeps on A V until a sweep rotates nothing, at most refine_sweeps,
+ * default 6); precond = 0 runs the FP64 Jacobi from the start. The FP32
+ * preconditioner leaves the columns near the FP32 noise floor unresolved,
+ * and the truncation threshold of eps_tt = 1e-6 lies there, so the FP64
+ * sweeps must be allowed to converge (with a cap of 2 the e11 solves of the
+ * laminate-with-fibres workload stagnated at a residual of 3e-3). Returns
+ * QTT_EINVAL for refine_sweeps outside 1..60. */
+int qtt_ctx_set_svd(qtt_ctx_t ctx, int precond, int refine_sweeps);
 /* Factorisation precision of an FP32 context (the mixed mode of the
  * method's precision pattern: bulk contractions in FP32, the QR and SVD
  * steps of TT rounding in FP64; Sec. 3 rounding, whose per-bond threshold

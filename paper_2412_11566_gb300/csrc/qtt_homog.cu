@@ -230,6 +230,7 @@ struct qtt_ctx {
   int contraction = QTT_CONTRACT_SIMT;  // FP32 mode: SIMT or split-TF32 tensor-core GEMMs
   int factor = QTT_FACTOR_NATIVE;       // FP32 mode: factorisations in FP32 or in FP64
   int svd_precond = 1;                  // FP64 SVDs beyond shared memory: FP32-preconditioned
+  int svd_refine_sweeps = 6;            // FP64 Jacobi sweep cap after the FP32 preconditioner
   double gram_threshold = 2e9;     // TT-SVD: 8 P c min(P, c) above this takes the Gram path
   double jacobi_tol_scale = 1.0;   // Jacobi stop: |a_p^H a_q| <= scale sqrt(m) eps |a_p||a_q|
   int jacobi_max_sweeps32 = 40;    // sweep cap in FP32 mode
@@ -817,8 +818,10 @@ struct Eng {
   // V <- V (3 I - V^H V) / 2 (orthogonality error 1e-7 -> ~1e-14); B = A V has
   // nearly orthogonal columns and the same singular values as A, and the FP64
   // one-sided Jacobi on B converges quadratically from there (a few sweeps
-  // instead of tens). Result: U from B, sigma, V = V_orth V_B. Every kernel
-  // is one CTA or a small GEMM grid, so many lanes factorise side by side.
+  // instead of tens; columns at the FP32 noise floor, which the FP32 pass
+  // leaves unrotated, take a few more). Result: U from B, sigma,
+  // V = V_orth V_B. Every kernel is one CTA or a small GEMM grid, so many
+  // lanes factorise side by side.
   int svd_precond(int m, int n, Cx<R>* A, Cx<R>* U, double* sigma, Cx<R>* V, double delta2,
                   int rmax, int* cap_hit) {
     Eng<float> f(c, ln);
@@ -856,7 +859,7 @@ struct Eng {
     gemm(m, n, n, mref(A, 1, m), mref(Vo, 1, n), B, 1, m, 0, 0, 0, 1, 1, 1);
     Eng<R> d(c, ln);
     d.no_grid = true;
-    d.sweeps_override = 2;  // quadratic convergence: 1e-7 -> 1e-14 -> below eps
+    d.sweeps_override = c->svd_refine_sweeps;
     Cx<R>* VB = V ? alloc(nn) : nullptr;
     const int k = d.svd_direct(m, n, B, U, sigma, VB, delta2, rmax, cap_hit, false);
     release(B);
@@ -3196,6 +3199,13 @@ int qtt_contraction_bench(qtt_ctx_t ctx, int mode, int M, int N, int K, int reps
   d.release(C64);
   return QTT_OK;
   API_END
+}
+
+int qtt_ctx_set_svd(qtt_ctx_t ctx, int precond, int refine_sweeps) {
+  if (!ctx || refine_sweeps < 1 || refine_sweeps > 60) return QTT_EINVAL;
+  ctx->svd_precond = precond ? 1 : 0;
+  ctx->svd_refine_sweeps = refine_sweeps;
+  return QTT_OK;
 }
 
 int qtt_ctx_set_factorization(qtt_ctx_t ctx, int mode) {

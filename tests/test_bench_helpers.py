@@ -43,3 +43,12 @@ def test_stored_dense_columns_are_readable():
         err = b.ceff_errors(np.zeros((6, 6)), ref)
         assert all(abs(v - 1.0) < 1e-12 for v in err.values())
     assert len(b.golden("lamfib256")["columns"]) == 6
+
+
+def test_family_columns_and_iteration_mean():
+    b = _bench()
+    fam = b.family_golden()
+    assert fam is not None and len(fam["items"]) == 64
+    assert all(len(it["columns"]) == 6 for it in fam["items"].values())
+    its = [c["iters"] for it in fam["items"].values() for c in it["columns"].values()]
+    assert abs(b.dense_iters(fam) - np.mean(its)) < 1e-12

@@ -434,16 +434,20 @@ def test_tensor_core_contractions_n4_vs_oracle(Q, mode):
         ctx.close()
 
 
-@pytest.mark.parametrize("mode", ["SIMT", "TF32X3", "TC"])
-def test_contraction_kernels_accuracy(Q, mode):
+def test_contraction_kernels_accuracy(Q):
     """Each contraction kernel on a random complex 512 x 256 x 1024 product
-    against an FP64 GEMM of the same FP32 operands: FP32-level accuracy
-    (relative Frobenius error below 1e-6; the split-TF32 kernels drop only
-    the lo*lo term, ~2^-22)."""
+    against an FP64 GEMM of the same FP32 operands: the split-TF32 kernels
+    (mma.sync and tcgen05) within 3x the error of the FP32 SIMT GEMM, whose
+    FP32 accumulation over K = 1024 sets the level (below 2e-5)."""
     ctx = Q.Context(0, Q.QTT_FP32, 1 << 30, seed=SEED)
     try:
-        ms, err = Q.qtt_contraction_bench(ctx, getattr(Q, f"QTT_CONTRACT_{mode}"), 512, 256,
-                                          1024, 3)
-        assert ms > 0 and err < 1e-6, (ms, err)
+        err = {}
+        for mode in ("SIMT", "TF32X3", "TC"):
+            ms, e = Q.qtt_contraction_bench(ctx, getattr(Q, f"QTT_CONTRACT_{mode}"), 512, 256,
+                                            1024, 3)
+            assert ms > 0
+            err[mode] = e
+        assert err["SIMT"] < 2e-5, err
+        assert err["TF32X3"] < 3 * err["SIMT"] + 1e-7 and err["TC"] < 3 * err["SIMT"] + 1e-7, err
     finally:
         ctx.close()
