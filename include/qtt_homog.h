@@ -33,9 +33,16 @@
  * the message of the last failing call on a context.
  *
  * Precision: QTT_FP64 keeps cores in complex128 and runs every step in FP64.
- * QTT_FP32 keeps cores in complex64 with FP32 contractions and
- * factorisations; norms, inner products, the Green operator assembly and the
- * C_eff average stay FP64.
+ * QTT_FP32 keeps cores in complex64 with FP32 contractions (SIMT, or split
+ * TF32 on the tensor cores: qtt_ctx_set_contraction) and FP32 or FP64
+ * factorisations (qtt_ctx_set_factorization); norms, inner products, the
+ * Green operator assembly and the C_eff average stay FP64.
+ *
+ * Concurrency: the solvers run up to qtt_ctx_set_concurrency solves side by
+ * side, each on its own CUDA stream; the GPU maps streams onto
+ * CUDA_DEVICE_MAX_CONNECTIONS hardware queues (8 unless the environment sets
+ * it before CUDA starts; 32 at most), and streams sharing a queue run one
+ * after the other.
  */
 #ifndef QTT_HOMOG_H
 #define QTT_HOMOG_H
