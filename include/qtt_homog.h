@@ -68,6 +68,8 @@ extern "C" {
 #define QTT_CONTRACT_SIMT 0
 #define QTT_CONTRACT_TF32X3 1
 #define QTT_CONTRACT_TC 2
+#define QTT_SCHEME_DIRECT 0
+#define QTT_SCHEME_CENTERED 1
 #define QTT_FACTOR_NATIVE 0
 #define QTT_FACTOR_FP64 1
 #define QTT_FACTOR_FP64_ROUNDING 2
@@ -180,8 +182,11 @@ int qtt_sfft_operator(qtt_ctx_t ctx, int n, int adjoint, double eps, qtt_op_t* o
  * (lambda0, mu0) times the 15 degree-4 monomials of xi/|xi|; the monomial
  * fields are compressed by TT-SVD at eps_tt and rank cap rmax once per
  * (n, eps_tt, rmax) and context, and the matrix multiplies their first core
- * (relative error at most cond(matrix) eps_tt, cond ~7). scheme: 0 = Direct.
- * n in 1..9. */
+ * (relative error at most cond(matrix) eps_tt, cond ~7). scheme (App. A
+ * table of divergence operators): QTT_SCHEME_DIRECT (k = i q) or
+ * QTT_SCHEME_CENTERED (k = i sin q; eq. (orig_green_eshelby) with k = i s
+ * is the Direct closed form at s = sin q, so the same 15 monomials of s/|s|
+ * are compressed; s = 0 at Nyquist components). n in 1..9. */
 int qtt_gamma_operator(qtt_ctx_t ctx, int n, double lambda0, double mu0, int scheme,
                        double eps_tt, int rmax, qtt_op_t* out);
 
@@ -259,7 +264,8 @@ typedef struct {
   int max_iter;    /* iteration cap (QTT_WNOCONV when reached) */
   double eps_tt;   /* rounding accuracy of every step */
   int rmax;        /* rank cap of every rounding */
-  int scheme;      /* Green operator discretisation: 0 = Direct */
+  int scheme;      /* Green operator discretisation: QTT_SCHEME_DIRECT or
+                      QTT_SCHEME_CENTERED */
   int oversample;  /* sketch rank = rmax + oversample */
 } qtt_solve_params;
 

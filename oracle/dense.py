@@ -94,18 +94,43 @@ def green_voigt_direct(xi: np.ndarray, lam0: float, mu0: float) -> np.ndarray:
     return out
 
 
-def green_voigt_symmetrised(xi: np.ndarray, lam0: float, mu0: float, N) -> np.ndarray:
+SCHEMES = ("direct", "centered")
+
+
+def scheme_vector(xi: np.ndarray, N, scheme: str = "direct") -> np.ndarray:
+    """The real vector whose direction enters the Green operator of a
+    discretisation scheme (App. A table of divergence operators k(q),
+    q_a = 2 pi xi_a / N_a). Direct: k = i q, so the direction of xi. Centered:
+    k = i sin(q), so the direction of s_a = sin(2 pi xi_a / N_a); inserting
+    k = i s into eq. (orig_green_eshelby) gives k_i (.)^-1 k_l^* = s_i (.)^-1 s_l
+    and s C0 s as the acoustic tensor, i.e. the Direct closed form at s. At a
+    Nyquist component (|xi_a| = N_a / 2) s_a = sin(pi) = 0 exactly."""
+    xi = np.asarray(xi, dtype=np.float64)
+    if scheme == "direct":
+        return xi
+    if scheme == "centered":
+        Nv = np.broadcast_to(np.asarray(N, dtype=np.float64), (3,))
+        s = np.sin(2.0 * np.pi * xi / Nv)
+        return np.where(2.0 * np.abs(xi) == Nv, 0.0, s)
+    raise ValueError(scheme)
+
+
+def green_voigt_symmetrised(xi: np.ndarray, lam0: float, mu0: float, N,
+                            scheme: str = "direct") -> np.ndarray:
     """Gamma_V with the Nyquist symmetrisation of App. A: at modes with a
     component |xi_a| = N_a/2 (the Nyquist frequency of an even axis of N_a
     points) the value is the average of Gamma_V(xi) and Gamma_V at xi with
     those components negated (its aliased partner -xi mod N, Gamma being
     even); elsewhere Gamma_V(xi). N is one extent for a cubic grid or the
-    three extents (N_1, N_2, N_3); an axis of extent 1 has no Nyquist mode."""
+    three extents (N_1, N_2, N_3); an axis of extent 1 has no Nyquist mode.
+    scheme: "direct" (k = i q) or "centered" (k = i sin q), see
+    scheme_vector."""
     xi = np.asarray(xi, dtype=np.float64)
     half = np.broadcast_to(np.asarray(N, dtype=np.float64), (3,)) / 2.0
     nyq = (np.abs(xi) == half) & (half >= 1.0)
     flip = np.where(nyq, -xi, xi)
-    return 0.5 * (green_voigt_direct(xi, lam0, mu0) + green_voigt_direct(flip, lam0, mu0))
+    v, vf = scheme_vector(xi, N, scheme), scheme_vector(flip, N, scheme)
+    return 0.5 * (green_voigt_direct(v, lam0, mu0) + green_voigt_direct(vf, lam0, mu0))
 
 
 def frequencies(N: int) -> np.ndarray:
@@ -124,7 +149,7 @@ def _stiffness_field_apply(phase, Cs, field):
     return out
 
 
-def green_field(shape, lam0, mu0, slabs=None):
+def green_field(shape, lam0, mu0, slabs=None, scheme="direct"):
     """Gamma_V at every frequency of an (N1, N2, N3) grid, symmetrised at the
     Nyquist modes of each axis: a list over xi_1 of (N2, N3, 6, 6) slabs.
     Computed once per solve (it depends on the grid and C0 only). slabs: the
@@ -135,7 +160,7 @@ def green_field(shape, lam0, mu0, slabs=None):
     out = []
     for a in (range(N1) if slabs is None else slabs):
         xi = np.stack([np.full_like(x2, f1[a]), x2, x3], axis=-1)
-        out.append(green_voigt_symmetrised(xi, lam0, mu0, (N1, N2, N3)))
+        out.append(green_voigt_symmetrised(xi, lam0, mu0, (N1, N2, N3), scheme))
     return out
 
 
@@ -148,7 +173,7 @@ def _apply_green(tau_hat, G):
 
 
 def basic_scheme(phase, E, nu, E_voigt, tol=1e-6, max_iter=5000, lame0=None, workers=-1,
-                 eps0=None, green=None):
+                 eps0=None, green=None, scheme="direct"):
     """Alg. 1 (FFT-based homogenisation) on a dense (N1, N2, N3) phase grid.
 
     Iterates eps_{m+1} = E - IFFT[Gamma_hat FFT[(C - C0) eps_m]] from eps_0 = E
@@ -168,7 +193,7 @@ def basic_scheme(phase, E, nu, E_voigt, tol=1e-6, max_iter=5000, lame0=None, wor
     Eb = np.broadcast_to(Ev[:, None, None, None], (6,) + shape).astype(np.complex128)
     eps = Eb.copy() if eps0 is None else np.asarray(eps0, dtype=np.complex128).copy()
     normE = np.linalg.norm(Ev) * np.sqrt(float(np.prod(shape)))
-    G = green_field(shape, lam0, mu0) if green is None else green
+    G = green_field(shape, lam0, mu0, scheme=scheme) if green is None else green
     hist = []
     it = 0
     for it in range(1, max_iter + 1):
@@ -186,7 +211,7 @@ def basic_scheme(phase, E, nu, E_voigt, tol=1e-6, max_iter=5000, lame0=None, wor
     return dict(eps=eps, sigma_bar=sig, iters=it, history=hist, lame0=(lam0, mu0))
 
 
-def ceff(phase, E, nu, tol=1e-6, max_iter=5000, lame0=None, loads=range(6)):
+def ceff(phase, E, nu, tol=1e-6, max_iter=5000, lame0=None, loads=range(6), scheme="direct"):
     """C_eff column by column from unit Voigt loads E = e_k (Sec. 2). Returns
     (Ceff real 6x6 with column k = Re sigma_bar(e_k), max |Im sigma_bar|, iters)."""
     C = np.zeros((6, 6))
@@ -195,7 +220,7 @@ def ceff(phase, E, nu, tol=1e-6, max_iter=5000, lame0=None, loads=range(6)):
     for k in loads:
         e = np.zeros(6)
         e[k] = 1.0
-        r = basic_scheme(phase, E, nu, e, tol=tol, max_iter=max_iter, lame0=lame0)
+        r = basic_scheme(phase, E, nu, e, tol=tol, max_iter=max_iter, lame0=lame0, scheme=scheme)
         C[:, k] = r["sigma_bar"].real
         imag = max(imag, float(np.abs(r["sigma_bar"].imag).max()))
         iters.append(r["iters"])

@@ -435,7 +435,7 @@ def axis_frequencies_bitrev(n: int) -> np.ndarray:
     return np.where(k <= N // 2, k, k - N).astype(np.float64)
 
 
-def gamma_field_sfft(n: int, lam0: float, mu0: float) -> np.ndarray:
+def gamma_field_sfft(n: int, lam0: float, mu0: float, scheme: str = "direct") -> np.ndarray:
     """Dense Voigt Green field in the SFFT momentum convention (Sec. 4.3):
     G[I, J, k'1, k'2, k'3] = conj(Gamma_V[I, J](xi(rev k'1), xi(rev k'2), xi(rev k'3))),
     Nyquist-symmetrised as in App. A (see oracle.dense)."""
@@ -445,9 +445,10 @@ def gamma_field_sfft(n: int, lam0: float, mu0: float) -> np.ndarray:
     X2, X3 = np.meshgrid(f, f, indexing="ij")
     for a in range(N):
         xi = np.stack([np.full_like(X2, f[a]), X2, X3], axis=-1)
-        out[:, :, a] = np.moveaxis(dense.green_voigt_symmetrised(xi, lam0, mu0, N), (-2, -1),
+        out[:, :, a] = np.moveaxis(dense.green_voigt_symmetrised(xi, lam0, mu0, N, scheme),
+                                   (-2, -1),
                                    (0, 1))
-    return out   # real: conj is the identity for the Direct scheme
+    return out   # real for both schemes: conj is the identity
 
 
 def controlled_field_to_tto(F: np.ndarray, n: int, eps: float, rmax: int):
@@ -459,9 +460,11 @@ def controlled_field_to_tto(F: np.ndarray, n: int, eps: float, rmax: int):
     return [c0] + raise_tt(cores[1:])
 
 
-def gamma_qtt(n: int, lam0: float, mu0: float, eps: float, rmax: int = 1 << 30):
-    """Gamma_hat^0 as a raised TTO in the SFFT momentum convention."""
-    return controlled_field_to_tto(gamma_field_sfft(n, lam0, mu0), n, eps, rmax)
+def gamma_qtt(n: int, lam0: float, mu0: float, eps: float, rmax: int = 1 << 30,
+              scheme: str = "direct"):
+    """Gamma_hat^0 of a discretisation scheme ("direct" or "centered", App. A)
+    as a raised TTO in the SFFT momentum convention."""
+    return controlled_field_to_tto(gamma_field_sfft(n, lam0, mu0, scheme), n, eps, rmax)
 
 
 # ------------------------------------------------------------------ stiffness operator

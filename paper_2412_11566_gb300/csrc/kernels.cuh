@@ -1002,7 +1002,10 @@ __device__ void green_monomials_at(const double xi[3], double* m15) {
         for (int d = c; d < 3; ++d) m15[g++] = nn[a] * nn[b] * nn[c] * nn[d];
 }
 
-__global__ void green_monomials_kernel(Cx<double>* out, int n) {
+// scheme 0 (Direct, k = i q): the monomials of xi/|xi|. scheme 1 (Centered,
+// k = i sin q): of s/|s| with s_a = sin(2 pi xi_a / N), which is 0 at a
+// Nyquist component (sinpi of an integer is exact).
+__global__ void green_monomials_kernel(Cx<double>* out, int n, int scheme) {
   const long long N = 1ll << n, N3 = N * N * N;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N3;
        e += (long long)gridDim.x * blockDim.x) {
@@ -1015,6 +1018,10 @@ __global__ void green_monomials_kernel(Cx<double>* out, int n) {
       const bool isn = (2 * (long long)fabs(xi[a]) == N);
       nyq |= isn;
       xf[a] = isn ? -xi[a] : xi[a];
+      if (scheme == 1) {
+        xi[a] = isn ? 0.0 : sinpi(2.0 * xi[a] / (double)N);
+        xf[a] = isn ? 0.0 : xi[a];
+      }
     }
     double g[15], gf[15];
     green_monomials_at(xi, g);

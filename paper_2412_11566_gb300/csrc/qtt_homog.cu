@@ -246,7 +246,7 @@ struct qtt_ctx {
     std::vector<void*> cores;
     std::vector<int> ranks;
   };
-  std::map<std::tuple<int, double, int>, GreenMono> green_mono_cache;
+  std::map<std::tuple<int, double, int, int>, GreenMono> green_mono_cache;  // (n, eps, rmax, scheme)
   size_t esize() const { return prec == QTT_FP64 ? 16 : 8; }
 };
 
@@ -2101,17 +2101,18 @@ void green_coeffs(double lam0, double mu0, double* C) {
 // (lam0, mu0). The operator's relative error is at most cond(C) eps (C's
 // condition number is ~7 for the media of the workloads).
 qtt_op* build_gamma(qtt_ctx* c, int n, double lam0, double mu0, int scheme, double eps, int rmax) {
-  QREQ(scheme == 0, "only the Direct scheme (0) is implemented");
+  QREQ(scheme == QTT_SCHEME_DIRECT || scheme == QTT_SCHEME_CENTERED,
+       "gamma: scheme must be 0 (Direct) or 1 (Centered)");
   QREQ(n >= 1 && n <= 9, "gamma: n must be in 1..9");
   QREQ(mu0 > 0 && lam0 + 2 * mu0 > 0, "gamma: reference medium not positive definite");
   Eng<double> e(c);
   const double eps_m = eps;
-  const auto key = std::make_tuple(n, eps_m, rmax);
+  const auto key = std::make_tuple(n, eps_m, rmax, scheme);
   auto it = c->green_mono_cache.find(key);
   if (it == c->green_mono_cache.end()) {
     const long long N3 = 1ll << (3 * n);
     Cx<double>* F = e.alloc(15 * N3);
-    green_monomials_kernel<<<grid1d(N3), 256, 0, e.st()>>>(F, n);
+    green_monomials_kernel<<<grid1d(N3), 256, 0, e.st()>>>(F, n, scheme);
     e.post("green_monomials_kernel", __LINE__);
     std::vector<int> dims(1 + 3 * n, 2), ranks;
     dims[0] = 15;

@@ -31,6 +31,7 @@ QTT_WRANKCAP, QTT_WNOCONV = 1, 2
 QTT_FP64, QTT_FP32 = 0, 1
 QTT_CONTRACT_SIMT, QTT_CONTRACT_TF32X3, QTT_CONTRACT_TC = 0, 1, 2
 QTT_FACTOR_NATIVE, QTT_FACTOR_FP64, QTT_FACTOR_FP64_ROUNDING = 0, 1, 2
+QTT_SCHEME_DIRECT, QTT_SCHEME_CENTERED = 0, 1
 MAXC = 64
 
 _p = C.c_void_p

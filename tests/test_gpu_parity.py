@@ -454,3 +454,31 @@ def test_contraction_kernels_accuracy(Q):
         assert err["TF32X3"] < 3 * err["SIMT"] + 1e-7, err
     finally:
         ctx.close()
+
+
+def test_gamma_operator_centered_vs_oracle(Q, ctx64):
+    """The Centered-scheme Green TTO (App. A table, k = i sin q) built on the
+    device from the monomials of s/|s|, against the oracle's TT-SVD of its
+    Centered Green field, for two reference media."""
+    n = 3
+    for lam0, mu0 in [(3.5, 1.25), (0.7, 4.0)]:
+        op = Q.qtt_gamma_operator(ctx64, n, lam0, mu0, Q.QTT_SCHEME_CENTERED, 1e-12)
+        G = oq.tto_full(from_lib_op(op.cores(), op.shape()[3]))
+        ref = oq.tto_full(oq.gamma_qtt(n, lam0, mu0, 1e-12, scheme="centered"))
+        assert rel(G, ref) < 1e-9
+        direct = oq.tto_full(oq.gamma_qtt(n, lam0, mu0, 1e-12))
+        assert rel(G, direct) > 1e-3
+
+
+def test_ls_solve_centered_vs_dense_oracle(Q, ctx64):
+    """The full solve with the Centered scheme against the dense FFT scheme
+    with the same Green operator (Alg. 1), 8^3 sphere, loads e11 and e23."""
+    n = 3
+    ph = synth.centred_sphere(n, 0.3)
+    E, nu = (1.0, 10.0), (0.3, 0.3)
+    dC = Q.qtt_from_phase_field(ctx64, ph, n, E, nu, None, 1e-10)
+    p = Q.solve_params(1e-6, 500, 1e-9, 64, Q.QTT_SCHEME_CENTERED)
+    C, infos, rc = Q.ls_solve_ceff(ctx64, dC, p, loads=[0, 3])
+    Cd, imag, its = dense.ceff(ph, E, nu, tol=1e-6, loads=[0, 3], scheme="centered")
+    for k in (0, 3):
+        assert np.abs(C[:, k] - Cd[:, k]).max() < 1e-5 * np.abs(Cd).max()

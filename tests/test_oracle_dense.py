@@ -293,3 +293,50 @@ def test_broadcast_grid_equals_full_grid():
         assert np.allclose(a["sigma_bar"], b["sigma_bar"], rtol=0, atol=1e-12)
         assert np.allclose(a["history"], b["history"], rtol=1e-10, atol=1e-14)
         assert np.allclose(a["eps"][:, 0], b["eps"][:, 0], atol=1e-12)
+
+
+def green_from_definition_complex(k, lam0, mu0):
+    """eq. (orig_green_eshelby) for a complex divergence operator k (App. A
+    table): [k_i (k_m^* C0_mjkn k_n)^-1 k_l^*]_sym with a Hermitian acoustic
+    tensor, by a matrix inverse and explicit symmetrisation."""
+    C0 = dense.stiffness_tensor(lam0, mu0)
+    K = np.einsum("m,mjkn,n->jk", k.conj(), C0, k)
+    g = np.einsum("i,jk,l->ijkl", k, np.linalg.inv(K), k.conj())
+    g = 0.5 * (g + g.transpose(1, 0, 2, 3))
+    g = 0.5 * (g + g.transpose(0, 1, 3, 2))
+    return g
+
+
+def test_centered_green_equals_definition():
+    """Centered scheme, k_j = i sin(q_j): the definition with that complex k
+    is real and equals the Direct closed form at s = sin(q), which is how the
+    oracle evaluates it; Nyquist components give s_j = 0 exactly."""
+    rng = np.random.default_rng(11)
+    N = 16
+    for _ in range(20):
+        xi = rng.integers(-N // 2 + 1, N // 2 + 1, size=3).astype(float)
+        if not np.any(np.sin(2 * np.pi * xi / N) != 0):
+            continue
+        lam0, mu0 = rng.uniform(0.1, 5), rng.uniform(0.1, 5)
+        k = 1j * np.sin(2 * np.pi * xi / N)
+        ref = green_from_definition_complex(k, lam0, mu0)
+        assert np.abs(ref.imag).max() < 1e-12
+        got = dense.green_tensor_direct(dense.scheme_vector(xi, N, "centered"), lam0, mu0)
+        assert np.allclose(got, ref.real, atol=1e-12)
+    v = dense.scheme_vector(np.array([N / 2, 0.0, -N / 2]), N, "centered")
+    assert np.all(v == 0)
+
+
+def test_centered_scheme_homogeneous_and_distinct():
+    """The Centered scheme keeps the homogeneous-medium exactness (C_eff = C1)
+    and gives a different C_eff than the Direct scheme on an inclusion."""
+    n = 3
+    ph = np.zeros((8, 8, 8), dtype=np.uint8)
+    E, nu = (3.0, 3.0), (0.3, 0.3)
+    C, _, _ = dense.ceff(ph, E, nu, tol=1e-12, lame0=(1.0, 1.2), scheme="centered")
+    assert np.allclose(C, dense.stiffness_voigt(*dense.lame(3.0, 0.3)), atol=1e-10)
+    ph = synth.centred_sphere(n, 0.3)
+    E, nu = (1.0, 10.0), (0.3, 0.3)
+    Cc, _, _ = dense.ceff(ph, E, nu, tol=1e-10, loads=[0], scheme="centered")
+    Cd, _, _ = dense.ceff(ph, E, nu, tol=1e-10, loads=[0])
+    assert np.abs(Cc[:, 0] - Cd[:, 0]).max() > 1e-3 * np.abs(Cd[:, 0]).max()

@@ -430,3 +430,19 @@ def _sfft_check(n):
     x = np.arange(N) + 1j
     rev = [int(format(k, f"0{n}b")[::-1], 2) for k in range(N)]
     assert np.allclose(S @ x, (np.fft.ifft(x) * np.sqrt(N))[rev], atol=1e-12)
+
+
+def test_qtt_oracle_matches_dense_oracle_centered():
+    """Oracle B with the Centered-scheme Green TTO against oracle A with the
+    Centered scheme (App. A table), 4^3 sphere, load e11."""
+    n = 2
+    ph = synth.centred_sphere(n, 0.3)
+    E, nu = (1.0, 10.0), (0.3, 0.3)
+    lam0 = dense.reference_lame(E, nu)
+    dC = oq.stiffness_qtt(ph, n, E, nu, lam0, 1e-12)
+    G = oq.gamma_qtt(n, *lam0, 1e-12, scheme="centered")
+    S, Sh = oq.sfft_operator(n), oq.sfft_operator(n, adjoint=True)
+    Ev = np.eye(6)[0]
+    b = oq.ls_solve(dC, G, S, Sh, Ev, n, 1e-11, 1e-12, 1000, lame0=lam0, seed=2412)
+    a = dense.basic_scheme(ph, E, nu, Ev, tol=1e-11, scheme="centered")
+    assert np.abs(b["sigma_bar"] - a["sigma_bar"]).max() < 1e-8 * np.abs(a["sigma_bar"]).max()
