@@ -169,6 +169,20 @@ int qtt_from_phase_matrices(qtt_ctx_t ctx, const uint8_t* phase, const int shape
                             int nphase, const double* mats, double eps_tt, int rmax,
                             qtt_op_t* out);
 
+/* Applicability estimate (Sec. 5.2: compress the geometry at two
+ * discretisation orders to see its rank and how the rank grows): builds the
+ * stiffness operator (as qtt_from_phase_field, no rank cap, at eps_tt) of
+ * phase_a on a 2^n grid and of phase_b, the same geometry sampled on a
+ * 2^(n+1) grid (extents 1 or 2^n, resp. 2^(n+1)), and writes out[0] = its
+ * largest TT rank at n, out[1] = at n + 1, out[2] = the growth factor
+ * out[1] / out[0] per order, out[3] = out[0] * out[2]^(n_target - n), the
+ * rank the geometry would need at 2^n_target if it kept growing that way
+ * (about 1 for laminates, about 2 per order for spheres). The operators are
+ * freed. */
+int qtt_rank_estimate(qtt_ctx_t ctx, const uint8_t* phase_a, const int shape_a[3],
+                      const uint8_t* phase_b, const int shape_b[3], int n, int nphase,
+                      const double* E, const double* nu, double eps_tt, int n_target,
+                      double* out);
 /* The SFFT (Sec. 4.1-4.2): S = P_rev F+ per axis, F+[k, x] =
  * N^-1/2 exp(+2 pi i k x / N), P_rev reversing the n output bits, as a TTO
  * with an identity Voigt core; adjoint = 1 gives S^H = S^-1. Built on the

@@ -2652,6 +2652,34 @@ int qtt_from_phase_field(qtt_ctx_t ctx, const uint8_t* phase, const int shape[3]
   API_END
 }
 
+int qtt_rank_estimate(qtt_ctx_t ctx, const uint8_t* phase_a, const int shape_a[3],
+                      const uint8_t* phase_b, const int shape_b[3], int n, int nphase,
+                      const double* E, const double* nu, double eps_tt, int n_target,
+                      double* out) {
+  API_BEGIN(ctx)
+  QREQ(ctx && phase_a && phase_b && shape_a && shape_b && E && nu && out,
+       "qtt_rank_estimate: null argument");
+  QREQ(n_target >= n, "qtt_rank_estimate: n_target below n");
+  int ra = 0, rb = 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    qtt_op_t o = nullptr;
+    const int rc = qtt_from_phase_field(ctx, pass ? phase_b : phase_a, pass ? shape_b : shape_a,
+                                        n + pass, nphase, E, nu, nullptr, eps_tt, 1 << 30, &o);
+    if (rc < 0) throw QttError(rc, ctx->err);
+    int r = 1;
+    for (int k = 0; k <= o->L; ++k) r = std::max(r, o->ranks[k]);
+    free_op(o);
+    (pass ? rb : ra) = r;
+  }
+  const double g = (double)rb / (double)ra;
+  out[0] = ra;
+  out[1] = rb;
+  out[2] = g;
+  out[3] = ra * std::pow(g, (double)(n_target - n));
+  return QTT_OK;
+  API_END
+}
+
 int qtt_sfft_operator(qtt_ctx_t ctx, int n, int adjoint, double eps, qtt_op_t* out) {
   API_BEGIN(ctx)
   QREQ(ctx && out, "qtt_sfft_operator: null argument");
@@ -2801,8 +2829,11 @@ void run_jobs(qtt_ctx* ctx, std::vector<SolveJob>& jobs, const qtt_solve_params*
       std::lock_guard<std::mutex> g(ctx->arena.mu);
       for (auto& kv : ctx->arena.free_) freeb = std::max(freeb, kv.second);
     }
-    const size_t slice = ((freeb / nl) & ~(size_t)255) - 4096;
-    QREQ(freeb / nl > (64u << 20), "concurrent solves: workspace too small for the lanes");
+    // the lanes share 7/8 of the largest free block; the rest stays with the
+    // context for what the solves leave behind (kept final strains)
+    const size_t share = freeb - freeb / 8;
+    const size_t slice = ((share / nl) & ~(size_t)255) - 4096;
+    QREQ(share / nl > (64u << 20), "concurrent solves: workspace too small for the lanes");
     for (int l = 0; l < nl; ++l) {
       blocks[l] = ctx->arena.alloc(slice);
       arenas[l].init(blocks[l], slice);

@@ -82,6 +82,8 @@ _sig("qtt_op_free", None, [_p])
 _sig("qtt_from_phase_field", _i, [_p, C.POINTER(C.c_uint8), _ip, _i, _i, _dp, _dp, _dp, _d, _i,
                                    C.POINTER(_p)])
 _sig("qtt_sfft_operator", _i, [_p, _i, _i, _d, C.POINTER(_p)])
+_sig("qtt_rank_estimate", _i, [_p, C.POINTER(C.c_uint8), _ip, C.POINTER(C.c_uint8), _ip, _i, _i,
+                               _dp, _dp, _d, _i, _dp])
 _sig("qtt_gamma_operator", _i, [_p, _i, _d, _d, _i, _d, _i, C.POINTER(_p)])
 _sig("qtt_op_apply", _i, [_p, _p, _p, _d, _i, _i, _i, C.POINTER(_p)])
 _sig("sfft_apply", _i, [_p, _p, _d, _i, C.POINTER(_p)])
@@ -348,6 +350,24 @@ def qtt_from_phase_field(ctx: Context, phase, n, E, nu, lame0=None, eps_tt=1e-6,
                                        None if l0 is None else l0.ctypes.data_as(_dp),
                                        eps_tt, rmax, C.byref(h)))
     return Op(ctx, h)
+
+
+def qtt_rank_estimate(ctx: Context, phase_a, phase_b, n, E, nu, eps_tt=1e-6, n_target=None):
+    """Applicability estimate (Sec. 5.2): largest stiffness-TTO rank of the same
+    geometry at 2^n (phase_a) and 2^(n+1) (phase_b), the growth factor per
+    order and the rank extrapolated to 2^n_target. Returns a dict."""
+    a = np.ascontiguousarray(phase_a, dtype=np.uint8)
+    b = np.ascontiguousarray(phase_b, dtype=np.uint8)
+    Ea = np.ascontiguousarray(E, dtype=np.float64)
+    nua = np.ascontiguousarray(nu, dtype=np.float64)
+    out = np.zeros(4)
+    nt = n + 1 if n_target is None else n_target
+    ctx.check(lib.qtt_rank_estimate(ctx.h, a.ctypes.data_as(C.POINTER(C.c_uint8)),
+                                    _ints(list(a.shape)), b.ctypes.data_as(C.POINTER(C.c_uint8)),
+                                    _ints(list(b.shape)), n, len(Ea), Ea.ctypes.data_as(_dp),
+                                    nua.ctypes.data_as(_dp), eps_tt, nt, out.ctypes.data_as(_dp)))
+    return {"rank_n": int(out[0]), "rank_n1": int(out[1]), "growth": float(out[2]),
+            "rank_target": float(out[3]), "n_target": nt}
 
 
 def qtt_sfft_operator(ctx: Context, n, adjoint=False, eps=1e-14):

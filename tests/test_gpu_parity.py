@@ -482,3 +482,20 @@ def test_ls_solve_centered_vs_dense_oracle(Q, ctx64):
     Cd, imag, its = dense.ceff(ph, E, nu, tol=1e-6, loads=[0, 3], scheme="centered")
     for k in (0, 3):
         assert np.abs(C[:, k] - Cd[:, k]).max() < 1e-5 * np.abs(Cd).max()
+
+
+def test_rank_estimate_two_orders(Q, ctx64):
+    """Applicability estimate (Sec. 5.2): the stiffness-TTO rank of a laminate
+    does not grow with the order; a sphere's does. The rank at the lower
+    order is the oracle's TT-SVD rank of the same field (within one, the
+    device truncating the reduced k-row field)."""
+    E, nu = (1.0, 10.0), (0.3, 0.3)
+    lam0 = dense.reference_lame(E, nu)
+    lam = Q.qtt_rank_estimate(ctx64, synth.laminate(5, 8), synth.laminate(6, 8), 5, E, nu, 1e-8,
+                              n_target=11)
+    assert abs(lam["growth"] - 1.0) < 1e-12 and lam["rank_target"] == lam["rank_n"]
+    sph = Q.qtt_rank_estimate(ctx64, synth.centred_sphere(3, 0.3), synth.centred_sphere(4, 0.3), 3,
+                              E, nu, 1e-8, n_target=8)
+    assert sph["growth"] > 1.5
+    ref = max(oq.tt_ranks(oq.stiffness_qtt(synth.centred_sphere(3, 0.3), 3, E, nu, lam0, 1e-8)))
+    assert abs(sph["rank_n"] - ref) <= 1
