@@ -14,4 +14,14 @@ Modules:
             CUDA path so that FP64 results can be compared to 1e-10.
 
 Every function names the passage of the paper it restates.
+
+Pins (tests/test_oracle_*.py, no GPU): the Green operator (Direct and
+Centered) against its definition and projector identities; the FFT against a
+brute-force DFT; homogeneous medium, laminate closed form, the LU solution of
+the discrete LS system, Voigt/Reuss/Hashin-Shtrikman bounds; broadcast grids
+against full grids; SFFT MPO rank and unitarity; rounding error bound; exact
+product rank; the sketched product exact at its true rank and quasi-optimal
+on flat spectra, with planted mistakes that fail; Philox known answers; the
+two oracles against each other. Between its exact and its flat-spectrum case
+the sketched product's error is measured, not bounded (parity unpinned there).
 """
