@@ -94,25 +94,122 @@ def green_voigt_direct(xi: np.ndarray, lam0: float, mu0: float) -> np.ndarray:
     return out
 
 
-SCHEMES = ("direct", "centered")
+SCHEMES = ("direct", "centered", "forward", "backward", "hex8r", "staggered")
+
+# Schemes whose divergence operator is k = c(q) v(q) with a factor c common to
+# the three components and a real vector v: Gamma is homogeneous of degree 0
+# in k, so it is the Direct closed form at v (real, even in v).
+REAL_SCHEMES = ("direct", "centered", "hex8r")
+
+
+def _axis_extents(N) -> np.ndarray:
+    return np.broadcast_to(np.asarray(N, dtype=np.float64), (3,))
+
+
+def _cos_sin(xi: np.ndarray, N, frac: float):
+    """cos and sin of frac * 2 pi xi_a / N_a, with the values at xi = 0 and at
+    the Nyquist component (2 |xi_a| = N_a) set exactly (sin(pi) = 0,
+    cos(pi / 2) = 0) so that the symbols there are exactly real or zero."""
+    Nv = _axis_extents(N)
+    t = frac * 2.0 * np.pi * xi / Nv
+    c, s = np.cos(t), np.sin(t)
+    nyq = 2.0 * np.abs(xi) == Nv
+    if frac == 1.0:
+        s = np.where(nyq, 0.0, s)
+        c = np.where(nyq, -1.0, c)
+    else:
+        c = np.where(nyq, 0.0, c)
+        s = np.where(nyq, np.sign(xi), s)
+    return c, s
 
 
 def scheme_vector(xi: np.ndarray, N, scheme: str = "direct") -> np.ndarray:
-    """The real vector whose direction enters the Green operator of a
-    discretisation scheme (App. A table of divergence operators k(q),
-    q_a = 2 pi xi_a / N_a). Direct: k = i q, so the direction of xi. Centered:
-    k = i sin(q), so the direction of s_a = sin(2 pi xi_a / N_a); inserting
-    k = i s into eq. (orig_green_eshelby) gives k_i (.)^-1 k_l^* = s_i (.)^-1 s_l
-    and s C0 s as the acoustic tensor, i.e. the Direct closed form at s. At a
-    Nyquist component (|xi_a| = N_a / 2) s_a = sin(pi) = 0 exactly."""
+    """The real vector v whose direction enters the Green operator of a scheme
+    with k = c(q) v (App. A table of divergence operators k(q), q_a = 2 pi
+    xi_a / N_a).
+      Direct:   k = i q, v = xi.
+      Centered: k = i sin(q), v_a = sin(q_a); inserting k = i s into eq.
+                (orig_green_eshelby) gives k_i (.)^-1 k_l^* = s_i (.)^-1 s_l
+                and s C0 s as the acoustic tensor, i.e. the Direct closed
+                form at s. At a Nyquist component sin(pi) = 0 exactly.
+      Hex8R:    k_j = (i/4) tan(q_j/2) prod_l (1 + e^{i q_l}) (the rotated
+                scheme of the table's source; its printed sum over l is read
+                as this product), = 2 i e^{i sum_l q_l / 2} v_j with
+                v_j = sin(q_j/2) prod_{l != j} cos(q_l/2). v = 0 (Gamma = 0)
+                where two components sit at the Nyquist frequency."""
     xi = np.asarray(xi, dtype=np.float64)
     if scheme == "direct":
         return xi
     if scheme == "centered":
-        Nv = np.broadcast_to(np.asarray(N, dtype=np.float64), (3,))
-        s = np.sin(2.0 * np.pi * xi / Nv)
-        return np.where(2.0 * np.abs(xi) == Nv, 0.0, s)
+        return _cos_sin(xi, N, 1.0)[1]
+    if scheme == "hex8r":
+        c, s = _cos_sin(xi, N, 0.5)
+        return np.stack([s[..., 0] * c[..., 1] * c[..., 2],
+                         c[..., 0] * s[..., 1] * c[..., 2],
+                         c[..., 0] * c[..., 1] * s[..., 2]], axis=-1)
     raise ValueError(scheme)
+
+
+def difference_symbols(xi: np.ndarray, N):
+    """Forward and backward difference symbols of the App. A table under
+    numpy's transform (u(x + e_a) -> e^{+i q_a} u_hat):
+    k+_a = e^{i q_a} - 1, k-_a = -(e^{-i q_a} - 1) = 1 - e^{-i q_a}.
+    Both are real (-2 and +2) at a Nyquist component."""
+    c, s = _cos_sin(np.asarray(xi, dtype=np.float64), N, 1.0)
+    return (c - 1.0) + 1j * s, (1.0 - c) + 1j * s
+
+
+def _voigt_symbol(k_normal: np.ndarray, k_shear: np.ndarray) -> np.ndarray:
+    """(..., 6, 3) matrix B with eps_hat_V = B u_hat: normal strains
+    eps_aa = k_normal_a u_a, engineering shears 2 eps_ab = k_shear_b u_a +
+    k_shear_a u_b (Voigt order 11, 22, 33, 23, 13, 12)."""
+    shape = k_normal.shape[:-1]
+    B = np.zeros(shape + (6, 3), dtype=np.complex128)
+    for a in range(3):
+        B[..., a, a] = k_normal[..., a]
+    for I, (a, b) in enumerate(VOIGT[3:], start=3):
+        B[..., I, a] = k_shear[..., b]
+        B[..., I, b] = k_shear[..., a]
+    return B
+
+
+def gradient_symbol(xi: np.ndarray, N, scheme: str) -> np.ndarray:
+    """B(q) (..., 6, 3) of the strain operator of a complex scheme (App. A
+    table): Forward and Backward use k+ resp. k- for every component; the
+    staggered grid (the table's dual scheme) takes its normal strains with
+    forward and its shear strains with backward differences."""
+    kp, km = difference_symbols(xi, N)
+    if scheme == "forward":
+        return _voigt_symbol(kp, kp)
+    if scheme == "backward":
+        return _voigt_symbol(km, km)
+    if scheme == "staggered":
+        return _voigt_symbol(kp, km)
+    raise ValueError(scheme)
+
+
+def green_voigt_from_symbol(B: np.ndarray, lam0: float, mu0: float) -> np.ndarray:
+    """eq. (orig_green_eshelby) in Voigt form for a strain operator B(q):
+    Gamma_V = B (B^H C0_V B)^-1 B^H (the 3 x 3 acoustic tensor B^H C0_V B is
+    Hermitian positive definite where B != 0); Gamma_V = 0 where B = 0. It
+    maps a Voigt stress-like polarisation to an engineering strain: the
+    displacement solving B^H (C0_V B u + tau) = 0 gives eps = -Gamma_V tau."""
+    C0 = stiffness_voigt(lam0, mu0)
+    Bh = np.conj(np.swapaxes(B, -1, -2))
+    K = Bh @ C0 @ B
+    zero = np.sum(np.abs(B) ** 2, axis=(-2, -1)) == 0
+    K = np.where(zero[..., None, None], np.eye(3), K)
+    G = B @ np.linalg.solve(K, Bh)
+    return np.where(zero[..., None, None], 0.0, G)
+
+
+def green_voigt(xi: np.ndarray, lam0: float, mu0: float, N, scheme: str = "direct"):
+    """Gamma_V(xi) of a scheme before the Nyquist rule: the Direct closed form
+    at scheme_vector for the real schemes, green_voigt_from_symbol for the
+    complex ones (complex output)."""
+    if scheme in REAL_SCHEMES:
+        return green_voigt_direct(scheme_vector(xi, N, scheme), lam0, mu0)
+    return green_voigt_from_symbol(gradient_symbol(xi, N, scheme), lam0, mu0)
 
 
 def green_voigt_symmetrised(xi: np.ndarray, lam0: float, mu0: float, N,
@@ -120,17 +217,19 @@ def green_voigt_symmetrised(xi: np.ndarray, lam0: float, mu0: float, N,
     """Gamma_V with the Nyquist symmetrisation of App. A: at modes with a
     component |xi_a| = N_a/2 (the Nyquist frequency of an even axis of N_a
     points) the value is the average of Gamma_V(xi) and Gamma_V at xi with
-    those components negated (its aliased partner -xi mod N, Gamma being
-    even); elsewhere Gamma_V(xi). N is one extent for a cubic grid or the
-    three extents (N_1, N_2, N_3); an axis of extent 1 has no Nyquist mode.
-    scheme: "direct" (k = i q) or "centered" (k = i sin q), see
-    scheme_vector."""
+    those components negated (its aliased partner -xi mod N); elsewhere
+    Gamma_V(xi). N is one extent for a cubic grid or the three extents
+    (N_1, N_2, N_3); an axis of extent 1 has no Nyquist mode. For the
+    Centered, Forward, Backward, Hex8R and staggered schemes the two values
+    coincide (their symbols at a Nyquist component are equal at +-N_a/2, or
+    differ only by a sign that Gamma does not see), so the rule changes only
+    the Direct scheme."""
     xi = np.asarray(xi, dtype=np.float64)
-    half = np.broadcast_to(np.asarray(N, dtype=np.float64), (3,)) / 2.0
+    half = _axis_extents(N) / 2.0
     nyq = (np.abs(xi) == half) & (half >= 1.0)
     flip = np.where(nyq, -xi, xi)
-    v, vf = scheme_vector(xi, N, scheme), scheme_vector(flip, N, scheme)
-    return 0.5 * (green_voigt_direct(v, lam0, mu0) + green_voigt_direct(vf, lam0, mu0))
+    return 0.5 * (green_voigt(xi, lam0, mu0, N, scheme)
+                  + green_voigt(flip, lam0, mu0, N, scheme))
 
 
 def frequencies(N: int) -> np.ndarray:

@@ -438,17 +438,20 @@ def axis_frequencies_bitrev(n: int) -> np.ndarray:
 def gamma_field_sfft(n: int, lam0: float, mu0: float, scheme: str = "direct") -> np.ndarray:
     """Dense Voigt Green field in the SFFT momentum convention (Sec. 4.3):
     G[I, J, k'1, k'2, k'3] = conj(Gamma_V[I, J](xi(rev k'1), xi(rev k'2), xi(rev k'3))),
-    Nyquist-symmetrised as in App. A (see oracle.dense)."""
+    Nyquist-symmetrised as in App. A (see oracle.dense). Real for the Direct,
+    Centered and Hex8R schemes; complex for Forward, Backward and the
+    staggered grid, whose Gamma(-xi) = conj(Gamma(xi)) makes the conjugate the
+    operator of the opposite transform sign."""
     f = axis_frequencies_bitrev(n)
     N = 1 << n
-    out = np.empty((6, 6, N, N, N))
+    out = np.empty((6, 6, N, N, N), dtype=np.complex128)
     X2, X3 = np.meshgrid(f, f, indexing="ij")
     for a in range(N):
         xi = np.stack([np.full_like(X2, f[a]), X2, X3], axis=-1)
         out[:, :, a] = np.moveaxis(dense.green_voigt_symmetrised(xi, lam0, mu0, N, scheme),
                                    (-2, -1),
                                    (0, 1))
-    return out   # real for both schemes: conj is the identity
+    return np.conj(out)
 
 
 def controlled_field_to_tto(F: np.ndarray, n: int, eps: float, rmax: int):
@@ -462,8 +465,8 @@ def controlled_field_to_tto(F: np.ndarray, n: int, eps: float, rmax: int):
 
 def gamma_qtt(n: int, lam0: float, mu0: float, eps: float, rmax: int = 1 << 30,
               scheme: str = "direct"):
-    """Gamma_hat^0 of a discretisation scheme ("direct" or "centered", App. A)
-    as a raised TTO in the SFFT momentum convention."""
+    """Gamma_hat^0 of a discretisation scheme (one of oracle.dense.SCHEMES, the
+    App. A table) as a raised TTO in the SFFT momentum convention."""
     return controlled_field_to_tto(gamma_field_sfft(n, lam0, mu0, scheme), n, eps, rmax)
 
 

@@ -13,6 +13,7 @@ import pytest
 
 from oracle import dense
 from paper_2412_11566_gb300 import synth
+from tests._helpers import laminate_closed_form
 
 GOLD = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -135,28 +136,6 @@ def test_homogeneous_medium_exact():
     C, imag, iters = dense.ceff(ph, E, nu, tol=1e-12, lame0=(0.7, 0.4))
     assert np.allclose(C, dense.stiffness_voigt(*dense.lame(2.0, 0.25)), atol=1e-12)
     assert max(iters) <= 2
-
-
-def laminate_closed_form(ph1d, E, nu):
-    """Exact C_eff of layers normal to x3 (normal n = {33, 23, 13} = Voigt
-    {2, 3, 4}, tangential t = {11, 22, 12} = Voigt {0, 1, 5})."""
-    Cs = [dense.stiffness_voigt(*dense.lame(e, v)) for e, v in zip(E, nu)]
-    n_idx, t_idx = [2, 3, 4], [0, 1, 5]
-    frac = np.array([np.mean(ph1d == p) for p in range(len(E))])
-    avg = lambda f: sum(w * f(C) for w, C in zip(frac, Cs))
-    Cnn_inv = lambda C: np.linalg.inv(C[np.ix_(n_idx, n_idx)])
-    Cstar_nn = np.linalg.inv(avg(Cnn_inv))
-    Cstar_tn = avg(lambda C: C[np.ix_(t_idx, n_idx)] @ Cnn_inv(C)) @ Cstar_nn
-    A = avg(lambda C: C[np.ix_(t_idx, t_idx)]
-            - C[np.ix_(t_idx, n_idx)] @ Cnn_inv(C) @ C[np.ix_(n_idx, t_idx)])
-    Cstar_tt = A + avg(lambda C: C[np.ix_(t_idx, n_idx)] @ Cnn_inv(C)) @ Cstar_nn @ \
-        avg(lambda C: Cnn_inv(C) @ C[np.ix_(n_idx, t_idx)])
-    out = np.zeros((6, 6))
-    out[np.ix_(n_idx, n_idx)] = Cstar_nn
-    out[np.ix_(t_idx, n_idx)] = Cstar_tn
-    out[np.ix_(n_idx, t_idx)] = Cstar_tn.T
-    out[np.ix_(t_idx, t_idx)] = Cstar_tt
-    return out
 
 
 def test_laminate_closed_form():

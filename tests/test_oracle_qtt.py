@@ -446,3 +446,46 @@ def test_qtt_oracle_matches_dense_oracle_centered():
     b = oq.ls_solve(dC, G, S, Sh, Ev, n, 1e-11, 1e-12, 1000, lame0=lam0, seed=2412)
     a = dense.basic_scheme(ph, E, nu, Ev, tol=1e-11, scheme="centered")
     assert np.abs(b["sigma_bar"] - a["sigma_bar"]).max() < 1e-8 * np.abs(a["sigma_bar"]).max()
+
+
+def _asymmetric_phase(n):
+    N = 1 << n
+    return (np.random.default_rng(31).random((N, N, N)) < 0.4).astype(np.uint8)
+
+
+@pytest.mark.parametrize("scheme", ["forward", "hex8r", "staggered"])
+def test_qtt_oracle_matches_dense_oracle_other_schemes(scheme):
+    """Oracle B with the Green TTO of the Forward, Hex8R and staggered schemes
+    (App. A table; complex for Forward and staggered, whose SFFT-side field is
+    the conjugate) against oracle A with the same scheme, on a seeded 4^3
+    two-phase field without mirror symmetry, load e11 and the shear load e23."""
+    n = 2
+    ph = _asymmetric_phase(n)
+    E, nu = (1.0, 10.0), (0.3, 0.3)
+    lam0 = dense.reference_lame(E, nu)
+    dC = oq.stiffness_qtt(ph, n, E, nu, lam0, 1e-12)
+    G = oq.gamma_qtt(n, *lam0, 1e-12, scheme=scheme)
+    S, Sh = oq.sfft_operator(n), oq.sfft_operator(n, adjoint=True)
+    for k in (0, 3):
+        Ev = np.eye(6)[k]
+        b = oq.ls_solve(dC, G, S, Sh, Ev, n, 1e-11, 1e-12, 1000, lame0=lam0, seed=2412)
+        a = dense.basic_scheme(ph, E, nu, Ev, tol=1e-11, scheme=scheme)
+        assert np.abs(b["sigma_bar"] - a["sigma_bar"]).max() < 1e-8 * np.abs(a["sigma_bar"]).max()
+
+
+def test_qtt_complex_scheme_needs_the_conjugate():
+    """Planted mistake: the staggered Green field without the SFFT-convention
+    conjugation is the operator of the mirrored grid, which the dense
+    comparison detects on a field without mirror symmetry."""
+    n = 2
+    ph = _asymmetric_phase(n)
+    E, nu = (1.0, 10.0), (0.3, 0.3)
+    lam0 = dense.reference_lame(E, nu)
+    dC = oq.stiffness_qtt(ph, n, E, nu, lam0, 1e-12)
+    F = np.conj(oq.gamma_field_sfft(n, *lam0, "staggered"))
+    G = oq.controlled_field_to_tto(F, n, 1e-12, 1 << 30)
+    S, Sh = oq.sfft_operator(n), oq.sfft_operator(n, adjoint=True)
+    Ev = np.eye(6)[3]
+    b = oq.ls_solve(dC, G, S, Sh, Ev, n, 1e-11, 1e-12, 1000, lame0=lam0, seed=2412)
+    a = dense.basic_scheme(ph, E, nu, Ev, tol=1e-11, scheme="staggered")
+    assert np.abs(b["sigma_bar"] - a["sigma_bar"]).max() > 1e-6 * np.abs(a["sigma_bar"]).max()
