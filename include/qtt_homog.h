@@ -68,8 +68,12 @@ extern "C" {
 #define QTT_CONTRACT_SIMT 0
 #define QTT_CONTRACT_TF32X3 1
 #define QTT_CONTRACT_TC 2
-#define QTT_SCHEME_DIRECT 0
+#define QTT_SCHEME_DIRECT 0    /* App. A table of divergence operators, in its order */
 #define QTT_SCHEME_CENTERED 1
+#define QTT_SCHEME_FORWARD 2
+#define QTT_SCHEME_BACKWARD 3
+#define QTT_SCHEME_HEX8R 4
+#define QTT_SCHEME_STAGGERED 5
 #define QTT_FACTOR_NATIVE 0
 #define QTT_FACTOR_FP64 1
 #define QTT_FACTOR_FP64_ROUNDING 2
@@ -189,18 +193,30 @@ int qtt_rank_estimate(qtt_ctx_t ctx, const uint8_t* phase_a, const int shape_a[3
  * device by TT-SVD of the per-axis matrix at accuracy eps. */
 int qtt_sfft_operator(qtt_ctx_t ctx, int n, int adjoint, double eps, qtt_op_t* out);
 
-/* The Green operator Gamma_hat^0 (App. A, eq. (orig_green_eshelby), Direct
- * scheme k = i q, isotropic C0 = (lambda0, mu0)) in the SFFT momentum
- * convention (Sec. 4.3: bit-reversed per axis, conjugated), as a raised TTO.
- * Built from its separable form (App. A): Gamma_V(xi) is a 36 x 15 matrix of
- * (lambda0, mu0) times the 15 degree-4 monomials of xi/|xi|; the monomial
- * fields are compressed by TT-SVD at eps_tt and rank cap rmax once per
- * (n, eps_tt, rmax) and context, and the matrix multiplies their first core
- * (relative error at most cond(matrix) eps_tt, cond ~7). scheme (App. A
- * table of divergence operators): QTT_SCHEME_DIRECT (k = i q) or
- * QTT_SCHEME_CENTERED (k = i sin q; eq. (orig_green_eshelby) with k = i s
- * is the Direct closed form at s = sin q, so the same 15 monomials of s/|s|
- * are compressed; s = 0 at Nyquist components). n in 1..9. */
+/* The Green operator Gamma_hat^0 (App. A, eq. (orig_green_eshelby),
+ * isotropic C0 = (lambda0, mu0)) of a discretisation scheme in the SFFT
+ * momentum convention (Sec. 4.3: bit-reversed per axis, conjugated), as a
+ * raised TTO. scheme (App. A table of divergence operators k(q)):
+ *   QTT_SCHEME_DIRECT (k = i q), QTT_SCHEME_CENTERED (k = i sin q) and
+ *   QTT_SCHEME_HEX8R (k_j = (i/4) tan(q_j/2) prod_l (1 + e^{i q_l}), the
+ *   table's sum over l read as this product) have k = common factor x real
+ *   vector v (v = xi, sin q, and sin(q_j/2) prod_{l!=j} cos(q_l/2)), and
+ *   Gamma is the Direct closed form at v. It is built from its separable
+ *   form: Gamma_V is a 36 x 15 matrix of (lambda0, mu0) times the 15
+ *   degree-4 monomials of v/|v|; the monomial fields are compressed by TT-SVD
+ *   at eps_tt and rank cap rmax once per (n, eps_tt, rmax, scheme) and
+ *   context, and the matrix multiplies their first core (relative error at
+ *   most cond(matrix) eps_tt, cond ~7). n in 1..9.
+ *   QTT_SCHEME_FORWARD (k+ = e^{iq} - 1), QTT_SCHEME_BACKWARD
+ *   (k- = 1 - e^{-iq}) and QTT_SCHEME_STAGGERED (normal strains with k+,
+ *   shear strains with k-) are complex: Gamma_V = B (B^H C0 B)^-1 B^H with
+ *   B the 6 x 3 strain symbol is evaluated at every frequency and the
+ *   36-entry field compressed by TT-SVD at (eps_tt, rmax). n in 1..8; the
+ *   field takes 36 x 2^(3n) x 16 bytes of workspace while it is built.
+ * At Nyquist modes App. A's symmetrisation applies (it changes only the Direct
+ * scheme). Errors: QTT_EINVAL for a scheme outside 0..5, n out of range or
+ * a reference medium that is not positive definite; QTT_ENOMEM when the
+ * workspace cannot hold the field. */
 int qtt_gamma_operator(qtt_ctx_t ctx, int n, double lambda0, double mu0, int scheme,
                        double eps_tt, int rmax, qtt_op_t* out);
 
@@ -278,8 +294,7 @@ typedef struct {
   int max_iter;    /* iteration cap (QTT_WNOCONV when reached) */
   double eps_tt;   /* rounding accuracy of every step */
   int rmax;        /* rank cap of every rounding */
-  int scheme;      /* Green operator discretisation: QTT_SCHEME_DIRECT or
-                      QTT_SCHEME_CENTERED */
+  int scheme;      /* Green operator discretisation, QTT_SCHEME_* (0..5) */
   int oversample;  /* sketch rank = rmax + oversample */
 } qtt_solve_params;
 

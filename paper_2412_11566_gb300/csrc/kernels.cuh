@@ -1002,15 +1002,24 @@ __device__ void green_monomials_at(const double xi[3], double* m15) {
         for (int d = c; d < 3; ++d) m15[g++] = nn[a] * nn[b] * nn[c] * nn[d];
 }
 
-// scheme 0 (Direct, k = i q): the monomials of xi/|xi|. scheme 1 (Centered,
-// k = i sin q): of s/|s| with s_a = sin(2 pi xi_a / N), which is 0 at a
-// Nyquist component (sinpi of an integer is exact).
+// Monomials of v/|v| for the schemes whose divergence operator is a common
+// factor times a real vector v (App. A table):
+//   scheme 0 (Direct, k = i q): v = xi.
+//   scheme 1 (Centered, k = i sin q): v_a = sin(2 pi xi_a / N), 0 at a Nyquist
+//     component.
+//   scheme 4 (Hex8R, k_j = (i/4) tan(q_j/2) prod_l (1 + e^{i q_l})):
+//     v_j = sin(q_j/2) prod_{l != j} cos(q_l/2); cos(q_l/2) = 0 at a Nyquist
+//     component and sin(q_j/2) = sign(xi_j) there, so v = 0 where two
+//     components sit at the Nyquist frequency.
+// At Nyquist modes the value is the average with the aliased partner (the
+// Nyquist components negated); the monomials are even in v, so for schemes 1
+// and 4 the average is the value itself.
 __global__ void green_monomials_kernel(Cx<double>* out, int n, int scheme) {
   const long long N = 1ll << n, N3 = N * N * N;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N3;
        e += (long long)gridDim.x * blockDim.x) {
     const int ks[3] = {(int)(e / (N * N)), (int)((e / N) % N), (int)(e % N)};
-    double xi[3], xf[3];
+    double xi[3], xf[3], hs[3], hc[3];
     bool nyq = false;
     for (int a = 0; a < 3; ++a) {
       const int k = n > 0 ? bitrev(ks[a], n) : 0;
@@ -1018,9 +1027,20 @@ __global__ void green_monomials_kernel(Cx<double>* out, int n, int scheme) {
       const bool isn = (2 * (long long)fabs(xi[a]) == N);
       nyq |= isn;
       xf[a] = isn ? -xi[a] : xi[a];
+      sincospi(xi[a] / (double)N, &hs[a], &hc[a]);
+      if (isn) {
+        hs[a] = xi[a] > 0 ? 1.0 : -1.0;
+        hc[a] = 0.0;
+      }
       if (scheme == 1) {
         xi[a] = isn ? 0.0 : sinpi(2.0 * xi[a] / (double)N);
         xf[a] = isn ? 0.0 : xi[a];
+      }
+    }
+    if (scheme == 4) {
+      for (int a = 0; a < 3; ++a) {
+        xi[a] = hs[a] * hc[(a + 1) % 3] * hc[(a + 2) % 3];
+        xf[a] = xi[a];
       }
     }
     double g[15], gf[15];
@@ -1030,6 +1050,135 @@ __global__ void green_monomials_kernel(Cx<double>* out, int n, int scheme) {
       for (int q = 0; q < 15; ++q) g[q] = 0.5 * (g[q] + gf[q]);
     }
     for (int q = 0; q < 15; ++q) out[(long long)q * N3 + e] = mk<double>(g[q], 0.0);
+  }
+}
+
+__host__ __device__ inline double2 zmul(double2 x, double2 y) {
+  return make_double2(x.x * y.x - x.y * y.y, x.x * y.y + x.y * y.x);
+}
+__host__ __device__ inline double2 zsub(double2 x, double2 y) {
+  return make_double2(x.x - y.x, x.y - y.y);
+}
+
+// eq. (orig_green_eshelby) in Voigt form for a strain symbol with normal
+// components kn and shear components kt (eps_aa = kn_a u_a, 2 eps_ab =
+// kt_b u_a + kt_a u_b, Voigt order 11 22 33 23 13 12): with B the 6 x 3
+// symbol, Gamma_V = B (B^H C0_V B)^-1 B^H for the isotropic C0 of Lame
+// parameters (lam0, mu0). The symbols must not all vanish and should be
+// scaled to |k| ~ 1 (Gamma is homogeneous of degree 0 in k). The 3 x 3 inverse
+// is the adjugate over the determinant. g[I * 6 + J] = conj(Gamma_V[I][J]).
+__host__ __device__ inline void green_symbol_voigt_conj(const double2 kn[3], const double2 kt[3],
+                                                        double lam0, double mu0, double2 g[36]) {
+  const int vi[3] = {1, 0, 0}, vj[3] = {2, 2, 1};  // Voigt 3, 4, 5 = (23), (13), (12)
+  double2 B[6][3];
+  for (int I = 0; I < 6; ++I)
+    for (int m = 0; m < 3; ++m) B[I][m] = make_double2(0.0, 0.0);
+  for (int a = 0; a < 3; ++a) B[a][a] = kn[a];
+  for (int t = 0; t < 3; ++t) {
+    B[3 + t][vi[t]] = kt[vj[t]];
+    B[3 + t][vj[t]] = kt[vi[t]];
+  }
+  // CB = C0_V B: lam0 tr + 2 mu0 on the normal rows, mu0 on the shear rows
+  double2 CB[6][3];
+  for (int m = 0; m < 3; ++m) {
+    const double trx = B[0][m].x + B[1][m].x + B[2][m].x;
+    const double try_ = B[0][m].y + B[1][m].y + B[2][m].y;
+    for (int a = 0; a < 3; ++a)
+      CB[a][m] = make_double2(lam0 * trx + 2.0 * mu0 * B[a][m].x,
+                              lam0 * try_ + 2.0 * mu0 * B[a][m].y);
+    for (int t = 3; t < 6; ++t) CB[t][m] = make_double2(mu0 * B[t][m].x, mu0 * B[t][m].y);
+  }
+  // K = B^H C0_V B (3 x 3 Hermitian)
+  double2 K[3][3];
+  for (int m = 0; m < 3; ++m)
+    for (int p = 0; p < 3; ++p) {
+      double re = 0, im = 0;
+      for (int I = 0; I < 6; ++I) {
+        const double2 u = B[I][m], v = CB[I][p];  // conj(u) v
+        re += u.x * v.x + u.y * v.y;
+        im += u.x * v.y - u.y * v.x;
+      }
+      K[m][p] = make_double2(re, im);
+    }
+  double2 cof[3][3];
+  for (int m = 0; m < 3; ++m)
+    for (int p = 0; p < 3; ++p) {
+      const int m1 = (m + 1) % 3, m2 = (m + 2) % 3, p1 = (p + 1) % 3, p2 = (p + 2) % 3;
+      cof[m][p] = zsub(zmul(K[m1][p1], K[m2][p2]), zmul(K[m1][p2], K[m2][p1]));
+    }
+  double2 det = make_double2(0.0, 0.0);
+  for (int p = 0; p < 3; ++p) {
+    const double2 t = zmul(K[0][p], cof[0][p]);
+    det.x += t.x;
+    det.y += t.y;
+  }
+  const double dd = det.x * det.x + det.y * det.y;
+  const double2 rdet = make_double2(det.x / dd, -det.y / dd);
+  for (int I = 0; I < 6; ++I) {
+    double2 W[3];  // (B K^-1)[I][:], K^-1[p][m] = cof[m][p] / det
+    for (int m = 0; m < 3; ++m) {
+      double2 acc = make_double2(0.0, 0.0);
+      for (int p = 0; p < 3; ++p) {
+        const double2 t = zmul(B[I][p], zmul(cof[m][p], rdet));
+        acc.x += t.x;
+        acc.y += t.y;
+      }
+      W[m] = acc;
+    }
+    for (int J = 0; J < 6; ++J) {
+      double re = 0, im = 0;
+      for (int m = 0; m < 3; ++m) {
+        const double2 w = W[m], u = B[J][m];  // w conj(u)
+        re += w.x * u.x + w.y * u.y;
+        im += w.y * u.x - w.x * u.y;
+      }
+      g[I * 6 + J] = make_double2(re, -im);
+    }
+  }
+}
+
+// Green field of the schemes with complex divergence operators (App. A table):
+// scheme 2 (Forward, k+_a = e^{i q_a} - 1), 3 (Backward, k-_a = 1 - e^{-i q_a})
+// and 5 (staggered grid: normal strains with k+, shear strains with k-), from
+// green_symbol_voigt_conj; Gamma_V = 0 at xi = 0. The symbols are real and
+// equal at +-N/2 for a Nyquist component, so the Nyquist rule leaves these
+// operators unchanged. Stored in the SFFT convention (its transform sign is
+// opposite to the one the symbols are written for, and Gamma(-xi) =
+// conj(Gamma(xi))): out[(I * 6 + J) * N3 + e] = conj(Gamma_V[I][J]) at the
+// frequency of bit-reversed index e.
+__global__ void green_symbol_field_kernel(Cx<double>* out, int n, double lam0, double mu0,
+                                          int scheme) {
+  const long long N = 1ll << n, N3 = N * N * N;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N3;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int ks[3] = {(int)(e / (N * N)), (int)((e / N) % N), (int)(e % N)};
+    double2 kp[3], km[3];
+    double nrm2 = 0;
+    for (int a = 0; a < 3; ++a) {
+      const int k = n > 0 ? bitrev(ks[a], n) : 0;
+      const double x = (k <= N / 2) ? (double)k : (double)(k - N);
+      double s, c;
+      sincospi(2.0 * x / (double)N, &s, &c);
+      if (2 * (long long)fabs(x) == N) {
+        s = 0.0;
+        c = -1.0;
+      }
+      kp[a] = make_double2(c - 1.0, s);
+      km[a] = make_double2(1.0 - c, s);
+      nrm2 += (c - 1.0) * (c - 1.0) + s * s;
+    }
+    if (nrm2 == 0.0) {
+      for (int P = 0; P < 36; ++P) out[(long long)P * N3 + e] = mk<double>(0.0, 0.0);
+      continue;
+    }
+    const double inv = 1.0 / sqrt(nrm2);
+    for (int a = 0; a < 3; ++a) {
+      kp[a] = make_double2(kp[a].x * inv, kp[a].y * inv);
+      km[a] = make_double2(km[a].x * inv, km[a].y * inv);
+    }
+    double2 g[36];
+    green_symbol_voigt_conj(scheme == 3 ? km : kp, scheme == 2 ? kp : km, lam0, mu0, g);
+    for (int P = 0; P < 36; ++P) out[(long long)P * N3 + e] = mk<double>(g[P].x, g[P].y);
   }
 }
 

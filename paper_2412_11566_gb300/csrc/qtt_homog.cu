@@ -2100,11 +2100,38 @@ void green_coeffs(double lam0, double mu0, double* C) {
 // medium), then its first core mixed by the 36 x 15 coefficient matrix C of
 // (lam0, mu0). The operator's relative error is at most cond(C) eps (C's
 // condition number is ~7 for the media of the workloads).
+//
+// The Forward, Backward and staggered schemes have complex divergence
+// operators and no such separable form: their Green field (36 complex
+// entries per frequency, green_symbol_field_kernel) is compressed directly
+// by TT-SVD, which bounds n by the 2^31-row unfolding (n <= 8) and needs
+// 36 x 2^(3n) x 16 bytes of workspace for the field (9.7 GB at n = 8).
+qtt_op* build_gamma_symbol(qtt_ctx* c, int n, double lam0, double mu0, int scheme, double eps,
+                           int rmax) {
+  QREQ(n >= 1 && n <= 8, "gamma: n must be in 1..8 for the Forward, Backward and staggered schemes");
+  Eng<double> e(c);
+  const long long N3 = 1ll << (3 * n);
+  Cx<double>* F = e.alloc(36 * N3);
+  green_symbol_field_kernel<<<grid1d(N3), 256, 0, e.st()>>>(F, n, lam0, mu0, scheme);
+  e.post("green_symbol_field_kernel", __LINE__);
+  const int bc[3] = {0, 0, 0};
+  qtt_op* o = raised_from_field(c, F, n, bc, eps, rmax);  // consumes F
+  o->n = n;
+  o->has_c0 = 1;
+  o->lame0[0] = lam0;
+  o->lame0[1] = mu0;
+  voigt_stiffness(lam0, mu0, o->C0);
+  return o;
+}
+
 qtt_op* build_gamma(qtt_ctx* c, int n, double lam0, double mu0, int scheme, double eps, int rmax) {
-  QREQ(scheme == QTT_SCHEME_DIRECT || scheme == QTT_SCHEME_CENTERED,
-       "gamma: scheme must be 0 (Direct) or 1 (Centered)");
-  QREQ(n >= 1 && n <= 9, "gamma: n must be in 1..9");
+  QREQ(scheme >= QTT_SCHEME_DIRECT && scheme <= QTT_SCHEME_STAGGERED,
+       "gamma: scheme must be 0..5 (Direct, Centered, Forward, Backward, Hex8R, staggered)");
   QREQ(mu0 > 0 && lam0 + 2 * mu0 > 0, "gamma: reference medium not positive definite");
+  if (scheme == QTT_SCHEME_FORWARD || scheme == QTT_SCHEME_BACKWARD ||
+      scheme == QTT_SCHEME_STAGGERED)
+    return build_gamma_symbol(c, n, lam0, mu0, scheme, eps, rmax);
+  QREQ(n >= 1 && n <= 9, "gamma: n must be in 1..9");
   Eng<double> e(c);
   const double eps_m = eps;
   const auto key = std::make_tuple(n, eps_m, rmax, scheme);

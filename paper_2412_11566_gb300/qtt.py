@@ -31,7 +31,8 @@ QTT_WRANKCAP, QTT_WNOCONV = 1, 2
 QTT_FP64, QTT_FP32 = 0, 1
 QTT_CONTRACT_SIMT, QTT_CONTRACT_TF32X3, QTT_CONTRACT_TC = 0, 1, 2
 QTT_FACTOR_NATIVE, QTT_FACTOR_FP64, QTT_FACTOR_FP64_ROUNDING = 0, 1, 2
-QTT_SCHEME_DIRECT, QTT_SCHEME_CENTERED = 0, 1
+(QTT_SCHEME_DIRECT, QTT_SCHEME_CENTERED, QTT_SCHEME_FORWARD, QTT_SCHEME_BACKWARD,
+ QTT_SCHEME_HEX8R, QTT_SCHEME_STAGGERED) = range(6)
 MAXC = 64
 
 _p = C.c_void_p
