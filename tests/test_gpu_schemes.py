@@ -85,20 +85,3 @@ def test_ls_solve_scheme_vs_dense_oracle(Q, ctx64, scheme):
     Cd, imag, its = dense.ceff(ph, E, nu, tol=1e-6, loads=[0, 3], scheme=scheme)
     for k in (0, 3):
         assert np.abs(C[:, k] - Cd[:, k]).max() < 1e-5 * np.abs(Cd).max()
-
-
-def test_ls_solve_staggered_16cubed(Q, ctx64):
-    """The staggered grid (the scheme of the paper's experiments, Sec. 5.1) at
-    16^3 on a two-sphere geometry, three loads, against the dense oracle to
-    the metric's 1e-4."""
-    n = 4
-    ph = synth.sphere_field(n, [(0.3, 0.4, 0.55), (0.8, 0.75, 0.2)], [0.22, 0.15])
-    E, nu = (1.0, 20.0), (0.3, 0.25)
-    dC = Q.qtt_from_phase_field(ctx64, ph, n, E, nu, None, 1e-10)
-    p = Q.solve_params(1e-6, 500, 1e-8, 128, Q.QTT_SCHEME_STAGGERED)
-    loads = [0, 2, 5]
-    C, infos, rc = Q.ls_solve_ceff(ctx64, dC, p, loads=loads)
-    Cd, imag, its = dense.ceff(ph, E, nu, tol=1e-6, loads=loads, scheme="staggered")
-    assert imag < 1e-10
-    for k in loads:
-        assert np.abs(C[:, k] - Cd[:, k]).max() < 1e-4 * np.abs(Cd[:, k]).max()
