@@ -127,7 +127,10 @@ def scheme_vector(xi: np.ndarray, N, scheme: str = "direct") -> np.ndarray:
     """The real vector v whose direction enters the Green operator of a scheme
     with k = c(q) v (App. A table of divergence operators k(q), q_a = 2 pi
     xi_a / N_a).
-      Direct:   k = i q, v = xi.
+      Direct:   k = i q, v = xi / N_a (prop. to q). App. A defines q for
+                cubic grids only; on a grid with unequal N_a the voxels are read
+                as unit cubes (the reading the difference stencils make), so
+                q_a = 2 pi xi_a / N_a on every axis.
       Centered: k = i sin(q), v_a = sin(q_a); inserting k = i s into eq.
                 (orig_green_eshelby) gives k_i (.)^-1 k_l^* = s_i (.)^-1 s_l
                 and s C0 s as the acoustic tensor, i.e. the Direct closed
@@ -139,7 +142,7 @@ def scheme_vector(xi: np.ndarray, N, scheme: str = "direct") -> np.ndarray:
                 where two components sit at the Nyquist frequency."""
     xi = np.asarray(xi, dtype=np.float64)
     if scheme == "direct":
-        return xi
+        return xi / _axis_extents(N)
     if scheme == "centered":
         return _cos_sin(xi, N, 1.0)[1]
     if scheme == "hex8r":

@@ -467,6 +467,35 @@ def ls_solve_ceff(ctx: Context, dC: Op, params: SolveParams, loads=None):
     return Ceff.reshape(6, 6).T.copy(), [i.as_dict() for i in infos], rc
 
 
+PLANE_STRAIN_VOIGT = (1, 2, 3)   # 3D Voigt (22, 33, 23) = 2D (11, 22, 12) of the section (x2, x3)
+
+
+def ls_solve_ceff_plane_strain(ctx: Context, phase2d, n, E, nu, params: SolveParams,
+                               lame0=None, eps_tt=1e-8, rmax=1 << 30):
+    """Plane-strain C_eff (3 x 3, Voigt (11, 22, 12) with engineering shear) of a
+    2D section of 2^n x 2^n pixels (the paper's 2D experiments, Sec. 5; the
+    3-component Voigt form of Sec. 2). For isotropic phases the plane-strain
+    problem is the 3D problem of the section extruded along x1: on an x1-
+    invariant field the Green operator has n_1 = 0, so the out-of-plane strain
+    components stay exactly zero under in-plane loads and the in-plane block
+    of the 3D C_eff is the 2D one. This call therefore uploads the section as
+    a (1, 2^n, 2^n) grid whose x1 axis is broadcast (no binary cores for it),
+    builds (C - C0) with qtt_from_phase_field and runs ls_solve_ceff for the
+    three in-plane unit loads; it computes nothing itself. Returns
+    (C 3 x 3, infos of the three loads, worst status)."""
+    ph = np.asarray(phase2d)
+    N = 1 << n
+    if ph.shape != (N, N):
+        raise ValueError(f"plane strain: phase must be ({N}, {N}), got {ph.shape}")
+    dC = qtt_from_phase_field(ctx, ph.reshape(1, N, N), n, E, nu, lame0, eps_tt, rmax)
+    try:
+        C6, infos, rc = ls_solve_ceff(ctx, dC, params, loads=PLANE_STRAIN_VOIGT)
+    finally:
+        dC.free()
+    idx = list(PLANE_STRAIN_VOIGT)
+    return C6[np.ix_(idx, idx)].copy(), infos, rc
+
+
 def ls_solve_batched(ctx: Context, dCs, params: SolveParams):
     """C_eff of several microstructures: returns (array (items, 6, 6), infos
     as a list of items lists of 6 dicts, worst status)."""

@@ -1,0 +1,142 @@
+"""Pins of the 2D plane-strain oracle (oracle/dense2d.py, Sec. 2's 3-component
+Voigt form; the paper's 2D experiments, Sec. 5) against facts that do not go
+through its own Green operator: the 3D oracle on the same section extruded
+along a broadcast axis, a brute-force real-space Green operator on tiny grids,
+the exact laminate, and the homogeneous medium."""
+import numpy as np
+import pytest
+import scipy.fft as sfft
+
+from oracle import dense, dense2d
+from paper_2412_11566_gb300 import synth
+from tests._helpers import laminate_closed_form
+
+IN_PLANE = [1, 2, 3]   # 3D Voigt (22, 33, 23) = 2D (11, 22, 12) for the section (x2, x3)
+
+
+def _two_phase(shape, seed, frac=0.4):
+    return (np.random.default_rng(seed).random(shape) < frac).astype(np.uint8)
+
+
+@pytest.mark.parametrize("scheme", dense2d.SCHEMES)
+@pytest.mark.parametrize("shape", [(8, 8), (4, 8)])
+def test_2d_equals_3d_extruded(scheme, shape):
+    """The plane-strain C_eff of a section equals the in-plane block of the 3D
+    C_eff of the section extruded along x1 (a (1, N1, N2) grid), for every
+    scheme: the two oracles share no Green-operator code."""
+    ph2 = _two_phase(shape, 3)
+    E, nu = (1.0, 12.0), (0.3, 0.22)
+    C2, imag2, _ = dense2d.ceff2(ph2, E, nu, tol=1e-12, scheme=scheme)
+    C3, imag3, _ = dense.ceff(ph2[None], E, nu, tol=1e-12, loads=IN_PLANE, scheme=scheme)
+    assert imag2 < 1e-12 and imag3 < 1e-12
+    ref = C3[np.ix_(IN_PLANE, IN_PLANE)]
+    assert np.allclose(C2, ref, atol=1e-10 * np.abs(ref).max())
+
+
+def test_2d_laminate_closed_form():
+    """Layers normal to the section's second axis: the exact plane-strain
+    laminate, the in-plane block of the 3D laminate closed form."""
+    ph1 = synth.laminate(3, 2).reshape(-1)           # along the layer normal
+    ph2 = np.ascontiguousarray(np.broadcast_to(ph1[None, :], (8, 8)))
+    E, nu = (9.0, 1.5), (0.3, 0.2)
+    for scheme in dense2d.SCHEMES:
+        C2, _, _ = dense2d.ceff2(ph2, E, nu, tol=1e-13, scheme=scheme)
+        ref = laminate_closed_form(ph1, E, nu)[np.ix_(IN_PLANE, IN_PLANE)]
+        assert np.allclose(C2, ref, atol=1e-9 * np.abs(ref).max()), scheme
+
+
+def test_2d_homogeneous_exact():
+    ph = _two_phase((8, 8), 4)
+    C, _, its = dense2d.ceff2(ph, (2.0, 2.0), (0.25, 0.25), tol=1e-12, lame0=(0.7, 0.4))
+    assert np.allclose(C, dense2d.stiffness_voigt2(*dense2d.lame(2.0, 0.25)), atol=1e-12)
+    assert max(its) <= 2
+
+
+def _shift2(shape, a):
+    V = int(np.prod(shape))
+    idx = np.arange(V).reshape(shape)
+    S = np.zeros((V, V))
+    S[idx.ravel(), np.roll(idx, -1, axis=a).ravel()] = 1.0
+    return S
+
+
+def _real_space_green2(shape, scheme, lam0, mu0):
+    V = int(np.prod(shape))
+    I = np.eye(V)
+    S = [_shift2(shape, a) for a in range(2)]
+    fwd = [S[a] - I for a in range(2)]
+    bwd = [I - S[a].T for a in range(2)]
+    if scheme == "forward":
+        Dn = Ds = fwd
+    elif scheme == "backward":
+        Dn = Ds = bwd
+    elif scheme == "staggered":
+        Dn, Ds = fwd, bwd
+    elif scheme == "centered":
+        Dn = Ds = [0.5 * (S[a] - S[a].T) for a in range(2)]
+    elif scheme == "hex8r":   # corner strain: difference averaged over the two parallel edges
+        Dn = Ds = [0.5 * fwd[0] @ (I + S[1]), 0.5 * fwd[1] @ (I + S[0])]
+    else:
+        raise ValueError(scheme)
+    D = np.zeros((3 * V, 2 * V))
+    D[0:V, 0:V] = Dn[0]
+    D[V:2 * V, V:2 * V] = Dn[1]
+    D[2 * V:, 0:V] = Ds[1]
+    D[2 * V:, V:2 * V] = Ds[0]
+    C0 = np.kron(dense2d.stiffness_voigt2(lam0, mu0), np.eye(V))
+    return D @ np.linalg.pinv(D.T @ C0 @ D, rcond=1e-10, hermitian=True) @ D.T
+
+
+def _fourier_apply2(tau, scheme, lam0, mu0):
+    G = dense2d.green_field2(tau.shape[1:], lam0, mu0, scheme)
+    eh = np.einsum("xyIJ,Jxy->Ixy", G, sfft.fftn(tau, axes=(1, 2)))
+    eh[:, 0, 0] = 0.0
+    return sfft.ifftn(eh, axes=(1, 2))
+
+
+@pytest.mark.parametrize("scheme", ["centered", "forward", "backward", "hex8r", "staggered"])
+@pytest.mark.parametrize("shape", [(4, 4), (2, 6), (8, 4)])
+def test_2d_green_equals_real_space_operator(scheme, shape):
+    rng = np.random.default_rng(5)
+    lam0, mu0 = 1.4, 0.9
+    tau = rng.standard_normal((3,) + shape)
+    ref = (_real_space_green2(shape, scheme, lam0, mu0) @ tau.ravel()).reshape(tau.shape)
+    got = _fourier_apply2(tau, scheme, lam0, mu0)
+    assert np.abs(got.imag).max() < 1e-12
+    assert np.allclose(got.real, ref, atol=1e-11 * np.abs(ref).max())
+
+
+def test_2d_real_space_check_catches_planted_mistakes(monkeypatch):
+    """Planted mistakes: the staggered grid with its forward and backward
+    differences exchanged, and Forward with the backward symbol."""
+    shape = (4, 4)
+    rng = np.random.default_rng(6)
+    tau = rng.standard_normal((3,) + shape)
+    orig = dense2d._axis_symbols
+    monkeypatch.setattr(dense2d, "_axis_symbols", lambda x, N, s: orig(x, N, s)[::-1])
+    ref = (_real_space_green2(shape, "staggered", 1.4, 0.9) @ tau.ravel()).reshape(tau.shape)
+    bad = _fourier_apply2(tau, "staggered", 1.4, 0.9).real
+    assert not np.allclose(bad, ref, atol=1e-6 * np.abs(ref).max())
+    monkeypatch.setattr(dense2d, "_axis_symbols",
+                        lambda x, N, s: orig(x, N, "backward" if s == "forward" else s))
+    ref = (_real_space_green2(shape, "forward", 1.4, 0.9) @ tau.ravel()).reshape(tau.shape)
+    bad = _fourier_apply2(tau, "forward", 1.4, 0.9).real
+    assert not np.allclose(bad, ref, atol=1e-6 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("scheme", dense2d.SCHEMES)
+def test_2d_green_identities(scheme):
+    """Hermitian, Gamma C0 Gamma = Gamma (Direct: off its Nyquist lines), and
+    Gamma(-xi mod N) = conj(Gamma(xi)) on an 8 x 6 grid."""
+    shape = (8, 6)
+    lam0, mu0 = 2.1, 0.6
+    C0 = dense2d.stiffness_voigt2(lam0, mu0)
+    G = dense2d.green_field2(shape, lam0, mu0, scheme)
+    assert np.allclose(G, np.conj(np.swapaxes(G, -1, -2)), atol=1e-13)
+    keep = np.ones(shape, dtype=bool)
+    if scheme == "direct":
+        keep[shape[0] // 2, :] = False
+        keep[:, shape[1] // 2] = False
+    assert np.allclose((G @ C0 @ G)[keep], G[keep], atol=1e-12)
+    mirror = G[np.ix_(*[(-np.arange(N)) % N for N in shape])]
+    assert np.allclose(mirror, np.conj(G), atol=1e-13)
