@@ -411,12 +411,94 @@ def matrix_to_mpo(M: np.ndarray, n: int, eps: float, rmax: int = 1 << 30):
     return [c.reshape(c.shape[0], 2, 2, c.shape[2]) for c in cores]
 
 
-def sfft_axis_mpo(n: int, eps: float = 1e-14):
-    """The SFFT (reduced QFT) of one axis as an MPO (Sec. 4.1-4.2)."""
+def sfft_axis_mpo(n: int, eps: float = 1e-12):
+    """The SFFT (reduced QFT) of one axis as an MPO (Sec. 4.1-4.2), by TT-SVD of
+    the dense matrix. The default accuracy 1e-12 gives the circuit's own ranks
+    (sfft_axis_mpo_zipup) with the DFT reproduced to ~1e-14; at 1e-14, the
+    SVD's noise level, rounding-noise directions pass the threshold (n = 8:
+    ranks up to 127 instead of 12)."""
     return matrix_to_mpo(sfft_dense(n), n, eps)
 
 
-def sfft_operator(n: int, eps: float = 1e-14, adjoint: bool = False):
+def qft_circuit_gates(n: int):
+    """The reduced QFT circuit of Sec. 4.1 (Hadamard and controlled-phase gates,
+    without the SWAP network) on n qubits, qubit b carrying bit b of the input
+    index MSB first, as gate MPOs in the order they act: for qubit q, H on q,
+    then cP(pi / 2^(m - q)) between q and every less significant qubit m > q.
+    Each cP is split, as Sec. 4.2 describes, into a copy tensor on q (bond
+    index = the bit of q) and a phase tensor on m (identity for bond 0,
+    P(theta) for bond 1), with identity pass-through cores between them.
+    Gate MPO cores have the layout (r, out, in, r')."""
+    I2 = np.eye(2, dtype=np.complex128)
+    H = np.array([[1, 1], [1, -1]], dtype=np.complex128) / math.sqrt(2.0)
+
+    def single(q, U):
+        g = [I2.reshape(1, 2, 2, 1) for _ in range(n)]
+        g[q] = U.reshape(1, 2, 2, 1)
+        return g
+
+    def cphase(q, m, theta):
+        g = [I2.reshape(1, 2, 2, 1) for _ in range(n)]
+        copy = np.zeros((1, 2, 2, 2), dtype=np.complex128)
+        for a in range(2):
+            copy[0, a, a, a] = 1.0
+        g[q] = copy
+        for s in range(q + 1, m):
+            w = np.zeros((2, 2, 2, 2), dtype=np.complex128)
+            for a in range(2):
+                w[a, :, :, a] = I2
+            g[s] = w
+        ph = np.zeros((2, 2, 2, 1), dtype=np.complex128)
+        ph[0, :, :, 0] = I2
+        ph[1, :, :, 0] = np.diag([1.0, np.exp(1j * theta)])
+        g[m] = ph
+        return g
+
+    gates = []
+    for q in range(n):
+        gates.append(single(q, H))
+        for m in range(q + 1, n):
+            gates.append(cphase(q, m, math.pi / (1 << (m - q))))
+    return gates
+
+
+def mpo_zipup(G, W, eps: float):
+    """G W (W acts first) by the zip-up sweep of Sec. 4.2: left to right, the
+    carried factor is contracted with the site's two cores, the result is
+    reshaped to (carried rank x out x in, bond of G x bond of W), split by an
+    SVD truncated at relative accuracy eps, and the left factor is kept as the
+    site's core while S V^H moves on to the next site."""
+    n = len(W)
+    carry = np.ones((1, 1, 1), dtype=np.complex128)       # (R, g, w)
+    cores = []
+    for b in range(n):
+        T = np.einsum("Rgw,gomh,wmiv->Roihv", carry, G[b], W[b])
+        R, o, i, h, v = T.shape
+        if b == n - 1:
+            cores.append(T.reshape(R, o, i, h * v))
+            break
+        U, S, Vh = np.linalg.svd(T.reshape(R * o * i, h * v), full_matrices=False)
+        k = max(1, int(np.sum(S > eps * S[0]))) if S[0] > 0 else 1
+        cores.append(U[:, :k].reshape(R, o, i, k))
+        carry = (S[:k, None] * Vh[:k]).reshape(k, h, v)
+    return cores
+
+
+def sfft_axis_mpo_zipup(n: int, eps: float = 1e-14):
+    """The SFFT MPO of one axis built the way Sec. 4.2 builds it: the reduced QFT
+    circuit's gates applied one after the other to the identity MPO by zip-up
+    sweeps, then one TT rounding at eps (the cores as a TT with mode size 4)
+    to reach the minimal ranks."""
+    I2 = np.eye(2, dtype=np.complex128)
+    op = [I2.reshape(1, 2, 2, 1) for _ in range(n)]
+    for g in qft_circuit_gates(n):
+        op = mpo_zipup(g, op, 1e-15)
+    flat = [c.reshape(c.shape[0], 4, c.shape[3]) for c in op]
+    flat, _ = tt_round(flat, eps, 1 << 30)
+    return [c.reshape(c.shape[0], 2, 2, c.shape[2]) for c in flat]
+
+
+def sfft_operator(n: int, eps: float = 1e-12, adjoint: bool = False):
     """3D SFFT TTO on the controlled QTT: identity Voigt core, then the axis
     MPOs of x1, x2, x3 joined by rank-1 bonds (Sec. 4.3). adjoint -> S^H = S^-1."""
     ax = sfft_axis_mpo(n, eps)

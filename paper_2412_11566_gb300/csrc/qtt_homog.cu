@@ -2178,11 +2178,19 @@ qtt_op* build_gamma(qtt_ctx* c, int n, double lam0, double mu0, int scheme, doub
   return o;
 }
 
+// The solver's SFFT MPOs are rounded at 1e-12. The reduced QFT circuit
+// (Sec. 4.1-4.2) has ranks 2^min(b, n-b) (at most 11-12 for n = 8 within
+// 1e-12), and rounding at 1e-12 reproduces the DFT to ~1e-14. Rounding at
+// 1e-14, the level of the SVD's own rounding noise, keeps noise directions
+// instead (ranks up to ~127 at n = 8), which only widens every S and S^H
+// product.
+constexpr double kSfftRoundEps = 1e-12;
+
 qtt_op* cached_sfft(qtt_ctx* c, int n, int adjoint) {
   auto key = std::make_pair(n, adjoint);
   auto it = c->sfft_cache.find(key);
   if (it != c->sfft_cache.end()) return it->second;
-  qtt_op* o = build_sfft(c, n, adjoint, 1e-14);
+  qtt_op* o = build_sfft(c, n, adjoint, kSfftRoundEps);
   c->sfft_cache[key] = o;
   return o;
 }

@@ -103,6 +103,37 @@ def test_sfft_mpo_rank_printed_value():
     assert max(c.shape[0] for c in oq.matrix_to_mpo(full_dft, n, 1e-10)) > 2 * g["value"]
 
 
+@pytest.mark.parametrize("n", [1, 2, 4, 6, 8])
+def test_sfft_zipup_circuit_equals_dense_and_ranks(n):
+    """Sec. 4.2: the reduced QFT circuit (Hadamards and controlled phases split
+    into copy and phase tensors) taken to an MPO by zip-up sweeps is the SFFT
+    S = P_rev F+ of Sec. 4.1 (and so the momentum convention of Sec. 4.3
+    follows from the circuit), and the TT-SVD MPO of the dense matrix at the
+    solver's accuracy 1e-12 has exactly the circuit MPO's ranks."""
+    z = oq.sfft_axis_mpo_zipup(n, 1e-12)
+    assert np.allclose(oq.tto_full(z), oq.sfft_dense(n), atol=1e-13)
+    assert [c.shape[0] for c in z] == [c.shape[0] for c in oq.sfft_axis_mpo(n, 1e-12)]
+    assert max(c.shape[0] for c in z) <= 1 << (n // 2)
+
+
+def test_sfft_zipup_printed_rank_and_planted_gate_mistakes():
+    """The circuit construction reaches the printed SFFT rank (10 at 1e-10 for
+    n = 8, Sec. 5.2); dropping one controlled phase or flipping the phase sign
+    gives a different operator."""
+    g = json.load(open(os.path.join(GOLD, "paper_values.json")))["sfft_mpo_rank"]
+    z = oq.sfft_axis_mpo_zipup(8, g["delta_acc"])
+    assert max(c.shape[0] for c in z) == g["value"]
+    n = 4
+    I2 = np.eye(2, dtype=np.complex128)
+    gates = oq.qft_circuit_gates(n)
+    for bad in (gates[:2] + gates[3:],
+                [[np.conj(c) for c in gt] for gt in gates]):
+        op = [I2.reshape(1, 2, 2, 1) for _ in range(n)]
+        for gt in bad:
+            op = oq.mpo_zipup(gt, op, 1e-15)
+        assert not np.allclose(oq.tto_full(op), oq.sfft_dense(n), atol=1e-6)
+
+
 def test_sfft_3d_operator_and_inverse():
     n = 2
     N = 1 << n
