@@ -14,7 +14,10 @@ Modules:
             without dense's Green operator so that the two can be compared.
   qtt    -- Oracle B: tensor-train primitives, the SFFT/Green/stiffness operators
             and the SFFT-based scheme (Alg. 2), in the same step order as the
-            CUDA path so that FP64 results can be compared to 1e-10.
+            CUDA path so that FP64 results can be compared to 1e-10; also the
+            paper's own constructions the CUDA path replaces, to compare with:
+            the SFFT MPO from the QFT circuit by zip-up (Sec. 4.2) and the
+            AMEn-adapted product (App. B).
 
 Every function names the passage of the paper it restates.
 

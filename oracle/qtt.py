@@ -374,6 +374,118 @@ def tto_apply_sketched(op, x, ell: int, seed: int, apply_id: int):
     return out
 
 
+def _right_orth_tt(cores):
+    """Right-orthogonalised copy (cores 1..L-1 with orthonormal rows)."""
+    return tt_right_orthogonalize(cores)
+
+
+def tto_apply_amen(op, x, eps: float, rmax: int = 1 << 30, y0=None, kick: int = 4,
+                   sweeps: int = 20, seed: int = 0, tol_change: float = None):
+    """Compressed product y ~ A x by the AMEn-adapted scheme of App. B.
+
+    y minimises ||y - A x|| core by core. With the other cores of y orthonormal
+    (left of core k and right of it), the local minimiser is the Galerkin
+    projection y_k = Y_{<k}^H (A x) Y_{>k}^H, formed from left and right
+    environments of the projections of A x onto y's frames. After each local
+    update the core is truncated (SVD at eps / sqrt(L - 1), rank cap rmax) and
+    enriched: an approximate residual z ~ A x - y, a TT of rank `kick` kept
+    up to date by the same projections onto its own frames, gives the
+    residual projected onto y's left frame and z's right frame; these columns
+    are appended to the core, a QR re-orthonormalises it, and the remainder
+    moves into core k + 1 (the Galerkin correction that adapts the rank).
+    Sweeps go left to right, each preceded by a right orthogonalisation of y
+    and z, until the relative change of y between two sweeps is below
+    tol_change (eps by default). Ends with a TT rounding at (eps, rmax).
+    Returns (y, sweeps done). op: cores (a, o, i, a'); x: cores (s, i, t)."""
+    L = len(op)
+    rng = np.random.default_rng(seed)
+    dims = [W.shape[1] for W in op]
+    tol_change = eps if tol_change is None else tol_change
+
+    def rand_tt(r):
+        rk = [1] + [r] * (L - 1) + [1]
+        return [(rng.standard_normal((rk[k], dims[k], rk[k + 1]))
+                 + 1j * rng.standard_normal((rk[k], dims[k], rk[k + 1]))) for k in range(L)]
+
+    y = [c.astype(np.complex128) for c in (rand_tt(2) if y0 is None else y0)]
+    z = rand_tt(kick)
+    d2 = 1.0 / max(L - 1, 1)
+    td = np.tensordot
+
+    # The contractions below take x's core, then A's core, then the frame's:
+    # the rank r(A) r(x) product core is never formed.
+    def right_env(F, W, X, R):
+        """sum conj(F[p, o, u]) W[a, o, i, b] X[s, i, t] R[u, b, t] -> [p, a, s]"""
+        A2 = td(td(X, R, axes=([2], [2])), W, axes=([1, 3], [2, 3]))    # (s, u, a, o)
+        return td(F.conj(), A2, axes=([1, 2], [3, 1])).transpose(0, 2, 1)
+
+    def left_apply(Lenv, W, X):
+        """sum Lenv[p, a, s] W[a, o, i, b] X[s, i, t] -> [p, o, b, t]"""
+        C2 = td(td(Lenv, X, axes=([2], [0])), W, axes=([1, 2], [0, 2]))  # (p, t, o, b)
+        return C2.transpose(0, 2, 3, 1)
+
+    def frame_overlap_right(Z, Y, R):
+        """sum conj(Z[q, o, v]) Y[p, o, u] R[v, u] -> [q, p]"""
+        return td(Z.conj(), td(Y, R, axes=([2], [1])), axes=([1, 2], [1, 2]))
+
+    prev = None
+    done = 0
+    for sw in range(sweeps):
+        y = _right_orth_tt(y)
+        z = _right_orth_tt(z)
+        # right environments: projections of A x and of y onto the right frames
+        Ry = [None] * (L + 1)
+        Rz = [None] * (L + 1)
+        Rzy = [None] * (L + 1)
+        Ry[L] = np.ones((1, 1, 1), dtype=np.complex128)
+        Rz[L] = np.ones((1, 1, 1), dtype=np.complex128)
+        Rzy[L] = np.ones((1, 1), dtype=np.complex128)
+        for k in range(L - 1, 0, -1):
+            Ry[k] = right_env(y[k], op[k], x[k], Ry[k + 1])
+            Rz[k] = right_env(z[k], op[k], x[k], Rz[k + 1])
+            Rzy[k] = frame_overlap_right(z[k], y[k], Rzy[k + 1])
+        Ly = np.ones((1, 1, 1), dtype=np.complex128)
+        Lz = np.ones((1, 1, 1), dtype=np.complex128)
+        Lzy = np.ones((1, 1), dtype=np.complex128)
+        for k in range(L):
+            W, X = op[k], x[k]
+            LWX = left_apply(Ly, W, X)                                  # (p, o, b, t)
+            yk = td(LWX, Ry[k + 1], axes=([2, 3], [1, 2]))              # Galerkin core
+            if k == L - 1:
+                y[k] = yk
+                break
+            p, o, u = yk.shape
+            U, S, Vh = _svd(yk.reshape(p * o, u))
+            nrm2 = float(np.sum(S ** 2))
+            kk, _ = truncation_rank(S, eps * eps * nrm2 * d2, rmax)
+            yt = ((U[:, :kk] * S[:kk]) @ Vh[:kk]).reshape(p, o, u)     # truncated core
+            # residual z_k = proj_z(A x) - proj_z(y), then orthonormalised
+            LzWX = left_apply(Lz, W, X)                                 # (q, o, b, t)
+            zk = (td(LzWX, Rz[k + 1], axes=([2, 3], [1, 2]))
+                  - td(td(Lzy, yt, axes=([1], [0])), Rzy[k + 1], axes=([2], [1])))
+            qz, _ = np.linalg.qr(zk.reshape(-1, zk.shape[2]))
+            z[k] = qz.reshape(zk.shape[0], o, qz.shape[1])
+            # enrichment: the residual on y's left frame and z's right frame
+            ek = (td(LWX, Rz[k + 1], axes=([2, 3], [1, 2]))
+                  - td(yt, Rzy[k + 1], axes=([2], [1])))
+            Q, _ = np.linalg.qr(np.concatenate([U[:, :kk], ek.reshape(p * o, -1)], axis=1))
+            y[k] = Q.reshape(p, o, Q.shape[1])
+            carry = Q.conj().T @ yt.reshape(p * o, u)                   # r_new x u
+            y[k + 1] = td(carry, y[k + 1], axes=([1], [0]))
+            # left environments with the new cores
+            Ly = td(y[k].conj(), LWX, axes=([0, 1], [0, 1]))            # (x, b, t)
+            Lz = td(z[k].conj(), LzWX, axes=([0, 1], [0, 1]))
+            Lzy = td(z[k].conj(), td(Lzy, y[k], axes=([1], [0])), axes=([0, 1], [0, 1]))
+        done = sw + 1
+        if prev is not None:
+            change = tt_norm(tt_add(y, prev, 1.0, -1.0)) / max(tt_norm(y), 1e-300)
+            if change < tol_change:
+                break
+        prev = [c.copy() for c in y]
+    y, _ = tt_round(y, eps, rmax)
+    return y, done
+
+
 def tto_sandwich_mean(op, x):
     """Mean over the grid of (A x) without forming A x: the binary cores are
     contracted with the averaging vector (1/2, 1/2). Returns the Voigt vector
