@@ -150,6 +150,109 @@ def laminate_with_fibres(n: int, radius: float = 0.06, offset=(0.0, 1.0 / 16),
     return out.astype(np.uint8).reshape(1, N, N)
 
 
+# ------------------------------------------------ the paper's geometry families
+# Sec. 5.1 (Fig. geometries: Laminate, Square, Circle) and App. F (Checkerboard,
+# Spots, Voronoi), as 2D sections of shape (N, N) and in the paper's two 3D
+# generalisations: extruded along x1 (section_3d: Pillar, Circular Pillar,
+# reduced Checkerboard, Fibres) or the same in every direction (Box, Sphere,
+# Checkerboard 3D, Voronoi 3D). The paper gives no sizes; the defaults below
+# are ours: square side L/2, circle radius 0.3 L, 2 x 2 checkerboard tiles,
+# 8 spots of radius 0.08 L, 16 Voronoi seeds.
+
+PAPER_MATERIALS = ((29.0 / 3.0, 4.0 / 3.0), (1.0 / 3.0, 1.0 / 3.0))
+"""(E, nu) of the geometry figures: grey phase E = 29/3 GPa, white E = 4/3 GPa,
+nu = 1/3 for both (phase 1 = grey, phase 0 = white: E = (4/3, 29/3))."""
+
+
+def paper_materials():
+    """(E, nu) per phase index (0 = white matrix, 1 = grey inclusion)."""
+    (e_grey, e_white), (nu_grey, nu_white) = PAPER_MATERIALS
+    return (e_white, e_grey), (nu_white, nu_grey)
+
+
+def laminate2d(n: int, layers: int = 2) -> np.ndarray:
+    """Layers normal to the section's second axis, stiff first: (N, N)."""
+    N = 1 << n
+    return np.ascontiguousarray(np.broadcast_to(laminate(n, layers).reshape(1, N), (N, N)))
+
+
+def square2d(n: int, side: float = 0.5) -> np.ndarray:
+    """Centred square inclusion of the given side (in L): (N, N)."""
+    c = _centres(1 << n)
+    inside = np.abs(c - 0.5) < side / 2
+    return (inside[:, None] & inside[None, :]).astype(np.uint8)
+
+
+def circle2d(n: int, radius: float = 0.3, centre=(0.5, 0.5)) -> np.ndarray:
+    """Disk inclusion (periodic distance): (N, N)."""
+    c = _centres(1 << n)
+    d2 = _periodic(c - centre[0])[:, None] ** 2 + _periodic(c - centre[1])[None, :] ** 2
+    return (d2 <= radius * radius).astype(np.uint8)
+
+
+def checkerboard2d(n: int, tiles: int = 2) -> np.ndarray:
+    """tiles x tiles alternating squares: (N, N)."""
+    N = 1 << n
+    t = (np.arange(N) * tiles) // N
+    return ((t[:, None] + t[None, :]) % 2).astype(np.uint8)
+
+
+def spots2d(n: int, count: int = 8, radius: float = 0.08, seed: int = 2412) -> np.ndarray:
+    """count disks of equal radius at seeded uniform centres, allowed to
+    overlap (union): (N, N)."""
+    rng = np.random.default_rng(seed)
+    out = np.zeros((1 << n, 1 << n), dtype=np.uint8)
+    for cx, cy in rng.random((count, 2)):
+        out |= circle2d(n, radius, (cx, cy))
+    return out
+
+
+def voronoi2d(n: int, seeds: int = 16, seed: int = 2412) -> np.ndarray:
+    """Periodic Voronoi tessellation of seeded uniform points; a cell belongs to
+    phase (index of its point) mod 2: (N, N)."""
+    rng = np.random.default_rng(seed)
+    pts = rng.random((seeds, 2))
+    c = _centres(1 << n)
+    d2 = (_periodic(c[:, None, None] - pts[None, None, :, 0]) ** 2
+          + _periodic(c[None, :, None] - pts[None, None, :, 1]) ** 2)
+    return (np.argmin(d2, axis=2) % 2).astype(np.uint8)
+
+
+def section_3d(section: np.ndarray) -> np.ndarray:
+    """A 2D section extruded along x1: shape (1, N, N) with x1 broadcast."""
+    return np.ascontiguousarray(section[None])
+
+
+def box3d(n: int, side: float = 0.5) -> np.ndarray:
+    """Centred cube inclusion (the Square seen from every direction)."""
+    c = _centres(1 << n)
+    inside = np.abs(c - 0.5) < side / 2
+    return (inside[:, None, None] & inside[None, :, None] & inside[None, None, :]).astype(np.uint8)
+
+
+def checkerboard3d(n: int, tiles: int = 2) -> np.ndarray:
+    """tiles^3 alternating cubes."""
+    N = 1 << n
+    t = (np.arange(N) * tiles) // N
+    return ((t[:, None, None] + t[None, :, None] + t[None, None, :]) % 2).astype(np.uint8)
+
+
+def voronoi3d(n: int, seeds: int = 16, seed: int = 2412) -> np.ndarray:
+    """Periodic 3D Voronoi tessellation, phase = (index of the point) mod 2."""
+    rng = np.random.default_rng(seed)
+    pts = rng.random((seeds, 3))
+    c = _centres(1 << n)
+    best = np.full((1 << n,) * 3, np.inf)
+    lab = np.zeros((1 << n,) * 3, dtype=np.int64)
+    for i, (px, py, pz) in enumerate(pts):
+        d2 = (_periodic(c - px)[:, None, None] ** 2 + _periodic(c - py)[None, :, None] ** 2
+              + _periodic(c - pz)[None, None, :] ** 2)
+        closer = d2 < best
+        best = np.where(closer, d2, best)
+        lab = np.where(closer, i, lab)
+    return (lab % 2).astype(np.uint8)
+
+
 def broadcast_dense(phase: np.ndarray, n: int) -> np.ndarray:
     """Expand broadcast axes of a phase field to the full (N, N, N) grid."""
     N = 1 << n
