@@ -231,7 +231,7 @@ int qtt_gamma_operator(qtt_ctx_t ctx, int n, double lambda0, double mu0, int sch
 int qtt_op_apply(qtt_ctx_t ctx, qtt_op_t op, qtt_tt_t in, double eps_tt, int rmax,
                  int oversample, int apply_id, qtt_tt_t* out);
 /* SFFT, inverse SFFT and Green products with the context's cached operators
- * (built on first use for the TT's n; Sec. 4.3, Alg. 2 lines 2-4, App. D
+ * (built on first use for the TT's n; Sec. 4.3, Alg. 2's transform and Green steps, App. D
  * lookup table). n[3] must be equal (cubic grids). */
 int sfft_apply(qtt_ctx_t ctx, qtt_tt_t in, double eps_tt, int rmax, qtt_tt_t* out);
 int isfft_apply(qtt_ctx_t ctx, qtt_tt_t in, double eps_tt, int rmax, qtt_tt_t* out);
