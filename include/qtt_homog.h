@@ -373,6 +373,18 @@ int qtt_contraction_bench(qtt_ctx_t ctx, int mode, int M, int N, int K, int reps
  * laminate-with-fibres workload stagnated at a residual of 3e-3). Returns
  * QTT_EINVAL for refine_sweeps outside 1..60. */
 int qtt_ctx_set_svd(qtt_ctx_t ctx, int precond, int refine_sweeps);
+/* Green operator of solves whose stiffness operator is broadcast along x1
+ * (a phase field of shape (1, N, N)), Sec. 4.3 on broadcast axes. Such a
+ * strain is x1-invariant, so after the SFFT its x1 bits hold only xi_1 = 0;
+ * with on = 1 the solves (ls_solve, ls_solve_ceff, ls_solve_batched,
+ * ls_solve_jobs and the gradient) use Gamma(0, xi_2, xi_3) (x) I on the x1
+ * cores, built from the 2^(2n)-point plane field instead of the 2^(3n)-point
+ * one. On these fields it acts as the full operator does, its ranks through
+ * the x1 cores are those of its first bond, and it allows n up to 13 (the
+ * full build stops at 9, or 8 for the complex schemes). Operators with
+ * another broadcast pattern keep the full Green operator. Default 0.
+ * Returns QTT_EINVAL for a null context. */
+int qtt_ctx_set_green_broadcast(qtt_ctx_t ctx, int on);
 /* Factorisation precision of an FP32 context (the mixed mode of the
  * method's precision pattern: bulk contractions in FP32, the QR and SVD
  * steps of TT rounding in FP64; Sec. 3 rounding, whose per-bond threshold

@@ -664,6 +664,24 @@ def gamma_qtt(n: int, lam0: float, mu0: float, eps: float, rmax: int = 1 << 30,
     return controlled_field_to_tto(gamma_field_sfft(n, lam0, mu0, scheme), n, eps, rmax)
 
 
+def gamma_qtt_plane(n: int, lam0: float, mu0: float, eps: float, rmax: int = 1 << 30,
+                    scheme: str = "direct"):
+    """Gamma_hat^0 restricted to the plane xi_1 = 0, tensored with the identity
+    on the x1 cores: Voigt core and x2, x3 cores from the TT-SVD of the
+    (6, 6, N, N) plane field (SFFT convention), then n identity cores
+    delta(a, a') I_2 inserted after the Voigt core. On x1-invariant fields,
+    whose SFFT lives at xi_1 = 0 only, it acts as gamma_qtt does (Sec. 4.3,
+    broadcast axes)."""
+    full = gamma_field_sfft(n, lam0, mu0, scheme)   # (6, 6, N1, N2, N3), N1 bit-reversed
+    plane = full[:, :, 0]                             # rev(0) = 0: xi_1 = 0
+    T = plane.reshape((36,) + (2,) * (2 * n))
+    cores = tt_svd(T.astype(np.complex128), eps, rmax)
+    c0 = cores[0].reshape(1, 6, 6, cores[0].shape[2])
+    r1 = c0.shape[3]
+    ident = np.einsum("ab,ij->aijb", np.eye(r1), np.eye(2)).astype(np.complex128)
+    return [c0] + [ident.copy() for _ in range(n)] + raise_tt(cores[1:])
+
+
 # ------------------------------------------------------------------ stiffness operator
 
 

@@ -1013,12 +1013,13 @@ __device__ void green_monomials_at(const double xi[3], double* m15) {
 //     components sit at the Nyquist frequency.
 // At Nyquist modes the value is the average with the aliased partner (the
 // Nyquist components negated); the monomials are even in v, so for schemes 1
-// and 4 the average is the value itself.
-__global__ void green_monomials_kernel(Cx<double>* out, int n, int scheme) {
-  const long long N = 1ll << n, N3 = N * N * N;
+// and 4 the average is the value itself. plane = 1 evaluates only the plane
+// xi_1 = 0: N^2 points (xi_2, xi_3), out[q * N^2 + e].
+__global__ void green_monomials_kernel(Cx<double>* out, int n, int scheme, int plane) {
+  const long long N = 1ll << n, N3 = plane ? N * N : N * N * N;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N3;
        e += (long long)gridDim.x * blockDim.x) {
-    const int ks[3] = {(int)(e / (N * N)), (int)((e / N) % N), (int)(e % N)};
+    const int ks[3] = {plane ? 0 : (int)(e / (N * N)), (int)((e / N) % N), (int)(e % N)};
     double xi[3], xf[3], hs[3], hc[3];
     bool nyq = false;
     for (int a = 0; a < 3; ++a) {
@@ -1145,13 +1146,14 @@ __host__ __device__ inline void green_symbol_voigt_conj(const double2 kn[3], con
 // operators unchanged. Stored in the SFFT convention (its transform sign is
 // opposite to the one the symbols are written for, and Gamma(-xi) =
 // conj(Gamma(xi))): out[(I * 6 + J) * N3 + e] = conj(Gamma_V[I][J]) at the
-// frequency of bit-reversed index e.
+// frequency of bit-reversed index e. plane = 1 evaluates only the plane
+// xi_1 = 0 (N3 = N^2 points).
 __global__ void green_symbol_field_kernel(Cx<double>* out, int n, double lam0, double mu0,
-                                          int scheme) {
-  const long long N = 1ll << n, N3 = N * N * N;
+                                          int scheme, int plane) {
+  const long long N = 1ll << n, N3 = plane ? N * N : N * N * N;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N3;
        e += (long long)gridDim.x * blockDim.x) {
-    const int ks[3] = {(int)(e / (N * N)), (int)((e / N) % N), (int)(e % N)};
+    const int ks[3] = {plane ? 0 : (int)(e / (N * N)), (int)((e / N) % N), (int)(e % N)};
     double2 kp[3], km[3];
     double nrm2 = 0;
     for (int a = 0; a < 3; ++a) {

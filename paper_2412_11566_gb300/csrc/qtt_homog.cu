@@ -241,6 +241,10 @@ struct qtt_ctx {
   ProfBuf prof;
   std::map<std::pair<int, int>, qtt_op*> sfft_cache;                            // (n, adjoint)
   std::map<std::tuple<int, double, double, int, double, int>, qtt_op*> gamma_cache;
+  // Green operators restricted to xi_1 = 0 (identity x1 cores) for stiffness
+  // operators broadcast along x1, when green_broadcast is set
+  int green_broadcast = 0;
+  std::map<std::tuple<int, double, double, int, double, int>, qtt_op*> gamma_plane_cache;
   // TT of the 15 Green monomial fields per (n, eps, rmax), FP64, in the arena
   struct GreenMono {
     std::vector<void*> cores;
@@ -295,6 +299,7 @@ struct qtt_op {
   int diag[QTT_MAX_CORES] = {0};
   void* core[QTT_MAX_CORES] = {nullptr};
   int n = 0;
+  int bcast[3] = {0, 0, 0};  // axes carried by identity cores (raised operators of fields)
   int has_c0 = 0;
   double lame0[2] = {0, 0};
   double C0[36] = {0};
@@ -1991,8 +1996,10 @@ qtt_op* assemble_raised(qtt_ctx* c, Eng<double>& e, std::vector<Cx<double>*>& tc
         ++src;
       }
     }
-  return c->prec == QTT_FP64 ? op_from_fp64<double>(c, cores, R, dout, din, diag)
-                             : op_from_fp64<float>(c, cores, R, dout, din, diag);
+  qtt_op* o = c->prec == QTT_FP64 ? op_from_fp64<double>(c, cores, R, dout, din, diag)
+                                  : op_from_fp64<float>(c, cores, R, dout, din, diag);
+  for (int a = 0; a < 3; ++a) o->bcast[a] = bcast[a] ? 1 : 0;
+  return o;
 }
 
 // Raised operator of a phase field whose cells carry one of nphase Voigt
@@ -2112,7 +2119,7 @@ qtt_op* build_gamma_symbol(qtt_ctx* c, int n, double lam0, double mu0, int schem
   Eng<double> e(c);
   const long long N3 = 1ll << (3 * n);
   Cx<double>* F = e.alloc(36 * N3);
-  green_symbol_field_kernel<<<grid1d(N3), 256, 0, e.st()>>>(F, n, lam0, mu0, scheme);
+  green_symbol_field_kernel<<<grid1d(N3), 256, 0, e.st()>>>(F, n, lam0, mu0, scheme, 0);
   e.post("green_symbol_field_kernel", __LINE__);
   const int bc[3] = {0, 0, 0};
   qtt_op* o = raised_from_field(c, F, n, bc, eps, rmax);  // consumes F
@@ -2139,7 +2146,7 @@ qtt_op* build_gamma(qtt_ctx* c, int n, double lam0, double mu0, int scheme, doub
   if (it == c->green_mono_cache.end()) {
     const long long N3 = 1ll << (3 * n);
     Cx<double>* F = e.alloc(15 * N3);
-    green_monomials_kernel<<<grid1d(N3), 256, 0, e.st()>>>(F, n, scheme);
+    green_monomials_kernel<<<grid1d(N3), 256, 0, e.st()>>>(F, n, scheme, 0);
     e.post("green_monomials_kernel", __LINE__);
     std::vector<int> dims(1 + 3 * n, 2), ranks;
     dims[0] = 15;
@@ -2202,6 +2209,71 @@ qtt_op* cached_gamma(qtt_ctx* c, int n, double lam0, double mu0, int scheme, dou
   qtt_op* o = build_gamma(c, n, lam0, mu0, scheme, eps, rmax);
   c->gamma_cache[key] = o;
   return o;
+}
+
+// Green operator for stiffness operators broadcast along x1. The strain of
+// such a problem is x1-invariant, so after the SFFT its x1 bits hold only the
+// frequency xi_1 = 0, where Gamma acts as Gamma(0, xi_2, xi_3); the operator
+// Gamma(0, xi_2, xi_3) (x) I on the x1 cores acts on these fields exactly as
+// the full operator does (Sec. 4.3 on broadcast axes). It is built from the
+// N^2-point plane field instead of the N^3 one: the 15 monomial fields for the
+// Direct, Centered and Hex8R schemes (mixed into the 36 Voigt entries through
+// the first core), the 36 entries for the others. Its rank through the x1
+// cores is that of the first bond. n <= 13 (2^31-row TT-SVD unfoldings).
+qtt_op* build_gamma_plane(qtt_ctx* c, int n, double lam0, double mu0, int scheme, double eps,
+                          int rmax) {
+  QREQ(scheme >= QTT_SCHEME_DIRECT && scheme <= QTT_SCHEME_STAGGERED,
+       "gamma (plane): scheme must be 0..5");
+  QREQ(n >= 1 && n <= 13, "gamma (plane): n must be in 1..13");
+  QREQ(mu0 > 0 && lam0 + 2 * mu0 > 0, "gamma: reference medium not positive definite");
+  Eng<double> e(c);
+  const long long N2 = 1ll << (2 * n);
+  const int bc[3] = {1, 0, 0};
+  qtt_op* o = nullptr;
+  if (scheme == QTT_SCHEME_FORWARD || scheme == QTT_SCHEME_BACKWARD ||
+      scheme == QTT_SCHEME_STAGGERED) {
+    Cx<double>* F = e.alloc(36 * N2);
+    green_symbol_field_kernel<<<grid1d(N2), 256, 0, e.st()>>>(F, n, lam0, mu0, scheme, 1);
+    e.post("green_symbol_field_kernel", __LINE__);
+    o = raised_from_field(c, F, n, bc, eps, rmax);  // consumes F
+  } else {
+    Cx<double>* F = e.alloc(15 * N2);
+    green_monomials_kernel<<<grid1d(N2), 256, 0, e.st()>>>(F, n, scheme, 1);
+    e.post("green_monomials_kernel", __LINE__);
+    std::vector<double> Ch(36 * 15), U(2 * 36 * 15, 0.0);
+    green_coeffs(lam0, mu0, Ch.data());
+    for (int P = 0; P < 36; ++P)
+      for (int g = 0; g < 15; ++g) U[2 * (P + 36 * g)] = Ch[P * 15 + g];  // column-major 36 x 15
+    Cx<double>* Ud = e.alloc(36 * 15);
+    QCHECK(cudaMemcpyAsync(Ud, U.data(), U.size() * sizeof(double), cudaMemcpyHostToDevice,
+                           e.st()));
+    QCHECK(e.ln->wait());
+    o = raised_from_field(c, F, n, bc, eps, rmax, 15, Ud);  // consumes F
+    QCHECK(e.ln->wait());
+    e.release(Ud);
+  }
+  o->n = n;
+  o->has_c0 = 1;
+  o->lame0[0] = lam0;
+  o->lame0[1] = mu0;
+  voigt_stiffness(lam0, mu0, o->C0);
+  return o;
+}
+
+// The Green operator a solve with stiffness operator d uses: the plane form
+// when the context asks for it and d is broadcast along x1 only, else the
+// full operator.
+qtt_op* solve_gamma(qtt_ctx* c, const qtt_op* d, const qtt_solve_params* p) {
+  if (c->green_broadcast && d->bcast[0] && !d->bcast[1] && !d->bcast[2]) {
+    auto key = std::make_tuple(d->n, d->lame0[0], d->lame0[1], p->scheme, p->eps_tt, 1 << 30);
+    auto it = c->gamma_plane_cache.find(key);
+    if (it != c->gamma_plane_cache.end()) return it->second;
+    qtt_op* o = build_gamma_plane(c, d->n, d->lame0[0], d->lame0[1], p->scheme, p->eps_tt,
+                                  1 << 30);
+    c->gamma_plane_cache[key] = o;
+    return o;
+  }
+  return cached_gamma(c, d->n, d->lame0[0], d->lame0[1], p->scheme, p->eps_tt, 1 << 30);
 }
 
 // E field as a rank-1 controlled QTT: Voigt core E sqrt(2)^(3n), binary
@@ -2405,6 +2477,7 @@ void qtt_ctx_destroy(qtt_ctx_t c) {
   prof_flush(c);
   for (auto& kv : c->sfft_cache) free_op(kv.second);
   for (auto& kv : c->gamma_cache) free_op(kv.second);
+  for (auto& kv : c->gamma_plane_cache) free_op(kv.second);
   for (auto& kv : c->green_mono_cache)
     for (void* p : kv.second.cores) c->arena.release(p);
   if (c->pinned) cudaFreeHost(c->pinned);
@@ -2827,7 +2900,7 @@ int ls_solve(qtt_ctx_t ctx, qtt_op_t dC, const double E_voigt[6], const qtt_solv
   const int n = dC->n;
   qtt_op* S = cached_sfft(ctx, n, 0);
   qtt_op* Sh = cached_sfft(ctx, n, 1);
-  qtt_op* G = cached_gamma(ctx, n, dC->lame0[0], dC->lame0[1], p->scheme, p->eps_tt, 1 << 30);
+  qtt_op* G = solve_gamma(ctx, dC, p);
   return DISPATCH(ctx, solve_impl, ctx, dC, S, Sh, G, dC->C0, E_voigt, p, sigma_bar, info, 0);
   API_END
 }
@@ -2952,7 +3025,7 @@ int solve_loads(qtt_ctx_t ctx, qtt_op_t dC, const qtt_solve_params* p, const int
   const int n = dC->n;
   qtt_op* S = cached_sfft(ctx, n, 0);
   qtt_op* Sh = cached_sfft(ctx, n, 1);
-  qtt_op* G = cached_gamma(ctx, n, dC->lame0[0], dC->lame0[1], p->scheme, p->eps_tt, 1 << 30);
+  qtt_op* G = solve_gamma(ctx, dC, p);
   QCHECK(cudaStreamSynchronize(ctx->stream));
   std::vector<SolveJob> jobs(nloads);
   for (int l = 0; l < nloads; ++l) {
@@ -2990,7 +3063,7 @@ int solve_jobs(qtt_ctx_t ctx, int njobs, const qtt_op_t* dC, const int* load,
     J.dC = d;
     J.S = cached_sfft(ctx, d->n, 0);
     J.Sh = cached_sfft(ctx, d->n, 1);
-    J.G = cached_gamma(ctx, d->n, d->lame0[0], d->lame0[1], p->scheme, p->eps_tt, 1 << 30);
+    J.G = solve_gamma(ctx, d, p);
     J.load = load[j];
   }
   QCHECK(cudaStreamSynchronize(ctx->stream));
@@ -3024,7 +3097,7 @@ int solve_batched(qtt_ctx_t ctx, int nitems, const qtt_op_t* dC, const qtt_solve
     const qtt_op* d = dC[i];
     qtt_op* S = cached_sfft(ctx, d->n, 0);
     qtt_op* Sh = cached_sfft(ctx, d->n, 1);
-    qtt_op* G = cached_gamma(ctx, d->n, d->lame0[0], d->lame0[1], p->scheme, p->eps_tt, 1 << 30);
+    qtt_op* G = solve_gamma(ctx, d, p);
     for (int k = 0; k < 6; ++k) {
       SolveJob& J = jobs[(size_t)i * 6 + k];
       J.dC = d;
@@ -3266,6 +3339,12 @@ int qtt_contraction_bench(qtt_ctx_t ctx, int mode, int M, int N, int K, int reps
   d.release(C64);
   return QTT_OK;
   API_END
+}
+
+int qtt_ctx_set_green_broadcast(qtt_ctx_t ctx, int on) {
+  if (!ctx) return QTT_EINVAL;
+  ctx->green_broadcast = on ? 1 : 0;
+  return QTT_OK;
 }
 
 int qtt_ctx_set_svd(qtt_ctx_t ctx, int precond, int refine_sweeps) {

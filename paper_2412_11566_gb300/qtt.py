@@ -108,6 +108,7 @@ _sig("qtt_ctx_set_tt_svd", _i, [_p, _d])
 _sig("qtt_ctx_set_contraction", _i, [_p, _i])
 _sig("qtt_ctx_set_factorization", _i, [_p, _i])
 _sig("qtt_ctx_set_svd", _i, [_p, _i, _i])
+_sig("qtt_ctx_set_green_broadcast", _i, [_p, _i])
 _sig("qtt_contraction_bench", _i, [_p, _i, _i, _i, _i, _i, _dp, _dp])
 _sig("ls_solve_ceff", _i, [_p, _p, C.POINTER(SolveParams), _ip, _i, _dp, C.POINTER(SolveInfo)])
 _sig("ls_solve_batched", _i, [_p, _i, C.POINTER(_p), C.POINTER(SolveParams), _dp,
@@ -199,6 +200,11 @@ class Context:
     def set_factorization(self, mode: int):
         """QTT_FACTOR_NATIVE or QTT_FACTOR_FP64 (FP32 contexts)."""
         self.check(lib.qtt_ctx_set_factorization(self.h, int(mode)))
+
+    def set_green_broadcast(self, on: bool = True):
+        """Plane Green operator for x1-broadcast stiffness operators (see
+        qtt_ctx_set_green_broadcast)."""
+        self.check(lib.qtt_ctx_set_green_broadcast(self.h, int(on)))
 
     def set_svd(self, precond: bool = True, refine_sweeps: int = 6):
         """FP64 SVD path for matrices beyond shared memory (see qtt_ctx_set_svd)."""
