@@ -592,30 +592,33 @@ def main():
             line["tensor_core_contraction"] = {"failed": str(ex)}
         # ---- plain FP64 single-instance form (one load at a time), sampled
         if time_left() > 200:
-            c64 = ctx if prec == Q.QTT_FP64 else Q.Context(local, Q.QTT_FP64, 32 << 30, seed=2412)
-            c64.set_concurrency(1)
-            i0 = timed_jobs[0][0]
-            dC = Q.qtt_from_phase_field(c64, host_phase(i0), fam[i0].n, fam[i0].E, fam[i0].nu,
-                                        None, fam[i0].eps_tt, fam[i0].rmax)
-            ns = 3
-            Q.ls_solve_ceff(c64, dC, Q.solve_params(w0.tol, 1, w0.eps_tt, w0.rmax, 0, 16),
-                            loads=[0])
-            torch.cuda.synchronize()
-            t = time.perf_counter()
-            Q.ls_solve_ceff(c64, dC, Q.solve_params(w0.tol, ns, w0.eps_tt, w0.rmax, 0, 16),
-                            loads=[0])
-            t_it = (time.perf_counter() - t) / ns
-            dC.free()
-            if c64 is not ctx:
-                c64.close()
-            it_mean = float(np.mean(iters))
-            plain = 1.0 / (t_it * it_mean)
-            line["plain_fp64_gpu"] = {
-                "value": plain, "unit": UNIT, "s_per_iteration": t_it,
-                "sample": f"FP64 context, one load at a time (item {i0}, load e11): {ns} "
-                          f"iterations timed, scaled by the {it_mean:.1f} iterations of the "
-                          f"timed batch's solves",
-                "value_over_plain": value / plain}
+            try:
+                c64 = ctx if prec == Q.QTT_FP64 else Q.Context(local, Q.QTT_FP64, 32 << 30, seed=2412)
+                c64.set_concurrency(1)
+                i0 = timed_jobs[0][0]
+                dC = Q.qtt_from_phase_field(c64, host_phase(i0), fam[i0].n, fam[i0].E, fam[i0].nu,
+                                            None, fam[i0].eps_tt, fam[i0].rmax)
+                ns = 3
+                Q.ls_solve_ceff(c64, dC, Q.solve_params(w0.tol, 1, w0.eps_tt, w0.rmax, 0, 16),
+                                loads=[0])
+                torch.cuda.synchronize()
+                t = time.perf_counter()
+                Q.ls_solve_ceff(c64, dC, Q.solve_params(w0.tol, ns, w0.eps_tt, w0.rmax, 0, 16),
+                                loads=[0])
+                t_it = (time.perf_counter() - t) / ns
+                dC.free()
+                if c64 is not ctx:
+                    c64.close()
+                it_mean = float(np.mean(iters))
+                plain = 1.0 / (t_it * it_mean)
+                line["plain_fp64_gpu"] = {
+                    "value": plain, "unit": UNIT, "s_per_iteration": t_it,
+                    "sample": f"FP64 context, one load at a time (item {i0}, load e11): {ns} "
+                              f"iterations timed, scaled by the {it_mean:.1f} iterations of the "
+                              f"timed batch's solves",
+                    "value_over_plain": value / plain}
+            except Exception as ex:  # noqa: BLE001
+                line["plain_fp64_gpu"] = {"failed": str(ex)}
         # ---- CPU oracle sample
         if time_left() > 90:
             try:
@@ -636,48 +639,89 @@ def main():
         # ---- one microstructure at a time: the 6 loads of the single
         # laminate-with-fibres workload on 6 lanes
         if time_left() > 200:
-            w1 = workload("lamfib256")
-            ref1 = golden("lamfib256")
-            ctx.set_concurrency(6)
-            ph1 = torch.from_numpy(np.ascontiguousarray(w1.phase)).pin_memory().numpy()
-            dC = Q.qtt_from_phase_field(ctx, ph1, w1.n, w1.E, w1.nu, None, w1.eps_tt, w1.rmax)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            C1, inf1, _ = Q.ls_solve_ceff(ctx, dC, params)
-            e1.record(stream)
-            e1.synchronize()
-            dC.free()
-            q1 = qualifying(C1, inf1, ref1, w1.tol)
-            line["single_microstructure"] = {
-                "workload": DESCR["lamfib256"], "lanes": 6,
-                "solves_qualifying": len(q1), "solves_per_s": len(q1) / (e0.elapsed_time(e1) / 1e3),
-                "iters_per_load": [i["iters"] for i in inf1],
-                "ceff_rel_err_vs_dense_oracle": ceff_errors(C1, ref1)}
+            try:
+                w1 = workload("lamfib256")
+                ref1 = golden("lamfib256")
+                ctx.set_concurrency(6)
+                ph1 = torch.from_numpy(np.ascontiguousarray(w1.phase)).pin_memory().numpy()
+                dC = Q.qtt_from_phase_field(ctx, ph1, w1.n, w1.E, w1.nu, None, w1.eps_tt, w1.rmax)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                C1, inf1, _ = Q.ls_solve_ceff(ctx, dC, params)
+                e1.record(stream)
+                e1.synchronize()
+                dC.free()
+                q1 = qualifying(C1, inf1, ref1, w1.tol)
+                line["single_microstructure"] = {
+                    "workload": DESCR["lamfib256"], "lanes": 6,
+                    "solves_qualifying": len(q1), "solves_per_s": len(q1) / (e0.elapsed_time(e1) / 1e3),
+                    "iters_per_load": [i["iters"] for i in inf1],
+                    "ceff_rel_err_vs_dense_oracle": ceff_errors(C1, ref1)}
+            except Exception as ex:  # noqa: BLE001
+                line["single_microstructure"] = {"failed": str(ex)}
+        # ---- the same six loads with the plane Green operator for x1-broadcast
+        # workloads (qtt_ctx_set_green_broadcast), against the row above
+        if time_left() > 200:
+            try:
+                w1 = workload("lamfib256")
+                ref1 = golden("lamfib256")
+                ctx.set_concurrency(6)
+                ctx.set_green_broadcast(True)
+                ph1 = torch.from_numpy(np.ascontiguousarray(w1.phase)).pin_memory().numpy()
+                dC = Q.qtt_from_phase_field(ctx, ph1, w1.n, w1.E, w1.nu, None, w1.eps_tt,
+                                            w1.rmax)
+                t_b = time.perf_counter()
+                Q.ls_solve_ceff(ctx, dC, Q.solve_params(w1.tol, 1, w1.eps_tt, w1.rmax, 0, 16),
+                                loads=[0])       # builds the plane operator outside the timing
+                t_b = time.perf_counter() - t_b
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                C1, inf1, _ = Q.ls_solve_ceff(ctx, dC, params)
+                e1.record(stream)
+                e1.synchronize()
+                dC.free()
+                q1 = qualifying(C1, inf1, ref1, w1.tol)
+                line["plane_green"] = {
+                    "workload": DESCR["lamfib256"], "lanes": 6,
+                    "green": "Gamma(0, xi_2, xi_3) (x) I on the x1 cores (x1-broadcast geometry)",
+                    "solves_qualifying": len(q1),
+                    "solves_per_s": len(q1) / (e0.elapsed_time(e1) / 1e3),
+                    "build_and_first_iteration_s": round(t_b, 3),
+                    "iters_per_load": [i["iters"] for i in inf1],
+                    "max_rank": max(i["max_rank"] for i in inf1),
+                    "ceff_rel_err_vs_dense_oracle": ceff_errors(C1, ref1)}
+            except Exception as ex:  # noqa: BLE001
+                line["plane_green"] = {"failed": str(ex)}
+            finally:
+                ctx.set_green_broadcast(False)
         # ---- the 8-sphere workload of the same materials and settings (one C_eff)
         if time_left() > 180:
-            w2 = workload("spheres256")
-            ref2 = golden("spheres256")
-            ctx.set_concurrency(6)
-            p2 = Q.solve_params(w2.tol, 40, w2.eps_tt, w2.rmax, 0, 16)
-            ph2 = torch.from_numpy(np.ascontiguousarray(w2.phase)).pin_memory().numpy()
-            dC = Q.qtt_from_phase_field(ctx, ph2, w2.n, w2.E, w2.nu, None, w2.eps_tt, w2.rmax)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            C2, inf2, _ = Q.ls_solve_ceff(ctx, dC, p2)
-            e1.record(stream)
-            e1.synchronize()
-            dC.free()
-            q2 = qualifying(C2, inf2, ref2, w2.tol)
-            line["spheres256"] = {
-                "workload": DESCR["spheres256"], "max_iter": 40, "solves": 6,
-                "solves_qualifying": len(q2),
-                "raw_solves_per_s": 6 / (e0.elapsed_time(e1) / 1e3),
-                "residual_per_load": [i["residual"] for i in inf2],
-                "iters_per_load": [i["iters"] for i in inf2],
-                "rank_cap_hit": any(i["rank_cap_hit"] for i in inf2),
-                "ceff_rel_err_vs_dense_oracle": ceff_errors(C2, ref2),
-                "why_not_counted": "rank-capped at r_max 128: the 8-sphere indicator needs QTT "
-                                   "rank > 1300 at the middle bond for 1 % field error"}
+            try:
+                w2 = workload("spheres256")
+                ref2 = golden("spheres256")
+                ctx.set_concurrency(6)
+                p2 = Q.solve_params(w2.tol, 40, w2.eps_tt, w2.rmax, 0, 16)
+                ph2 = torch.from_numpy(np.ascontiguousarray(w2.phase)).pin_memory().numpy()
+                dC = Q.qtt_from_phase_field(ctx, ph2, w2.n, w2.E, w2.nu, None, w2.eps_tt, w2.rmax)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                C2, inf2, _ = Q.ls_solve_ceff(ctx, dC, p2)
+                e1.record(stream)
+                e1.synchronize()
+                dC.free()
+                q2 = qualifying(C2, inf2, ref2, w2.tol)
+                line["spheres256"] = {
+                    "workload": DESCR["spheres256"], "max_iter": 40, "solves": 6,
+                    "solves_qualifying": len(q2),
+                    "raw_solves_per_s": 6 / (e0.elapsed_time(e1) / 1e3),
+                    "residual_per_load": [i["residual"] for i in inf2],
+                    "iters_per_load": [i["iters"] for i in inf2],
+                    "rank_cap_hit": any(i["rank_cap_hit"] for i in inf2),
+                    "ceff_rel_err_vs_dense_oracle": ceff_errors(C2, ref2),
+                    "why_not_counted": "rank-capped at r_max 128: the 8-sphere indicator needs QTT "
+                                       "rank > 1300 at the middle bond for 1 % field error"}
+            except Exception as ex:  # noqa: BLE001
+                line["spheres256"] = {"failed": str(ex)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
