@@ -374,11 +374,6 @@ def tto_apply_sketched(op, x, ell: int, seed: int, apply_id: int):
     return out
 
 
-def _right_orth_tt(cores):
-    """Right-orthogonalised copy (cores 1..L-1 with orthonormal rows)."""
-    return tt_right_orthogonalize(cores)
-
-
 def tto_apply_amen(op, x, eps: float, rmax: int = 1 << 30, y0=None, kick: int = 4,
                    sweeps: int = 20, seed: int = 0, tol_change: float = None):
     """Compressed product y ~ A x by the AMEn-adapted scheme of App. B.
@@ -431,8 +426,8 @@ def tto_apply_amen(op, x, eps: float, rmax: int = 1 << 30, y0=None, kick: int = 
     prev = None
     done = 0
     for sw in range(sweeps):
-        y = _right_orth_tt(y)
-        z = _right_orth_tt(z)
+        y = tt_right_orthogonalize(y)
+        z = tt_right_orthogonalize(z)
         # right environments: projections of A x and of y onto the right frames
         Ry = [None] * (L + 1)
         Rz = [None] * (L + 1)
