@@ -30,3 +30,17 @@ def test_every_entry_point_cites_and_documents():
     body = txt[txt.index("typedef struct qtt_op* qtt_op_t;"):]
     decls = re.findall(r"\n((?:int|void|size_t|uint64_t|const char\*) [a-z_0-9]+\()", body)
     assert len(decls) >= 25
+
+
+def test_context_setters_reject_a_null_context(lib_built):
+    """The setters validate their context before touching it (host code only,
+    no CUDA call), so they can be called here without a GPU."""
+    lib = ctypes.CDLL(lib_built.LIB_PATH)
+    calls = [("qtt_ctx_set_green_broadcast", (1,)), ("qtt_ctx_set_concurrency", (6,)),
+             ("qtt_ctx_set_contraction", (0,)), ("qtt_ctx_set_factorization", (0,)),
+             ("qtt_ctx_set_svd", (1, 6)), ("qtt_ctx_set_tt_svd", (ctypes.c_double(2e9),)),
+             ("qtt_ctx_set_jacobi", (ctypes.c_double(1.0), 40)), ("qtt_ctx_set_profiling", (1,))]
+    for name, args in calls:
+        f = getattr(lib, name)
+        f.restype = ctypes.c_int
+        assert f(None, *args) == lib_built.QTT_EINVAL, name
