@@ -140,3 +140,19 @@ def test_2d_green_identities(scheme):
     assert np.allclose((G @ C0 @ G)[keep], G[keep], atol=1e-12)
     mirror = G[np.ix_(*[(-np.arange(N)) % N for N in shape])]
     assert np.allclose(mirror, np.conj(G), atol=1e-13)
+
+
+@pytest.mark.parametrize("scheme", ["direct", "staggered"])
+def test_extruded_section_keeps_out_of_plane_strain_zero(scheme):
+    """Under in-plane loads (22, 33, 23) the 3D oracle's iterates on a section
+    extruded along x1 keep eps_11, 2 eps_12 and 2 eps_13 at zero (Gamma's rows
+    with an index 1 vanish at xi_1 = 0), the fact the plane-strain reading rests
+    on; the in-plane strain equals the 2D oracle's."""
+    ph2 = _two_phase((8, 8), 9)
+    E, nu = (1.0, 12.0), (0.3, 0.22)
+    for k3, k2 in zip(IN_PLANE, range(3)):
+        r3 = dense.basic_scheme(ph2[None], E, nu, np.eye(6)[k3], tol=1e-12, scheme=scheme)
+        r2 = dense2d.basic_scheme2(ph2, E, nu, np.eye(3)[k2], tol=1e-12, scheme=scheme)
+        eps3 = r3["eps"][:, 0]
+        assert np.abs(eps3[[0, 4, 5]]).max() < 1e-13
+        assert np.allclose(eps3[IN_PLANE], r2["eps"], atol=1e-10)
