@@ -698,6 +698,34 @@ def main():
                 line["plane_green"] = {"failed": str(ex)}
             finally:
                 ctx.set_green_broadcast(False)
+        # ---- 2D plane strain: the paper's Square section (256^2, its materials)
+        # through ls_solve_ceff_plane_strain (the section extruded along a
+        # broadcast x1 axis), against the stored 2D dense-oracle columns
+        if time_left() > 300:
+            try:
+                from paper_2412_11566_gb300 import synth as _synth
+                ref2d = golden("square256_plane_strain")
+                sec = _synth.square2d(8)
+                E2d, nu2d = _synth.paper_materials()
+                ctx.set_concurrency(3)
+                p2d = Q.solve_params(1e-4, 200, 1e-6, 128, 0, 16)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                C2d, inf2d, _ = Q.ls_solve_ceff_plane_strain(ctx, sec, 8, E2d, nu2d, p2d,
+                                                             eps_tt=1e-6, rmax=128)
+                e1.record(stream)
+                e1.synchronize()
+                q2d = qualifying(C2d, inf2d, ref2d, 1e-4, loads=range(3))
+                line["plane_strain_2d"] = {
+                    "workload": "paper's 2D Square section (side L/2) on 256^2, E 4/3 and 29/3, "
+                                "nu 1/3, plane strain, tol 1e-4, eps_tt 1e-6, r_max 128",
+                    "solves": 3, "solves_qualifying": len(q2d),
+                    "solves_per_s": len(q2d) / (e0.elapsed_time(e1) / 1e3),
+                    "iters_per_load": [i["iters"] for i in inf2d],
+                    "max_rank": max(i["max_rank"] for i in inf2d),
+                    "ceff_rel_err_vs_dense_oracle": ceff_errors(C2d, ref2d)}
+            except Exception as ex:  # noqa: BLE001
+                line["plane_strain_2d"] = {"failed": str(ex)}
         # ---- the 8-sphere workload of the same materials and settings (one C_eff)
         if time_left() > 180:
             try:

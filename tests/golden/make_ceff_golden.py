@@ -5,6 +5,12 @@ geometry generator. Run from the repo root:
 
     python tests/golden/make_ceff_golden.py --workload lamfib256 [--tol 1e-4] [--loads 0,1,2,3,4,5]
     python tests/golden/make_ceff_golden.py --family lamfib256 --items 64
+    python tests/golden/make_ceff_golden.py --plane2d square256
+
+With --plane2d the 2D plane-strain C_eff (Voigt 11, 22, 12) of the paper's
+Square section (synth.square2d, side L/2, the paper's materials) on a 256^2
+grid is written by the 2D oracle (oracle/dense2d.py) to
+tests/golden/square256_plane_strain_ceff_tol<tol>.json, columns of 3 entries.
 
 With --family the items of synth.lamfib_family (n = 8) are written to
 tests/golden/<family>_family_ceff_tol<tol>.json under "items" (item index ->
@@ -26,7 +32,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
 sys.path.insert(0, ROOT)
 
-from oracle import dense  # noqa: E402
+from oracle import dense, dense2d  # noqa: E402
 from paper_2412_11566_gb300 import synth  # noqa: E402
 
 
@@ -50,15 +56,42 @@ def solve_columns(w, loads, tol, dst):
         yield
 
 
+def plane2d_square(tol):
+    """The paper's 2D Square section at 256^2 with its materials, plane strain."""
+    n = 8
+    sec = synth.square2d(n)
+    E, nu = synth.paper_materials()
+    out_path = os.path.join(os.path.dirname(__file__),
+                            f"square{1 << n}_plane_strain_ceff_tol{tol:g}.json")
+    res = {"_about": "plane-strain C_eff (Voigt 11, 22, 12) of synth.square2d(8) with "
+                     "synth.paper_materials() by the 2D oracle (oracle/dense2d.py, Alg. 1, "
+                     "Direct scheme, fp64), written by tests/golden/make_ceff_golden.py",
+           "n": n, "tol": tol, "E": list(E), "nu": list(nu), "grid": list(sec.shape),
+           "columns": {}}
+    for k in range(3):
+        t = time.time()
+        r = dense2d.basic_scheme2(sec, E, nu, np.eye(3)[k], tol=tol, max_iter=5000)
+        res["columns"][str(k)] = {"sigma_bar_re": r["sigma_bar"].real.tolist(),
+                                  "sigma_bar_im": r["sigma_bar"].imag.tolist(),
+                                  "iters": r["iters"], "seconds": time.time() - t}
+        print(f"square256 plane strain load {k}: {r['iters']} iterations", flush=True)
+    json.dump(res, open(out_path, "w"), indent=1)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="spheres256")
     ap.add_argument("--family", default=None)
+    ap.add_argument("--plane2d", default=None)
     ap.add_argument("--items", type=int, default=64)
     ap.add_argument("--tol", type=float, default=1e-4)
     ap.add_argument("--loads", default="0,1,2,3,4,5")
     args = ap.parse_args()
     loads = [int(v) for v in args.loads.split(",")]
+    if args.plane2d:
+        assert args.plane2d == "square256"
+        plane2d_square(args.tol)
+        return
     if args.family:
         assert args.family == "lamfib256"
         ws = synth.lamfib_family(8, args.items)

@@ -52,3 +52,17 @@ def test_family_columns_and_iteration_mean():
     assert all(len(it["columns"]) == 6 for it in fam["items"].values())
     its = [c["iters"] for it in fam["items"].values() for c in it["columns"].values()]
     assert abs(b.dense_iters(fam) - np.mean(its)) < 1e-12
+
+
+def test_plane_strain_golden_through_the_bench_helpers():
+    """The 2D row's stored columns (3 entries each, Voigt 11, 22, 12) load through
+    bench.golden and work with ceff_errors / qualifying on a 3 x 3 C_eff."""
+    b = _bench()
+    ref = b.golden("square256_plane_strain")
+    assert ref is not None and sorted(ref["columns"]) == ["0", "1", "2"]
+    C = np.array([ref["columns"][str(k)]["sigma_bar_re"] for k in range(3)]).T
+    assert C.shape == (3, 3) and np.allclose(C, C.T, atol=1e-8)
+    err = b.ceff_errors(C * (1 + 2e-5), ref)
+    assert max(err.values()) < 3e-5
+    infos = [{"residual": 5e-5}] * 3
+    assert b.qualifying(C, infos, ref, 1e-4, loads=range(3)) == [0, 1, 2]
