@@ -58,4 +58,5 @@ def test_plane_green_setting_leaves_other_geometries_alone(Q):
     E, nu = (1.0, 10.0), (0.3, 0.3)
     a = _solve(Q, ph, n, E, nu, Q.QTT_SCHEME_DIRECT, True, [0])
     b = _solve(Q, ph, n, E, nu, Q.QTT_SCHEME_DIRECT, False, [0])
-    assert np.array_equal(a, b)
+    # same operators and sketches; only the order of atomic FP64 sums may differ
+    assert np.allclose(a, b, rtol=1e-12, atol=1e-12 * np.abs(b).max())
