@@ -90,6 +90,45 @@ def tt_svd(T: np.ndarray, eps: float, rmax: int = 1 << 30):
     return cores
 
 
+def tt_svd_randomized(T: np.ndarray, eps: float, rmax: int = 1 << 30, oversample: int = 8,
+                      seed: int = 0):
+    """TT-SVD with randomized SVDs of the unfoldings (App. D: the preprocessing
+    that scales to large grids), left to right. At each bond the unfolding M
+    (P x c) is sketched as Y = M Omega with a Gaussian Omega of k + oversample
+    columns; Q = orth(Y), and the SVD of the small Q^H M gives the bond. k starts
+    at 8 and doubles until the discarded tail of Q^H M's spectrum plus the part
+    of M outside range(Q) is within the per-bond threshold
+    eps ||T|| / sqrt(L - 1) (or k reaches min(P, c)); then the rank is chosen
+    by the tail rule and capped at rmax, as in tt_svd."""
+    rng = np.random.default_rng(seed)
+    dims = T.shape
+    L = len(dims)
+    delta2 = (eps * np.linalg.norm(T)) ** 2 / max(L - 1, 1)
+    cores = []
+    M = T.reshape(dims[0], -1).astype(np.complex128)
+    r = 1
+    for j in range(L - 1):
+        M = M.reshape(r * dims[j], -1)
+        P, c = M.shape
+        k = min(8, P, c)
+        while True:
+            Om = rng.standard_normal((c, min(k + oversample, c))) \
+                + 1j * rng.standard_normal((c, min(k + oversample, c)))
+            Q, _ = np.linalg.qr(M @ Om)
+            B = Q.conj().T @ M
+            outside = np.linalg.norm(M - Q @ B) ** 2      # energy outside range(Q)
+            U, S, Vh = _svd(B)
+            kk, _ = truncation_rank(S, max(delta2 - outside, 0.0), rmax)
+            if (outside <= 0.25 * delta2 and kk < Q.shape[1]) or k >= min(P, c):
+                break
+            k = min(2 * k, P, c)
+        cores.append((Q @ U[:, :kk]).reshape(r, dims[j], kk))
+        M = S[:kk, None] * Vh[:kk]
+        r = kk
+    cores.append(M.reshape(r, dims[-1], 1))
+    return cores
+
+
 def tt_full(cores) -> np.ndarray:
     """Dense tensor of a TT (eq. (tt_format))."""
     out = cores[0]

@@ -548,3 +548,22 @@ def test_plane_green_on_broadcast_geometry(scheme):
     a = oq.ls_solve(dC3, Gf, S, Sh, np.eye(6)[0], n, 0.0, 1e-12, 1000, max_iter=3, lame0=lam0)
     b = oq.ls_solve(dC3, Gp, S, Sh, np.eye(6)[0], n, 0.0, 1e-12, 1000, max_iter=3, lame0=lam0)
     assert np.abs(a["sigma_bar"] - b["sigma_bar"]).max() > 1e-4 * np.abs(a["sigma_bar"]).max()
+
+
+def test_randomized_tt_svd_matches_tt_svd():
+    """App. D's randomized TT-SVD: on an exact-rank TT it finds the same ranks
+    as the TT-SVD at 1e-12 and 1e-6; on the 16^3 Green field it meets the
+    TT-SVD's error bound eps ||T|| with at most one more rank per bond."""
+    rng = np.random.default_rng(3)
+    ranks = [1, 4, 6, 8, 8, 8, 8, 8, 8, 8, 6, 4, 2, 1]
+    T = oq.tt_full(random_tt(rng, [6] + [2] * 12, ranks)).reshape([6] + [2] * 12)
+    for eps in (1e-12, 1e-6):
+        b = oq.tt_svd_randomized(T, eps, seed=1)
+        assert oq.tt_ranks(b) == oq.tt_ranks(oq.tt_svd(T, eps))
+        assert np.linalg.norm(oq.tt_full(b).reshape(T.shape) - T) < 1e-12 * np.linalg.norm(T)
+    G = oq.gamma_field_sfft(4, 1.3, 0.7).reshape((36,) + (2,) * 12).astype(np.complex128)
+    for eps in (1e-2, 1e-4, 1e-6):
+        a, b = oq.tt_svd(G, eps), oq.tt_svd_randomized(G, eps, seed=2)
+        err = np.linalg.norm(oq.tt_full(b).reshape(G.shape) - G) / np.linalg.norm(G)
+        assert err <= eps
+        assert all(rb <= ra + 1 for ra, rb in zip(oq.tt_ranks(a), oq.tt_ranks(b)))
