@@ -156,3 +156,23 @@ def test_extruded_section_keeps_out_of_plane_strain_zero(scheme):
         eps3 = r3["eps"][:, 0]
         assert np.abs(eps3[[0, 4, 5]]).max() < 1e-13
         assert np.allclose(eps3[IN_PLANE], r2["eps"], atol=1e-10)
+
+
+def test_extruded_strain_has_the_2d_ranks():
+    """The deviation from a 3-component Voigt core costs only the x1 cores: the
+    converged strain of the extruded section, compressed as a 6-component QTT
+    over 3n binary cores, has the 2D field's ranks on its 2n in-plane cores
+    (within one, from the truncation) and rank 3 through its n x1 cores."""
+    from oracle import qtt as oq
+    n = 5
+    N = 1 << n
+    sec = synth.square2d(n)
+    E, nu = synth.paper_materials()
+    e2 = dense2d.basic_scheme2(sec, E, nu, np.eye(3)[0], tol=1e-8)["eps"].real
+    e3 = np.broadcast_to(dense.basic_scheme(sec[None], E, nu, np.eye(6)[1], tol=1e-8)["eps"].real,
+                         (6, N, N, N))
+    r2 = oq.tt_ranks(oq.tt_svd(e2.reshape((3,) + (2,) * (2 * n)).astype(np.complex128), 1e-6))
+    r3 = oq.tt_ranks(oq.tt_svd(np.ascontiguousarray(e3).reshape((6,) + (2,) * (3 * n))
+                                 .astype(np.complex128), 1e-6))
+    assert all(r == 3 for r in r3[1:n + 2])
+    assert all(abs(a - b) <= 1 for a, b in zip(r3[n + 1:], r2[1:]))
