@@ -302,7 +302,8 @@ def lamfib_family(n: int = 8, items: int = 64, base_seed: int = 2412):
 
 def by_name(name: str) -> Workload:
     """The named workloads of the benchmark and the stored C_eff columns."""
-    table = {"spheres256": spheres256, "lamfib256": lamfib256}
+    table = {"spheres256": spheres256, "lamfib256": lamfib256,
+             "lamfib2048": laminate_fibres2048}
     return table[name]()
 
 
@@ -326,5 +327,8 @@ def sphere128_grad() -> Workload:
 
 
 def laminate_fibres2048(n: int = 11) -> Workload:
+    """The large QTT-only configuration: laminate_with_fibres on 2048^3
+    (broadcast x1), matrix E=1, inclusions E=100, nu 0.3; tol 1e-4, eps_tt
+    1e-6, r_max 256."""
     return Workload(f"lamfib{1 << n}", n, laminate_with_fibres(n), (1.0, 100.0), (0.3, 0.3),
                     1e-4, 1e-6, 256)

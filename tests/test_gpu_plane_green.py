@@ -4,6 +4,9 @@ must match solves with the full Green operator and the dense oracle; solves
 on geometries without that broadcast must be unaffected by the setting. The
 identity behind it is pinned on the CPU in
 tests/test_oracle_qtt.py::test_plane_green_on_broadcast_geometry."""
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -17,6 +20,7 @@ pytestmark = [
 ]
 
 SEED = 2412
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
 
 
 @pytest.fixture(scope="module")
@@ -60,3 +64,27 @@ def test_plane_green_setting_leaves_other_geometries_alone(Q):
     b = _solve(Q, ph, n, E, nu, Q.QTT_SCHEME_DIRECT, False, [0])
     # same operators and sketches; only the order of atomic FP64 sums may differ
     assert np.allclose(a, b, rtol=1e-12, atol=1e-12 * np.abs(b).max())
+
+
+@pytest.mark.skipif(os.environ.get("QTT_RUN_2048") != "1",
+                    reason="the 2048^3 QTT-only configuration: set QTT_RUN_2048=1 (about 200 GB "
+                           "of workspace; minutes per load)")
+def test_lamfib2048_load_e11(Q):
+    """The 2048^3 laminate-with-fibres configuration (contrast 100, tol 1e-4,
+    eps_tt 1e-6, r_max 256), load e11, through the plane Green operator,
+    against the stored dense-oracle column (the dense scheme on the reduced
+    (1, 2048, 2048) grid)."""
+    w = synth.by_name("lamfib2048")
+    ref = json.load(open(os.path.join(GOLD, "lamfib2048_ceff_tol0.0001.json")))["columns"]["0"]
+    ctx = Q.Context(0, Q.QTT_FP64, 200 << 30, seed=SEED)
+    try:
+        ctx.set_green_broadcast(True)
+        dC = Q.qtt_from_phase_field(ctx, w.phase, w.n, w.E, w.nu, None, w.eps_tt, w.rmax)
+        C, infos, rc = Q.ls_solve_ceff(ctx, dC, Q.solve_params(w.tol, 600, w.eps_tt, w.rmax, 0, 16),
+                                       loads=[0])
+        dC.free()
+    finally:
+        ctx.close()
+    r = np.asarray(ref["sigma_bar_re"])
+    assert infos[0]["residual"] < w.tol
+    assert np.abs(C[:, 0] - r).max() <= 1e-4 * np.abs(r).max()
