@@ -192,6 +192,23 @@ int qtt_rank_estimate(qtt_ctx_t ctx, const uint8_t* phase_a, const int shape_a[3
  * with an identity Voigt core; adjoint = 1 gives S^H = S^-1. Built on the
  * device by TT-SVD of the per-axis matrix at accuracy eps. */
 int qtt_sfft_operator(qtt_ctx_t ctx, int n, int adjoint, double eps, qtt_op_t* out);
+/* The SFFT MPO of one axis built the way Sec. 4.2 builds it, on the host (no
+ * context, no GPU): the reduced QFT circuit of Sec. 4.1 (Hadamard and
+ * controlled-phase gates, no SWAP network; each controlled phase split into
+ * a copy and a phase tensor) applied gate by gate to the identity MPO by
+ * zip-up sweeps, then one TT rounding at eps. It is the operator
+ * S[k', x] = N^-1/2 exp(2 pi i rev(k') x / N) that qtt_sfft_operator builds
+ * by TT-SVD, with the circuit's ranks. Output: ranks[0..n] (n + 1 ints) and
+ * the cores (r_k, 2 out, 2 in, r_{k+1}) concatenated in core order, row-major,
+ * interleaved complex doubles, into `cores` of capacity `cap` doubles;
+ * *needed receives the number of doubles. Each partial product of the gates
+ * is rounded at eps / 100, so the ranks stay near the final ones and the
+ * cost is milliseconds (0.05 s at n = 12). Returns QTT_EINVAL for n outside
+ * 1..24, eps <= 0, null ranks/needed, or cores null or too small (ranks and
+ * *needed are filled in then, so a first call with cap = 0 sizes the
+ * buffer); QTT_ENOMEM if host memory runs out. */
+int qtt_sfft_mpo_zipup(int n, double eps, int* ranks, double* cores, size_t cap,
+                       size_t* needed);
 
 /* The Green operator Gamma_hat^0 (App. A, eq. (orig_green_eshelby),
  * isotropic C0 = (lambda0, mu0)) of a discretisation scheme in the SFFT

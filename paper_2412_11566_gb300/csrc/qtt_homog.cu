@@ -23,6 +23,7 @@
 
 #include "../../include/qtt_homog.h"
 #include "kernels.cuh"
+#include "sfft_zipup.h"
 #include "tc_gemm.cuh"
 
 using namespace qtt;
@@ -3339,6 +3340,30 @@ int qtt_contraction_bench(qtt_ctx_t ctx, int mode, int M, int N, int K, int reps
   d.release(C64);
   return QTT_OK;
   API_END
+}
+
+int qtt_sfft_mpo_zipup(int n, double eps, int* ranks, double* cores, size_t cap,
+                       size_t* needed) {
+  if (n < 1 || n > 24 || !(eps > 0) || !ranks || !needed) return QTT_EINVAL;
+  qtt_zipup::Mpo op;
+  try {
+    op = qtt_zipup::sfft_mpo(n, eps);
+  } catch (const std::bad_alloc&) {
+    return QTT_ENOMEM;
+  }
+  size_t tot = 0;
+  for (const auto& c : op) tot += 2 * c.a.size();
+  *needed = tot;
+  ranks[0] = 1;
+  for (int k = 0; k < n; ++k) ranks[k + 1] = op[k].r1;
+  if (!cores || cap < tot) return QTT_EINVAL;
+  size_t off = 0;
+  for (const auto& c : op)
+    for (const auto& z : c.a) {
+      cores[off++] = z.real();
+      cores[off++] = z.imag();
+    }
+  return QTT_OK;
 }
 
 int qtt_ctx_set_green_broadcast(qtt_ctx_t ctx, int on) {

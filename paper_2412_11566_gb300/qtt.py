@@ -109,6 +109,7 @@ _sig("qtt_ctx_set_contraction", _i, [_p, _i])
 _sig("qtt_ctx_set_factorization", _i, [_p, _i])
 _sig("qtt_ctx_set_svd", _i, [_p, _i, _i])
 _sig("qtt_ctx_set_green_broadcast", _i, [_p, _i])
+_sig("qtt_sfft_mpo_zipup", _i, [_i, _d, C.POINTER(_i), _dp, C.c_size_t, C.POINTER(C.c_size_t)])
 _sig("qtt_contraction_bench", _i, [_p, _i, _i, _i, _i, _i, _dp, _dp])
 _sig("ls_solve_ceff", _i, [_p, _p, C.POINTER(SolveParams), _ip, _i, _dp, C.POINTER(SolveInfo)])
 _sig("ls_solve_batched", _i, [_p, _i, C.POINTER(_p), C.POINTER(SolveParams), _dp,
@@ -375,6 +376,28 @@ def qtt_rank_estimate(ctx: Context, phase_a, phase_b, n, E, nu, eps_tt=1e-6, n_t
                                     nua.ctypes.data_as(_dp), eps_tt, nt, out.ctypes.data_as(_dp)))
     return {"rank_n": int(out[0]), "rank_n1": int(out[1]), "growth": float(out[2]),
             "rank_target": float(out[3]), "n_target": nt}
+
+
+def qtt_sfft_mpo_zipup(n, eps=1e-12):
+    """The SFFT MPO of one axis from the QFT circuit by zip-up (host, no GPU):
+    a list of complex cores (r, 2, 2, r')."""
+    ranks = (_i * (n + 1))()
+    need = C.c_size_t()
+    rc = lib.qtt_sfft_mpo_zipup(int(n), float(eps), ranks, None, 0, C.byref(need))
+    if rc != QTT_EINVAL or need.value == 0:
+        raise QttError(rc, "qtt_sfft_mpo_zipup: sizing call failed")
+    buf = np.empty(need.value, dtype=np.float64)
+    rc = lib.qtt_sfft_mpo_zipup(int(n), float(eps), ranks, buf.ctypes.data_as(_dp), buf.size,
+                                C.byref(need))
+    if rc != QTT_OK:
+        raise QttError(rc, "qtt_sfft_mpo_zipup failed")
+    z = buf.view(np.complex128)
+    out, off = [], 0
+    for k in range(n):
+        cnt = ranks[k] * 4 * ranks[k + 1]
+        out.append(z[off:off + cnt].reshape(ranks[k], 2, 2, ranks[k + 1]).copy())
+        off += cnt
+    return out
 
 
 def qtt_sfft_operator(ctx: Context, n, adjoint=False, eps=1e-14):

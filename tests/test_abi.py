@@ -44,3 +44,24 @@ def test_context_setters_reject_a_null_context(lib_built):
         f = getattr(lib, name)
         f.restype = ctypes.c_int
         assert f(None, *args) == lib_built.QTT_EINVAL, name
+
+
+def test_native_zipup_sfft_matches_the_oracle(lib_built):
+    """The library's host zip-up construction of the SFFT MPO (Sec. 4.2; no GPU)
+    is S = P_rev F+ (the oracle's dense bit-reversed DFT) for n = 1..8, has the
+    ranks of the oracle's circuit construction at 1e-12, and reaches the
+    printed rank 10 at 1e-10 for n = 8 (Sec. 5.2)."""
+    import numpy as np
+    from oracle import qtt as oq
+    Q = lib_built
+    for n in range(1, 9):
+        cores = Q.qtt_sfft_mpo_zipup(n, 1e-12)
+        assert np.allclose(oq.tto_full(cores), oq.sfft_dense(n), atol=1e-13)
+        assert [c.shape[0] for c in cores] == [c.shape[0] for c in oq.sfft_axis_mpo_zipup(n, 1e-12)]
+    assert max(c.shape[0] for c in Q.qtt_sfft_mpo_zipup(8, 1e-10)) == 10
+    import ctypes as C
+    need = C.c_size_t()
+    ranks = (C.c_int * 26)()
+    assert Q.lib.qtt_sfft_mpo_zipup(25, 1e-12, ranks, None, 0, C.byref(need)) == Q.QTT_EINVAL
+    big = Q.qtt_sfft_mpo_zipup(20, 1e-10)        # 2^20 points per axis, no dense matrix
+    assert len(big) == 20 and max(c.shape[0] for c in big) <= 12
