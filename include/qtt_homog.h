@@ -249,7 +249,8 @@ int qtt_op_apply(qtt_ctx_t ctx, qtt_op_t op, qtt_tt_t in, double eps_tt, int rma
                  int oversample, int apply_id, qtt_tt_t* out);
 /* SFFT, inverse SFFT and Green products with the context's cached operators
  * (built on first use for the TT's n; Sec. 4.3, Alg. 2's transform and Green steps, App. D
- * lookup table). n[3] must be equal (cubic grids). */
+ * lookup table). n[3] must be equal (cubic grids). gamma0_apply's scheme is
+ * one of QTT_SCHEME_* (0..5), as for qtt_gamma_operator. */
 int sfft_apply(qtt_ctx_t ctx, qtt_tt_t in, double eps_tt, int rmax, qtt_tt_t* out);
 int isfft_apply(qtt_ctx_t ctx, qtt_tt_t in, double eps_tt, int rmax, qtt_tt_t* out);
 int gamma0_apply(qtt_ctx_t ctx, const int n[3], double lambda0, double mu0, int scheme,
@@ -419,8 +420,8 @@ int qtt_ctx_set_green_broadcast(qtt_ctx_t ctx, int on);
  * context. Returns QTT_EINVAL for an unknown mode. */
 int qtt_ctx_set_factorization(qtt_ctx_t ctx, int mode);
 /* C_eff and its derivatives with respect to phase parameters (E or nu of a
- * phase). The Direct-scheme LS operator (with the Nyquist symmetrisation of
- * App. A) is self-adjoint, so the adjoint solution of load l equals its
+ * phase). The LS operator of every scheme (with the Nyquist symmetrisation of
+ * App. A for the Direct one) is self-adjoint, so the adjoint solution of load l equals its
  * forward strain and dC_eff[l][k]/dp = mean(eps_l^T (dC/dp) eps_k): the six
  * forward solves are kept and contracted with the raised TTO of dC/dp
  * (qtt_from_phase_matrices of the derivative of the phase stiffness). phase,
