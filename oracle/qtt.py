@@ -40,7 +40,7 @@ import math
 
 import numpy as np
 
-from . import dense
+from . import dense, dense2d
 
 # ------------------------------------------------------------------ helpers
 
@@ -750,7 +750,8 @@ def to_voigt_field(cores, n: int) -> np.ndarray:
 
 
 def ls_solve(dC, G, S, Sh, E_voigt, n: int, tol: float, eps: float, rmax: int,
-             max_iter: int = 5000, oversample: int = 16, seed: int = 2412, lame0=None):
+             max_iter: int = 5000, oversample: int = 16, seed: int = 2412, lame0=None,
+             e_field=None, c0=None):
     """Alg. 2 (SFFT-based homogenisation), one unit load:
         tau_m   = round((C - C0) eps_m)
         tauh_m  = round(S tau_m)
@@ -760,8 +761,11 @@ def ls_solve(dC, G, S, Sh, E_voigt, n: int, tol: float, eps: float, rmax: int,
     (product number 4 (m - 1) + j for the j-th product of iteration m), each
     rounding at (eps, rmax); stop when ||eps_m+1 - eps_m||_F / ||E||_F < tol.
     sigma_bar = C0 E + mean((C - C0) eps_final) (Sec. 2, C_eff paragraph).
-    Returns dict(eps, sigma_bar, iters, history, max_rank, cap_hit)."""
-    Ett = e_tt(n, E_voigt)
+    Returns dict(eps, sigma_bar, iters, history, max_rank, cap_hit).
+    e_field / c0: the mean-strain TT and the reference Voigt stiffness for a
+    Voigt form other than the 3D one (the 2D plane-strain operators below);
+    by default e_tt(n, E_voigt) and the 3D stiffness of lame0."""
+    Ett = e_tt(n, E_voigt) if e_field is None else e_field
     normE = tt_norm(Ett)
     ell = rmax + oversample
     x = Ett
@@ -786,9 +790,58 @@ def ls_solve(dC, G, S, Sh, E_voigt, n: int, tol: float, eps: float, rmax: int,
         if rel < tol:
             break
     sig = tto_sandwich_mean(dC, x)
-    if lame0 is not None:
+    if c0 is not None:
+        sig = sig + np.asarray(c0) @ np.asarray(E_voigt, dtype=np.float64)
+    elif lame0 is not None:
         sig = sig + dense.stiffness_voigt(*lame0) @ np.asarray(E_voigt, dtype=np.float64)
     return dict(eps=x, sigma_bar=sig, iters=it, history=hist, max_rank=maxr, cap_hit=cap)
+
+
+# ------------------------------------------------------------------ 2D (plane strain)
+# The paper's 2D form (Sec. 2: 3-component Voigt vectors, 3 x 3 stiffness; a
+# controlled QTT whose Voigt core has d = 3, Sec. 4.3) on a 2^n x 2^n grid:
+# L = 2n + 1 cores, x1 bits then x2 bits, most significant first.
+
+
+def _field_to_tto(F: np.ndarray, bits: int, eps: float, rmax: int):
+    """(v, v, 2^bits...) Voigt-matrix field -> raised TTO with Voigt core (1, v, v, a1)."""
+    v = F.shape[0]
+    cores = tt_svd(F.reshape((v * v,) + (2,) * bits).astype(np.complex128), eps, rmax)
+    c0 = cores[0].reshape(1, v, v, cores[0].shape[2])
+    return [c0] + raise_tt(cores[1:])
+
+
+def sfft_operator_2d(n: int, eps: float = 1e-12, adjoint: bool = False):
+    """2D SFFT TTO: 3 x 3 identity Voigt core, then the axis MPO of x1 and x2."""
+    ax = sfft_axis_mpo(n, eps)
+    op = [np.eye(3, dtype=np.complex128).reshape(1, 3, 3, 1)] + ax + ax
+    return tto_adjoint(op) if adjoint else op
+
+
+def gamma_qtt_2d(n: int, lam0: float, mu0: float, eps: float, rmax: int = 1 << 30,
+                 scheme: str = "direct"):
+    """2D Green TTO in the SFFT convention: conj(Gamma_V) of oracle.dense2d at the
+    bit-reversed frequencies, Nyquist rule included."""
+    f = axis_frequencies_bitrev(n)
+    X1, X2 = np.meshgrid(f, f, indexing="ij")
+    G = dense2d.green2_symmetrised(np.stack([X1, X2], axis=-1), lam0, mu0, 1 << n, scheme)
+    return _field_to_tto(np.conj(np.moveaxis(G, (-2, -1), (0, 1))), 2 * n, eps, rmax)
+
+
+def stiffness_qtt_2d(phase: np.ndarray, n: int, E, nu, lame0, eps: float, rmax: int = 1 << 30):
+    """(C(x) - C0) of a 2^n x 2^n section in plane strain as a raised TTO."""
+    C0 = dense2d.stiffness_voigt2(*lame0)
+    F = np.zeros((3, 3) + phase.shape)
+    for p, (e, v) in enumerate(zip(E, nu)):
+        F += (dense2d.stiffness_voigt2(*dense2d.lame(e, v)) - C0)[:, :, None, None] * (phase == p)
+    return _field_to_tto(F, 2 * n, eps, rmax)
+
+
+def e_tt_2d(n: int, E_voigt3):
+    """Rank-1 mean strain TT in 2D: Voigt core E sqrt(2)^(2n), binary cores (1, 1)/sqrt(2)."""
+    c0 = (np.asarray(E_voigt3, dtype=np.complex128) * math.sqrt(2.0) ** (2 * n)).reshape(1, 3, 1)
+    b = np.full((1, 2, 1), 1.0 / math.sqrt(2.0), dtype=np.complex128)
+    return [c0] + [b.copy() for _ in range(2 * n)]
 
 
 def phase_matrices_qtt(phase: np.ndarray, n: int, mats, eps: float, rmax: int = 1 << 30):

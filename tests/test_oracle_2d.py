@@ -176,3 +176,34 @@ def test_extruded_strain_has_the_2d_ranks():
                                  .astype(np.complex128), 1e-6))
     assert all(r == 3 for r in r3[1:n + 2])
     assert all(abs(a - b) <= 1 for a, b in zip(r3[n + 1:], r2[1:]))
+
+
+@pytest.mark.parametrize("scheme", ["direct", "staggered"])
+def test_qtt_2d_matches_dense_2d_and_the_extruded_qtt(scheme):
+    """The paper's 2D form in the QTT oracle (3-component Voigt core, 2n binary
+    cores) gives the 2D dense oracle's iterates, and the extruded 3D QTT solve
+    with the plane Green operator (the device's 2D route) gives the same
+    in-plane mean stress."""
+    from oracle import qtt as oq
+    n = 3
+    sec = _two_phase((8, 8), 4)
+    E, nu = (1.0, 12.0), (0.3, 0.22)
+    lam0 = dense2d.reference_lame(E, nu)
+    C02 = dense2d.stiffness_voigt2(*lam0)
+    dC2 = oq.stiffness_qtt_2d(sec, n, E, nu, lam0, 1e-12)
+    G2 = oq.gamma_qtt_2d(n, *lam0, 1e-12, scheme=scheme)
+    S2, Sh2 = oq.sfft_operator_2d(n), oq.sfft_operator_2d(n, adjoint=True)
+    dC3 = oq.stiffness_qtt(synth.broadcast_dense(sec[None], n), n, E, nu, lam0, 1e-12)
+    G3 = oq.gamma_qtt_plane(n, *lam0, 1e-12, scheme=scheme)
+    S3, Sh3 = oq.sfft_operator(n), oq.sfft_operator(n, adjoint=True)
+    for k2, k3 in ((0, 1), (2, 3)):
+        Ev2 = np.eye(3)[k2]
+        b = oq.ls_solve(dC2, G2, S2, Sh2, Ev2, n, 0.0, 1e-12, 1000, max_iter=15,
+                        e_field=oq.e_tt_2d(n, Ev2), c0=C02)
+        a = dense2d.basic_scheme2(sec, E, nu, Ev2, tol=0.0, max_iter=15, scheme=scheme)
+        assert np.allclose(b["history"], a["history"], rtol=1e-9, atol=1e-13)
+        assert np.abs(b["sigma_bar"] - a["sigma_bar"]).max() < 1e-10 * np.abs(a["sigma_bar"]).max()
+        c = oq.ls_solve(dC3, G3, S3, Sh3, np.eye(6)[k3], n, 0.0, 1e-12, 1000, max_iter=15,
+                        lame0=lam0)
+        assert np.abs(c["sigma_bar"][IN_PLANE] - b["sigma_bar"]).max() < \
+            1e-9 * np.abs(b["sigma_bar"]).max()
