@@ -16,8 +16,9 @@ Modules:
             and the SFFT-based scheme (Alg. 2), in the same step order as the
             CUDA path so that FP64 results can be compared to 1e-10; also the
             paper's own constructions the CUDA path replaces, to compare with:
-            the SFFT MPO from the QFT circuit by zip-up (Sec. 4.2) and the
-            AMEn-adapted product (App. B).
+            the SFFT MPO from the QFT circuit by zip-up (Sec. 4.2), the
+            AMEn-adapted product (App. B), the randomized TT-SVD (App. D),
+            and the 2D controlled QTT with a 3-component Voigt core.
 
 Every function names the passage of the paper it restates.
 
