@@ -275,3 +275,23 @@ def test_sfft_stress_error_within_the_papers_level(make):
                                         "paper_values.json")))["relative_stress_error"]["value"]
     assert r["iters"] == d["iters"]
     assert err < level
+
+
+def test_laminate_exact_after_one_iteration():
+    """Sec. 5.2: for the Laminate the analytic solution is reached after a single
+    iteration. With the paper's materials the first iterate's C_eff equals the
+    laminate closed form to rounding, in 2D (plane strain) and in 3D, and the
+    stop test ends at the second iteration (a residual at rounding level)."""
+    E, nu = synth.paper_materials()
+    ph1 = synth.laminate(5, 2).reshape(-1)
+    ref3 = laminate_closed_form(ph1, E, nu)
+    sec = synth.laminate2d(5)
+    C1 = np.array([dense2d.basic_scheme2(sec, E, nu, np.eye(3)[k], tol=0.0, max_iter=1)
+                   ["sigma_bar"].real for k in range(3)]).T
+    assert np.abs(C1 - ref3[np.ix_(IN_PLANE, IN_PLANE)]).max() < 1e-13 * np.abs(ref3).max()
+    r = dense2d.basic_scheme2(sec, E, nu, np.eye(3)[0], tol=1e-4)
+    assert r["iters"] == 2 and r["history"][1] < 1e-12
+    ph3 = synth.laminate(5, 2)                       # (1, 1, 32): layers normal to x3
+    C3 = np.array([dense.basic_scheme(ph3, E, nu, np.eye(6)[k], tol=0.0, max_iter=1)
+                   ["sigma_bar"].real for k in range(6)]).T
+    assert np.abs(C3 - ref3).max() < 1e-13 * np.abs(ref3).max()
