@@ -295,3 +295,19 @@ def test_laminate_exact_after_one_iteration():
     C3 = np.array([dense.basic_scheme(ph3, E, nu, np.eye(6)[k], tol=0.0, max_iter=1)
                    ["sigma_bar"].real for k in range(6)]).T
     assert np.abs(C3 - ref3).max() < 1e-13 * np.abs(ref3).max()
+
+
+@pytest.mark.parametrize("scheme", ["direct", "staggered"])
+def test_green_rank_grows_linearly_with_the_order(scheme):
+    """Sec. 5.2: the Green operator's rank grows about linearly with the
+    discretisation order. 2D Green TTO at delta_acc = 1e-6 (the paper's
+    materials), 16^2 to 256^2: every order adds a similar number of ranks
+    (between 5 and 20), far from the doubling per order of an uncompressible
+    operator."""
+    from oracle import qtt as oq
+    E, nu = synth.paper_materials()
+    lam0 = dense2d.reference_lame(E, nu)
+    ranks = [max(oq.tt_ranks(oq.gamma_qtt_2d(n, *lam0, 1e-6, scheme=scheme))) for n in range(4, 9)]
+    inc = np.diff(ranks)
+    assert np.all(inc >= 5) and np.all(inc <= 20)
+    assert ranks[-1] < 3 * ranks[0]
